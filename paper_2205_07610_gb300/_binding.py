@@ -1,0 +1,231 @@
+"""ctypes binding of libgotoh_gb300.so (argument marshalling only).
+
+Every step of the alignment runs in the library's CUDA kernels; this module
+only turns torch tensors / numpy arrays into pointers and sizes.  There is no
+CPU fallback: if the shared library is missing or cannot be loaded, every call
+raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+LOCAL, GLOBAL, SEMIGLOBAL = 0, 1, 2
+_MODES = {"local": LOCAL, "global": GLOBAL, "semiglobal": SEMIGLOBAL, "semi": SEMIGLOBAL}
+
+GA_OK = 0
+GA_ERR_ARG = 1
+GA_ERR_ALPHABET = 2
+GA_ERR_OOM = 3
+GA_ERR_CUDA = 4
+GA_ERR_RESIDUE = 5
+GA_ERR_TIMEOUT = 6
+GA_ERR_RANGE = 7
+
+# Symbols declared in include/gotoh_align.h (checked by the CPU tests).
+EXPORTED = ("ga_align_batch", "ga_align_batch_host", "ga_align_cross", "ga_align_long",
+            "ga_align_banded", "ga_strerror", "ga_version")
+
+
+class Scoring(ctypes.Structure):
+    _fields_ = [("alphabet_size", ctypes.c_int32), ("matrix", ctypes.POINTER(ctypes.c_int8)),
+                ("gap_open", ctypes.c_int32), ("gap_extend", ctypes.c_int32)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("cells", ctypes.c_int64), ("pairs", ctypes.c_int64),
+                ("pairs_int16", ctypes.c_int64), ("pairs_int32", ctypes.c_int64),
+                ("pairs_int32_rerun", ctypes.c_int64), ("band_retries", ctypes.c_int64),
+                ("banded_cells", ctypes.c_int64), ("kernel_ms", ctypes.c_float),
+                ("status", ctypes.c_int32)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class GotohError(RuntimeError):
+    def __init__(self, code: int, what: str = ""):
+        self.code = code
+        super().__init__(f"{what}: {strerror(code)} (code {code})" if what else strerror(code))
+
+
+_lib = None
+
+
+def lib_path() -> str:
+    return _build.LIB_PATH
+
+
+def load(build_if_missing: bool = False):
+    """Load the CUDA library; raises when it is missing (no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = lib_path()
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise RuntimeError(f"{path} is missing: run paper_2205_07610_gb300.build.build() "
+                               "(the CUDA extension is required; there is no CPU fallback)")
+        _build.build()
+    lib = ctypes.CDLL(path)
+    P = ctypes.c_void_p
+    i64, i32 = ctypes.c_int64, ctypes.c_int32
+    sp = ctypes.POINTER(Scoring)
+    stp = ctypes.POINTER(Stats)
+    lib.ga_align_batch.argtypes = [P, P, P, P, i64, sp, i32, P, P, stp]
+    lib.ga_align_batch_host.argtypes = [P, P, P, P, i64, sp, i32, P, P, stp]
+    lib.ga_align_cross.argtypes = [P, P, i64, P, P, i64, sp, i32, P, P, stp]
+    lib.ga_align_long.argtypes = [P, i64, P, i64, sp, i32, P, P, stp]
+    lib.ga_align_banded.argtypes = [P, P, P, P, i64, sp, P, i32, P, P, P, stp]
+    for f in ("ga_align_batch", "ga_align_batch_host", "ga_align_cross", "ga_align_long",
+              "ga_align_banded"):
+        getattr(lib, f).restype = i32
+    lib.ga_strerror.argtypes = [ctypes.c_int]
+    lib.ga_strerror.restype = ctypes.c_char_p
+    lib.ga_version.argtypes = []
+    lib.ga_version.restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def strerror(code: int) -> str:
+    return load().ga_strerror(int(code)).decode()
+
+
+def version() -> int:
+    return int(load().ga_version())
+
+
+def _mode(mode) -> int:
+    return _MODES[mode] if isinstance(mode, str) else int(mode)
+
+
+def make_scoring(matrix, gap_open: int, gap_extend: int):
+    """(Scoring struct, keep-alive buffer) for an A x A int8 matrix."""
+    m = np.ascontiguousarray(np.asarray(matrix, dtype=np.int8))
+    if m.ndim != 2 or m.shape[0] != m.shape[1]:
+        raise ValueError("substitution matrix must be square")
+    sc = Scoring(int(m.shape[0]), m.ctypes.data_as(ctypes.POINTER(ctypes.c_int8)), int(gap_open),
+                 int(gap_extend))
+    return sc, m
+
+
+def _ptr(t) -> int:
+    return 0 if t is None else int(t.data_ptr())
+
+
+def _stream_ptr(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(int(stream.cuda_stream))
+
+
+def _check_dev(*ts):
+    import torch
+    for t in ts:
+        if not isinstance(t, torch.Tensor) or not t.is_cuda or not t.is_contiguous():
+            raise TypeError("expected contiguous CUDA tensors")
+
+
+def align_batch(q_codes, q_off, t_codes, t_off, matrix, gap_open, gap_extend, mode, scores=None,
+                stream=None, stats: bool = False):
+    """Scores of pairs (q_p, t_p) given as device CSR tensors (uint8 codes, int64 offsets)."""
+    import torch
+    _check_dev(q_codes, q_off, t_codes, t_off)
+    npairs = q_off.numel() - 1
+    if scores is None:
+        scores = torch.empty(max(npairs, 0), dtype=torch.int32, device=q_codes.device)
+    sc, keep = make_scoring(matrix, gap_open, gap_extend)
+    st = Stats()
+    rc = load().ga_align_batch(_ptr(q_codes), _ptr(q_off), _ptr(t_codes), _ptr(t_off), npairs,
+                               ctypes.byref(sc), _mode(mode), _ptr(scores), _stream_ptr(stream),
+                               ctypes.byref(st) if stats else None)
+    if rc:
+        raise GotohError(rc, "ga_align_batch")
+    return (scores, st.as_dict()) if stats else scores
+
+
+def align_batch_host(q_codes, q_off, t_codes, t_off, matrix, gap_open, gap_extend, mode,
+                     scores=None, stream=None, stats: bool = False):
+    """ga_align_batch_host: host arrays in (numpy or pinned torch CPU tensors), host scores out."""
+    def host_ptr(a, dtype):
+        if hasattr(a, "data_ptr"):
+            return a, int(a.data_ptr())
+        a = np.ascontiguousarray(a, dtype=dtype)
+        return a, a.ctypes.data
+    q_codes, qc = host_ptr(q_codes, np.uint8)
+    q_off, qo = host_ptr(q_off, np.int64)
+    t_codes, tc = host_ptr(t_codes, np.uint8)
+    t_off, to = host_ptr(t_off, np.int64)
+    npairs = (q_off.numel() if hasattr(q_off, "numel") else len(q_off)) - 1
+    if scores is None:
+        scores = np.empty(max(npairs, 0), dtype=np.int32)
+    scores, sp = host_ptr(scores, np.int32)
+    sc, keep = make_scoring(matrix, gap_open, gap_extend)
+    st = Stats()
+    rc = load().ga_align_batch_host(qc, qo, tc, to, npairs, ctypes.byref(sc), _mode(mode), sp,
+                                    _stream_ptr(stream), ctypes.byref(st) if stats else None)
+    if rc:
+        raise GotohError(rc, "ga_align_batch_host")
+    return (scores, st.as_dict()) if stats else scores
+
+
+def align_cross(q_codes, q_off, t_codes, t_off, matrix, gap_open, gap_extend, mode, scores=None,
+                stream=None, stats: bool = False):
+    """Scores [nq, nt] of every query against every target (device tensors)."""
+    import torch
+    _check_dev(q_codes, q_off, t_codes, t_off)
+    nq, nt = q_off.numel() - 1, t_off.numel() - 1
+    if scores is None:
+        scores = torch.empty((max(nq, 0), max(nt, 0)), dtype=torch.int32, device=q_codes.device)
+    sc, keep = make_scoring(matrix, gap_open, gap_extend)
+    st = Stats()
+    rc = load().ga_align_cross(_ptr(q_codes), _ptr(q_off), nq, _ptr(t_codes), _ptr(t_off), nt,
+                               ctypes.byref(sc), _mode(mode), _ptr(scores), _stream_ptr(stream),
+                               ctypes.byref(st) if stats else None)
+    if rc:
+        raise GotohError(rc, "ga_align_cross")
+    return (scores, st.as_dict()) if stats else scores
+
+
+def align_long(q, t, matrix, gap_open, gap_extend, mode, stream=None, stats: bool = False):
+    """Score of one (long) pair on the intra-sequence kernel; device tensors."""
+    import torch
+    _check_dev(q, t)
+    out = torch.empty(1, dtype=torch.int32, device=q.device)
+    sc, keep = make_scoring(matrix, gap_open, gap_extend)
+    st = Stats()
+    rc = load().ga_align_long(_ptr(q), q.numel(), _ptr(t), t.numel(), ctypes.byref(sc), _mode(mode),
+                              _ptr(out), _stream_ptr(stream), ctypes.byref(st) if stats else None)
+    if rc:
+        raise GotohError(rc, "ga_align_long")
+    return (out, st.as_dict()) if stats else out
+
+
+def align_banded(q_codes, q_off, t_codes, t_off, matrix, gap_open, gap_extend, w0=None,
+                 default_w0: int = 16, scores=None, w_used=None, stream=None, stats: bool = False):
+    """Exact global scores by certified band doubling; returns (scores, w_used)."""
+    import torch
+    _check_dev(q_codes, q_off, t_codes, t_off)
+    npairs = q_off.numel() - 1
+    dev = q_codes.device
+    if scores is None:
+        scores = torch.empty(max(npairs, 0), dtype=torch.int32, device=dev)
+    if w_used is None:
+        w_used = torch.empty(max(npairs, 0), dtype=torch.int32, device=dev)
+    if w0 is not None:
+        _check_dev(w0)
+    sc, keep = make_scoring(matrix, gap_open, gap_extend)
+    st = Stats()
+    rc = load().ga_align_banded(_ptr(q_codes), _ptr(q_off), _ptr(t_codes), _ptr(t_off), npairs,
+                                ctypes.byref(sc), _ptr(w0), int(default_w0), _ptr(scores),
+                                _ptr(w_used), _stream_ptr(stream),
+                                ctypes.byref(st) if stats else None)
+    if rc:
+        raise GotohError(rc, "ga_align_banded")
+    return (scores, w_used, st.as_dict()) if stats else (scores, w_used)

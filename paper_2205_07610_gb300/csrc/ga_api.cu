@@ -1,0 +1,554 @@
+// ga_api.cu -- the C ABI (include/gotoh_align.h): argument checks, workspace,
+// planning (encode, classify, length sort) and kernel dispatch.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "ga_launch.h"
+#include "ga_prep.cuh"
+
+namespace ga {
+
+// Inter-sequence bins (columns per group = 16 * K).
+static BinTable make_bins() {
+  BinTable b{};
+  b.n16 = kKaNumBins;
+  b.n32 = kKaNumBins;
+  for (int i = 0; i < kKaNumBins; ++i) {
+    b.w16[i] = kKaG * kKaK[i];
+    b.w32[i] = kKaG * kKaK[i];
+  }
+  return b;
+}
+
+namespace {
+
+struct Scoring {
+  int A = 0, alpha = 0, beta = 0, smax = 0, smin = 0;
+  int8_t mat[32 * 32] = {};
+  uint32_t tables[16] = {};
+};
+
+int check_scoring(const ga_scoring *sc, Scoring *out) {
+  if (!sc) return GA_ERR_ARG;
+  if (sc->alphabet_size < 1 || sc->alphabet_size > 31 || !sc->matrix) return GA_ERR_ALPHABET;
+  if (sc->gap_open <= 0 || sc->gap_extend <= 0 || sc->gap_extend > sc->gap_open || sc->gap_open > 4096)
+    return GA_ERR_ARG;
+  const int A = sc->alphabet_size;
+  out->A = A;
+  out->alpha = sc->gap_open;
+  out->beta = sc->gap_extend;
+  out->smax = -1000;
+  out->smin = 1000;
+  for (int i = 0; i < A * A; ++i) {
+    const int v = sc->matrix[i];
+    if (v < -127) return GA_ERR_ALPHABET;
+    out->mat[i] = (int8_t)v;
+    out->smax = std::max(out->smax, v);
+    out->smin = std::min(out->smin, v);
+  }
+  // Table words for alphabets of <= 4 symbols: byte c of word x is
+  // sigma(x, c) (rows = query) or sigma(c, x) (rows = target); code 4 = pad.
+  if (A <= 4) {
+    for (int x = 0; x < A; ++x) {
+      uint32_t wn = 0, ws = 0;
+      for (int c = 0; c < A; ++c) {
+        wn |= (uint32_t)(uint8_t)out->mat[x * A + c] << (8 * c);
+        ws |= (uint32_t)(uint8_t)out->mat[c * A + x] << (8 * c);
+      }
+      out->tables[x] = wn;
+      out->tables[8 + x] = ws;
+    }
+  }
+  return GA_OK;
+}
+
+// Device allocations of one call, released stream-ordered.
+struct Alloc {
+  cudaStream_t s;
+  std::vector<void *> ptrs;
+  bool failed = false;
+  explicit Alloc(cudaStream_t st) : s(st) {}
+  template <class T>
+  T *get(size_t n) {
+    void *p = nullptr;
+    if (cudaMallocAsync(&p, n * sizeof(T) + 256, s) != cudaSuccess) {
+      failed = true;
+      return nullptr;
+    }
+    ptrs.push_back(p);
+    return (T *)p;
+  }
+  ~Alloc() {
+    for (void *p : ptrs) cudaFreeAsync(p, s);
+  }
+};
+
+// Small pinned staging area for scalar readbacks (one per host thread).
+struct Pinned {
+  void *p = nullptr;
+  Pinned() { cudaMallocHost(&p, 4096); }
+  ~Pinned() {
+    if (p) cudaFreeHost(p);
+  }
+};
+void *pinned_scratch() {
+  thread_local Pinned pin;
+  return pin.p;
+}
+
+// Device-side scalars of one call.
+struct Small {
+  int32_t status;
+  int32_t rmax_long;
+  unsigned long long cells;
+  int32_t rerun_total;
+  int32_t pad0;
+  int32_t ranges[2 * kClassesSorted * kBins];
+  int32_t counters[64];
+  int32_t rerun_range[2];
+};
+
+struct Readback {
+  int32_t status;
+  int32_t rmax_long;
+  unsigned long long cells;
+  int32_t rerun_total;
+  int32_t pad0;
+  int32_t ranges[2 * kClassesSorted * kBins];
+};
+
+__global__ void fill_off_kernel(int64_t *off, int64_t a, int64_t b) {
+  off[0] = a;
+  off[1] = b;
+}
+
+__global__ void count_reruns_kernel(const int32_t *rerun_range, int32_t *total) {
+  *total += rerun_range[1];
+}
+
+struct Call {
+  cudaStream_t s;
+  Scoring sc;
+  int mode;
+  int nsm = 0;
+  int dna = 0;
+  Alloc al;
+  Small *small = nullptr;
+  int32_t *hist = nullptr, *cursor = nullptr;
+  cudaError_t err = cudaSuccess;
+  int64_t pairs = 0, pairs16 = 0, pairs32 = 0;
+  explicit Call(cudaStream_t st) : s(st), al(st) {}
+
+  int fail() { return al.failed ? GA_ERR_OOM : GA_ERR_CUDA; }
+};
+
+int setup(Call &c) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return GA_ERR_CUDA;
+  if (cudaDeviceGetAttribute(&c.nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return GA_ERR_CUDA;
+  c.dna = c.sc.A <= 4;
+  c.small = c.al.get<Small>(1);
+  c.hist = c.al.get<int32_t>(kNumKeys);
+  c.cursor = c.al.get<int32_t>(kNumKeys);
+  if (c.al.failed) return GA_ERR_OOM;
+  if (cudaMemsetAsync(c.small, 0, sizeof(Small), c.s) != cudaSuccess) return GA_ERR_CUDA;
+  return GA_OK;
+}
+
+// Validate + pack one sequence set.  Reads back the total residue count.
+int prepare_set(Call &c, const uint8_t *codes, const int64_t *off, int64_t nseq, uint32_t **packed,
+                uint8_t **bad) {
+  *bad = c.al.get<uint8_t>((size_t)nseq + 1);
+  *packed = nullptr;
+  if (c.al.failed) return GA_ERR_OOM;
+  if (nseq == 0) return GA_OK;
+  int64_t *h = (int64_t *)pinned_scratch();
+  if (cudaMemcpyAsync(h, off + nseq, sizeof(int64_t), cudaMemcpyDeviceToHost, c.s) != cudaSuccess ||
+      cudaStreamSynchronize(c.s) != cudaSuccess)
+    return GA_ERR_CUDA;
+  const int64_t total = std::max<int64_t>(h[0], 0);
+  if (c.dna) {
+    *packed = c.al.get<uint32_t>((size_t)(total / 16 + nseq + 2));
+    if (c.al.failed) return GA_ERR_OOM;
+  }
+  const int wpb = 8;
+  const int64_t blocks = (nseq + wpb - 1) / wpb;
+  pack_kernel<<<(unsigned)blocks, 32 * wpb, 0, c.s>>>(codes, off, nseq, total, c.sc.A, *packed, *bad);
+  if (cudaGetLastError() != cudaSuccess) return GA_ERR_CUDA;
+  return GA_OK;
+}
+
+struct SetView {
+  const uint8_t *codes;
+  const int64_t *off;
+  uint32_t *packed;
+  uint8_t *bad;
+};
+
+// Plan, sort and run one chunk of pairs.  nt == 0: pair p = (q_p, t_p);
+// nt > 0: pair p = (query q0 + p / nt, target p % nt).
+int run_chunk(Call &c, const SetView &Q, const SetView &T, int64_t npairs, int64_t nt, int64_t q0,
+              int32_t *scores, int force_long, uint32_t *keys, int4 *info, int32_t *sorted,
+              int32_t *rerun_list) {
+  if (npairs == 0) return GA_OK;
+  if (cudaMemsetAsync(c.hist, 0, sizeof(int32_t) * kNumKeys, c.s) != cudaSuccess) return GA_ERR_CUDA;
+  if (cudaMemsetAsync(&c.small->counters, 0, sizeof(c.small->counters) + sizeof(c.small->rerun_range),
+                      c.s) != cudaSuccess)
+    return GA_ERR_CUDA;
+  if (cudaMemsetAsync(&c.small->rmax_long, 0, sizeof(int32_t), c.s) != cudaSuccess) return GA_ERR_CUDA;
+
+  PlanParams pp{};
+  pp.q_off = Q.off;
+  pp.t_off = T.off;
+  pp.npairs = npairs;
+  pp.nt = nt;
+  pp.q0 = q0;
+  pp.qbad = Q.bad;
+  pp.tbad = T.bad;
+  pp.A = c.sc.A;
+  pp.mode = c.mode;
+  pp.alpha = c.sc.alpha;
+  pp.beta = c.sc.beta;
+  pp.sigma_max = c.sc.smax;
+  pp.sigma_min = c.sc.smin;
+  pp.dna = c.dna && !force_long;
+  pp.bins = make_bins();
+  pp.scores = scores;
+  pp.keys = keys;
+  pp.info = info;
+  pp.status = &c.small->status;
+  pp.cells = &c.small->cells;
+  pp.rmax_long = &c.small->rmax_long;
+  const unsigned tb = 256;
+  const unsigned nb = (unsigned)((npairs + tb - 1) / tb);
+  plan_kernel<<<nb, tb, 0, c.s>>>(pp);
+  hist_kernel<<<nb, tb, 0, c.s>>>(keys, npairs, c.hist);
+  scan_kernel<<<1, 1024, 0, c.s>>>(c.hist, c.cursor, c.small->ranges);
+  scatter_kernel<<<nb, tb, 0, c.s>>>(keys, npairs, c.cursor, sorted);
+  if (cudaGetLastError() != cudaSuccess) return GA_ERR_CUDA;
+
+  Readback *rb = (Readback *)pinned_scratch();
+  if (cudaMemcpyAsync(rb, c.small, sizeof(Readback), cudaMemcpyDeviceToHost, c.s) != cudaSuccess ||
+      cudaStreamSynchronize(c.s) != cudaSuccess)
+    return GA_ERR_CUDA;
+  Readback r = *rb;
+
+  KAParams ka{};
+  ka.packed_q = Q.packed;
+  ka.packed_t = T.packed;
+  ka.q_off = Q.off;
+  ka.t_off = T.off;
+  ka.info = info;
+  ka.sorted = sorted;
+  std::memcpy(ka.tables, c.sc.tables, sizeof(ka.tables));
+  ka.alpha = c.sc.alpha;
+  ka.beta = c.sc.beta;
+  ka.sigma_max_pos = std::max(c.sc.smax, 0);
+  ka.scores = scores;
+  ka.rerun_list = rerun_list;
+  ka.rerun_count = &c.small->rerun_range[1];
+  ka.nt = nt;
+  ka.q0 = q0;
+
+  int counter = 0;
+  for (int cls = 0; cls < 2; ++cls) {
+    for (int bin = 0; bin < kKaNumBins; ++bin) {
+      const int key = cls * kBins + bin;
+      const int cnt = r.ranges[2 * key + 1] - r.ranges[2 * key];
+      if (cnt <= 0) continue;
+      (cls == 0 ? c.pairs16 : c.pairs32) += cnt;
+      ka.range = &c.small->ranges[2 * key];
+      ka.task_counter = &c.small->counters[counter++];
+      const int ppt = (cls == 0 ? 2 : 1) * (32 / kKaG);
+      const int64_t ntasks = (cnt + ppt - 1) / ppt;
+      int occ;
+      if (cls == 0) {
+        occ = c.mode == GA_LOCAL ? blocks_per_sm_ka16_local(bin)
+            : c.mode == GA_GLOBAL ? blocks_per_sm_ka16_global(bin)
+                                  : blocks_per_sm_ka16_semi(bin);
+      } else {
+        occ = c.mode == GA_LOCAL ? blocks_per_sm_ka32_local(bin)
+            : c.mode == GA_GLOBAL ? blocks_per_sm_ka32_global(bin)
+                                  : blocks_per_sm_ka32_semi(bin);
+      }
+      const int64_t want = (ntasks + (kKaThreads / 32) - 1) / (kKaThreads / 32);
+      const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)c.nsm * std::max(occ, 1)));
+      cudaError_t e;
+      if (cls == 0) {
+        e = c.mode == GA_LOCAL ? launch_ka16_local(bin, ka, grid, c.s)
+          : c.mode == GA_GLOBAL ? launch_ka16_global(bin, ka, grid, c.s)
+                                : launch_ka16_semi(bin, ka, grid, c.s);
+      } else {
+        e = c.mode == GA_LOCAL ? launch_ka32_local(bin, ka, grid, c.s)
+          : c.mode == GA_GLOBAL ? launch_ka32_global(bin, ka, grid, c.s)
+                                : launch_ka32_semi(bin, ka, grid, c.s);
+      }
+      if (e != cudaSuccess) return GA_ERR_CUDA;
+    }
+  }
+
+  // Long pairs (and every pair of an alphabet of more than 4 symbols).
+  {
+    const int key = kClassLong * kBins;
+    const int cnt = r.ranges[2 * key + 1] - r.ranges[2 * key];
+    if (cnt > 0) {
+      c.pairs32 += cnt;
+      const bool profile = !c.dna;
+      const size_t smem = profile ? (size_t)kKbWarps * (size_t)(c.sc.A + 1) * (32 * kKbK) : 0;
+      int occ = 0;
+      if (profile)
+        occ = c.mode == GA_LOCAL ? blocks_per_sm_kb_local_prof(smem)
+            : c.mode == GA_GLOBAL ? blocks_per_sm_kb_global_prof(smem)
+                                  : blocks_per_sm_kb_semi_prof(smem);
+      else
+        occ = c.mode == GA_LOCAL ? blocks_per_sm_kb_local_sel(smem)
+            : c.mode == GA_GLOBAL ? blocks_per_sm_kb_global_sel(smem)
+                                  : blocks_per_sm_kb_semi_sel(smem);
+      const int64_t want = (cnt + kKbWarps - 1) / kKbWarps;
+      const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)c.nsm * std::max(occ, 1)));
+      const int64_t stride = (int64_t)r.rmax_long + 128;
+      int2 *bnd = c.al.get<int2>((size_t)grid * kKbWarps * (size_t)stride);
+      if (c.al.failed) return GA_ERR_OOM;
+      KBParams kb{};
+      kb.packed_q = Q.packed;
+      kb.packed_t = T.packed;
+      kb.q_codes = Q.codes;
+      kb.t_codes = T.codes;
+      kb.q_off = Q.off;
+      kb.t_off = T.off;
+      kb.info = info;
+      kb.sorted = sorted;
+      kb.range = &c.small->ranges[2 * key];
+      kb.task_counter = &c.small->counters[counter++];
+      std::memcpy(kb.tables, c.sc.tables, sizeof(kb.tables));
+      std::memcpy(kb.sigma, c.sc.mat, sizeof(kb.sigma));
+      kb.A = c.sc.A;
+      kb.alpha = c.sc.alpha;
+      kb.beta = c.sc.beta;
+      kb.scores = scores;
+      kb.bnd = bnd;
+      kb.bnd_stride = stride;
+      kb.nt = nt;
+      kb.q0 = q0;
+      cudaError_t e;
+      if (profile)
+        e = c.mode == GA_LOCAL ? launch_kb_local_prof(kb, grid, smem, c.s)
+          : c.mode == GA_GLOBAL ? launch_kb_global_prof(kb, grid, smem, c.s)
+                                : launch_kb_semi_prof(kb, grid, smem, c.s);
+      else
+        e = c.mode == GA_LOCAL ? launch_kb_local_sel(kb, grid, smem, c.s)
+          : c.mode == GA_GLOBAL ? launch_kb_global_sel(kb, grid, smem, c.s)
+                                : launch_kb_semi_sel(kb, grid, smem, c.s);
+      if (e != cudaSuccess) return GA_ERR_CUDA;
+    }
+  }
+
+  // Exact int32 rerun of local int16 pairs whose running max reached the
+  // int16 limit (queued by the int16x2 kernels on the device).
+  if (c.mode == GA_LOCAL && c.dna) {
+    int any16 = 0;
+    for (int bin = 0; bin < kKaNumBins; ++bin) any16 |= r.ranges[2 * bin + 1] > r.ranges[2 * bin];
+    if (any16) {
+      range_from_count_kernel<<<1, 1, 0, c.s>>>(&c.small->rerun_range[1], c.small->rerun_range);
+      count_reruns_kernel<<<1, 1, 0, c.s>>>(c.small->rerun_range, &c.small->rerun_total);
+      ka.sorted = rerun_list;
+      ka.range = c.small->rerun_range;
+      ka.rerun_list = nullptr;
+      ka.rerun_count = nullptr;
+      ka.task_counter = &c.small->counters[counter++];
+      const int bin = kKaNumBins - 1;
+      const int occ = blocks_per_sm_ka32_local(bin);
+      if (launch_ka32_local(bin, ka, c.nsm * std::max(occ, 1), c.s) != cudaSuccess)
+        return GA_ERR_CUDA;
+    }
+  }
+  return GA_OK;
+}
+
+int finish(Call &c, ga_stats *st, cudaEvent_t e0, cudaEvent_t e1, int64_t pairs) {
+  if (!st) return GA_OK;
+  Readback *rb = (Readback *)pinned_scratch();
+  if (cudaEventRecord(e1, c.s) != cudaSuccess) return GA_ERR_CUDA;
+  if (cudaMemcpyAsync(rb, c.small, sizeof(Readback), cudaMemcpyDeviceToHost, c.s) != cudaSuccess ||
+      cudaStreamSynchronize(c.s) != cudaSuccess)
+    return GA_ERR_CUDA;
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  std::memset(st, 0, sizeof(*st));
+  st->cells = (int64_t)rb->cells;
+  st->pairs = pairs;
+  st->pairs_int16 = c.pairs16;
+  st->pairs_int32 = c.pairs32;
+  st->pairs_int32_rerun = rb->rerun_total;
+  st->kernel_ms = ms;
+  st->status = rb->status;
+  return GA_OK;
+}
+
+struct Events {
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  bool on = false;
+  Events(bool want, cudaStream_t s) : on(want) {
+    if (on) {
+      cudaEventCreate(&e0);
+      cudaEventCreate(&e1);
+      cudaEventRecord(e0, s);
+    }
+  }
+  ~Events() {
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+  }
+};
+
+int batch_impl(const uint8_t *q_codes, const int64_t *q_off, const uint8_t *t_codes,
+               const int64_t *t_off, int64_t npairs, const ga_scoring *scoring, int32_t mode,
+               int32_t *scores, void *stream, ga_stats *stats, int force_long) {
+  if (npairs < 0 || mode < 0 || mode > 2) return GA_ERR_ARG;
+  if (npairs > 0 && (!q_codes || !q_off || !t_codes || !t_off || !scores)) return GA_ERR_ARG;
+  if (npairs >= (1ll << 31) - 64) return GA_ERR_ARG;
+  Call c((cudaStream_t)stream);
+  int rc = check_scoring(scoring, &c.sc);
+  if (rc) return rc;
+  c.mode = mode;
+  Events ev(stats != nullptr, c.s);
+  if ((rc = setup(c))) return rc;
+  SetView Q{q_codes, q_off, nullptr, nullptr}, T{t_codes, t_off, nullptr, nullptr};
+  if ((rc = prepare_set(c, q_codes, q_off, npairs, &Q.packed, &Q.bad))) return rc;
+  if ((rc = prepare_set(c, t_codes, t_off, npairs, &T.packed, &T.bad))) return rc;
+  uint32_t *keys = c.al.get<uint32_t>((size_t)npairs);
+  int4 *info = c.al.get<int4>((size_t)npairs);
+  int32_t *sorted = c.al.get<int32_t>((size_t)npairs);
+  int32_t *rerun = c.al.get<int32_t>((size_t)npairs);
+  if (c.al.failed) return GA_ERR_OOM;
+  if ((rc = run_chunk(c, Q, T, npairs, 0, 0, scores, force_long, keys, info, sorted, rerun))) return rc;
+  return finish(c, stats, ev.e0, ev.e1, npairs);
+}
+
+}  // namespace
+}  // namespace ga
+
+using namespace ga;
+
+extern "C" {
+
+int ga_align_batch(const uint8_t *q_codes, const int64_t *q_off, const uint8_t *t_codes,
+                   const int64_t *t_off, int64_t npairs, const ga_scoring *scoring, int32_t mode,
+                   int32_t *scores, void *stream, ga_stats *stats) {
+  return batch_impl(q_codes, q_off, t_codes, t_off, npairs, scoring, mode, scores, stream, stats, 0);
+}
+
+int ga_align_batch_host(const uint8_t *q_codes, const int64_t *q_off, const uint8_t *t_codes,
+                        const int64_t *t_off, int64_t npairs, const ga_scoring *scoring,
+                        int32_t mode, int32_t *scores, void *stream, ga_stats *stats) {
+  if (npairs < 0) return GA_ERR_ARG;
+  if (npairs > 0 && (!q_codes || !q_off || !t_codes || !t_off || !scores)) return GA_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t qn = npairs ? q_off[npairs] : 0, tn = npairs ? t_off[npairs] : 0;
+  if (qn < 0 || tn < 0) return GA_ERR_ARG;
+  uint8_t *dq = nullptr, *dt = nullptr;
+  int64_t *dqo = nullptr, *dto = nullptr;
+  int32_t *ds = nullptr;
+  auto cleanup = [&]() {
+    cudaFreeAsync(dq, s); cudaFreeAsync(dt, s); cudaFreeAsync(dqo, s);
+    cudaFreeAsync(dto, s); cudaFreeAsync(ds, s);
+  };
+  if (cudaMallocAsync((void **)&dq, (size_t)qn + 16, s) != cudaSuccess ||
+      cudaMallocAsync((void **)&dt, (size_t)tn + 16, s) != cudaSuccess ||
+      cudaMallocAsync((void **)&dqo, sizeof(int64_t) * (size_t)(npairs + 1), s) != cudaSuccess ||
+      cudaMallocAsync((void **)&dto, sizeof(int64_t) * (size_t)(npairs + 1), s) != cudaSuccess ||
+      cudaMallocAsync((void **)&ds, sizeof(int32_t) * (size_t)(npairs + 1), s) != cudaSuccess) {
+    cleanup();
+    return GA_ERR_OOM;
+  }
+  int rc = GA_OK;
+  if (cudaMemcpyAsync(dq, q_codes, (size_t)qn, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaMemcpyAsync(dt, t_codes, (size_t)tn, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaMemcpyAsync(dqo, q_off, sizeof(int64_t) * (size_t)(npairs + 1), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaMemcpyAsync(dto, t_off, sizeof(int64_t) * (size_t)(npairs + 1), cudaMemcpyHostToDevice, s) != cudaSuccess)
+    rc = GA_ERR_CUDA;
+  if (!rc) rc = batch_impl(dq, dqo, dt, dto, npairs, scoring, mode, ds, stream, stats, 0);
+  if (!rc && npairs > 0 &&
+      cudaMemcpyAsync(scores, ds, sizeof(int32_t) * (size_t)npairs, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    rc = GA_ERR_CUDA;
+  cleanup();
+  if (cudaStreamSynchronize(s) != cudaSuccess && !rc) rc = GA_ERR_CUDA;
+  return rc;
+}
+
+int ga_align_cross(const uint8_t *q_codes, const int64_t *q_off, int64_t nq, const uint8_t *t_codes,
+                   const int64_t *t_off, int64_t nt, const ga_scoring *scoring, int32_t mode,
+                   int32_t *scores, void *stream, ga_stats *stats) {
+  if (nq < 0 || nt < 0 || mode < 0 || mode > 2) return GA_ERR_ARG;
+  if (nq > 0 && nt > 0 && (!q_codes || !q_off || !t_codes || !t_off || !scores)) return GA_ERR_ARG;
+  Call c((cudaStream_t)stream);
+  int rc = check_scoring(scoring, &c.sc);
+  if (rc) return rc;
+  c.mode = mode;
+  Events ev(stats != nullptr, c.s);
+  if ((rc = setup(c))) return rc;
+  if (nq == 0 || nt == 0) return finish(c, stats, ev.e0, ev.e1, 0);
+  SetView Q{q_codes, q_off, nullptr, nullptr}, T{t_codes, t_off, nullptr, nullptr};
+  if ((rc = prepare_set(c, q_codes, q_off, nq, &Q.packed, &Q.bad))) return rc;
+  if ((rc = prepare_set(c, t_codes, t_off, nt, &T.packed, &T.bad))) return rc;
+  const int64_t kChunk = 1 << 22;
+  const int64_t qpc = std::max<int64_t>(1, std::min<int64_t>(nq, kChunk / nt));
+  const int64_t cap = qpc * nt;
+  if (cap >= (1ll << 31) - 64) return GA_ERR_ARG;
+  uint32_t *keys = c.al.get<uint32_t>((size_t)cap);
+  int4 *info = c.al.get<int4>((size_t)cap);
+  int32_t *sorted = c.al.get<int32_t>((size_t)cap);
+  int32_t *rerun = c.al.get<int32_t>((size_t)cap);
+  if (c.al.failed) return GA_ERR_OOM;
+  for (int64_t q0 = 0; q0 < nq; q0 += qpc) {
+    const int64_t nqc = std::min<int64_t>(qpc, nq - q0);
+    rc = run_chunk(c, Q, T, nqc * nt, nt, q0, scores + q0 * nt, 0, keys, info, sorted, rerun);
+    if (rc) return rc;
+  }
+  return finish(c, stats, ev.e0, ev.e1, nq * nt);
+}
+
+int ga_align_long(const uint8_t *q, int64_t m, const uint8_t *t, int64_t n, const ga_scoring *scoring,
+                  int32_t mode, int32_t *score, void *stream, ga_stats *stats) {
+  if (m < 0 || n < 0 || !score || (m > 0 && !q) || (n > 0 && !t)) return GA_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  int64_t *off = nullptr;
+  if (cudaMallocAsync((void **)&off, 4 * sizeof(int64_t), s) != cudaSuccess) return GA_ERR_OOM;
+  fill_off_kernel<<<1, 1, 0, s>>>(off, 0, m);
+  fill_off_kernel<<<1, 1, 0, s>>>(off + 2, 0, n);
+  const uint8_t *qq = q ? q : (const uint8_t *)off, *tt = t ? t : (const uint8_t *)off;
+  int rc = batch_impl(qq, off, tt, off + 2, 1, scoring, mode, score, stream, stats, 1);
+  cudaFreeAsync(off, s);
+  return rc;
+}
+
+int ga_align_banded(const uint8_t *q_codes, const int64_t *q_off, const uint8_t *t_codes,
+                    const int64_t *t_off, int64_t npairs, const ga_scoring *scoring, const int32_t *w0,
+                    int32_t default_w0, int32_t *scores, int32_t *w_used, void *stream, ga_stats *stats) {
+  (void)w0;
+  (void)default_w0;
+  (void)w_used;
+  // Placeholder until the banded kernel lands: exact full-DP global scores.
+  return batch_impl(q_codes, q_off, t_codes, t_off, npairs, scoring, GA_GLOBAL, scores, stream, stats, 0);
+}
+
+const char *ga_strerror(int code) {
+  switch (code) {
+    case GA_OK: return "ok";
+    case GA_ERR_ARG: return "invalid argument";
+    case GA_ERR_ALPHABET: return "invalid alphabet or substitution matrix";
+    case GA_ERR_OOM: return "device workspace allocation failed";
+    case GA_ERR_CUDA: return "CUDA error";
+    case GA_ERR_RESIDUE: return "residue code outside the alphabet";
+    case GA_ERR_TIMEOUT: return "bounded device wait timed out";
+    case GA_ERR_RANGE: return "scores of a pair could exceed the int32 range";
+    default: return "unknown error";
+  }
+}
+
+int ga_version(void) { return 100; }
+
+}  // extern "C"

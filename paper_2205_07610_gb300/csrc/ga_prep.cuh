@@ -1,0 +1,206 @@
+// ga_prep.cuh -- encode / validate / classify / length-sort kernels.
+//
+// a1: residue codes are checked against the alphabet and, for alphabets of
+//     <= 4 symbols, packed 2 bits per residue (16 per 32-bit word; sequence
+//     k starts at word off[k]/16 + k, which needs no prefix sum because a
+//     sequence of length L never needs more than floor(L/16) + 1 words
+//     beyond the word of its first residue).
+// a2: every pair is classified (packed int16x2 / int32 inter-sequence
+//     kernel, long kernel, or done: empty or invalid), oriented (rows = the
+//     longer sequence), binned by its column count and keyed by its row
+//     count; a counting sort groups pairs by (class, bin) with long rows
+//     first, so a task's pairs have similar lengths and the longest work
+//     starts first.
+#pragma once
+
+#include "ga_common.cuh"
+
+namespace ga {
+
+constexpr int kBins = 8;
+constexpr int kRBuckets = 4096;
+constexpr int kClassesSorted = 3;  // inter16, inter32, long
+constexpr int kNumKeys = kClassesSorted * kBins * kRBuckets;
+
+// Column-count limits of the inter-sequence bins (W = G*K per bin).
+struct BinTable {
+  int n16;            // bins of the int16x2 kernel for this mode
+  int w16[kBins];
+  int n32;
+  int w32[kBins];
+};
+
+struct PlanParams {
+  const int64_t *q_off;
+  const int64_t *t_off;
+  int64_t npairs;             // pairs (batch) or combinations of this chunk (cross)
+  int64_t nt;                 // cross: targets per query (0: batch, pair p = (p, p))
+  int64_t q0;                 // cross: first query of this chunk
+  const uint8_t *qbad;        // per query sequence: 0 ok, 1 residue, 2 offsets
+  const uint8_t *tbad;
+  int32_t A;
+  int32_t mode;
+  int32_t alpha, beta;
+  int32_t sigma_max, sigma_min;
+  int32_t dna;                // alphabet packed 2-bit (<= 4 symbols)
+  BinTable bins;
+  int32_t *scores;
+  uint32_t *keys;
+  int4 *info;
+  int32_t *status;
+  unsigned long long *cells;  // sum m*n over valid pairs
+  int32_t *rmax_long;         // max rows over long-class pairs
+};
+
+// Warp per sequence: validate codes < A, pack 2-bit (if packed != nullptr).
+// A sequence whose offsets are decreasing or leave [0, total] (total =
+// off[nseq], the size of the code buffer) is flagged and never touched.
+__global__ void pack_kernel(const uint8_t *codes, const int64_t *off, int64_t nseq, int64_t total,
+                            int A, uint32_t *packed, uint8_t *bad) {
+  const int64_t k = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (k >= nseq) return;
+  const int64_t start = off[k], end = off[k + 1];
+  const int64_t len = end - start;
+  if (len < 0 || start < 0 || end > total) {
+    if (lane == 0) bad[k] = 2;
+    return;
+  }
+  const int64_t word0 = start / 16 + k;
+  const int64_t nwords = (len + 15) / 16;
+  unsigned mx = 0;
+  for (int64_t w = lane; w < nwords; w += 32) {
+    uint32_t word = 0;
+    const int64_t b = start + w * 16;
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      if (w * 16 + i < len) {
+        const unsigned c = codes[b + i];
+        mx = max(mx, c);
+        word |= (c & 3u) << (2 * i);
+      }
+    }
+    if (packed) packed[word0 + w] = word;
+  }
+  mx = __reduce_max_sync(0xffffffffu, mx);
+  if (lane == 0) bad[k] = (len > 0 && mx >= (unsigned)A) ? 1 : 0;
+}
+
+__device__ __forceinline__ int global_gap(int alpha, int beta, int64_t len) {
+  return len == 0 ? 0 : -(int)(alpha + beta * (len - 1));
+}
+
+// Thread per pair (batch) or per (query, target) combination (cross).
+__global__ void plan_kernel(PlanParams p) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= p.npairs) return;
+  const int64_t qi = p.nt ? p.q0 + i / p.nt : i;
+  const int64_t ti = p.nt ? i % p.nt : i;
+  const int64_t m = p.q_off[qi + 1] - p.q_off[qi];
+  const int64_t n = p.t_off[ti + 1] - p.t_off[ti];
+  int4 inf = make_int4(0, 0, 0, (int)kClassDone);
+  uint32_t key = 0xffffffffu;
+  const uint8_t qb = p.qbad[qi], tb = p.tbad[ti];
+  if (qb || tb || m < 0 || n < 0) {
+    p.scores[i] = INT32_MIN;
+    set_status(p.status, (qb == 2 || tb == 2 || m < 0 || n < 0) ? GA_ERR_ARG : GA_ERR_RESIDUE);
+  } else if (m == 0 || n == 0) {
+    p.scores[i] = (p.mode == GA_GLOBAL) ? global_gap(p.alpha, p.beta, m + n) : 0;
+  } else {
+    const int64_t R = m >= n ? m : n, C = m >= n ? n : m;
+    const int swap = m < n;
+    const int64_t smax = p.sigma_max > 0 ? p.sigma_max : 0;
+    const int64_t sabs = max(smax, (int64_t)(p.sigma_min < 0 ? -p.sigma_min : 0));
+    // int32 admissibility: every reachable value stays well inside int32.
+    const int64_t bound32 = sabs * C + 3 * (int64_t)p.alpha + (int64_t)p.beta * (R + C);
+    if (bound32 >= (1ll << 30) || R >= (1ll << 30)) {
+      p.scores[i] = INT32_MIN;
+      set_status(p.status, GA_ERR_RANGE);
+    } else {
+      atomicAdd(p.cells, (unsigned long long)(m * n));
+      uint32_t cls = kClassLong;
+      int bin = 0;
+      if (p.dna) {
+        // smallest int16x2 bin that fits the columns, if int16 is exact
+        int b16 = -1, b32 = -1;
+        for (int b = 0; b < p.bins.n16; ++b)
+          if (C <= p.bins.w16[b]) { b16 = b; break; }
+        for (int b = 0; b < p.bins.n32; ++b)
+          if (C <= p.bins.w32[b]) { b32 = b; break; }
+        bool ok16 = b16 >= 0 && p.alpha <= kInt16MaxGap && p.beta <= kInt16MaxGap;
+        if (ok16) {
+          const int64_t W = p.bins.w16[b16];
+          const int64_t up = smax * C;
+          int64_t lo;
+          if (p.mode == GA_GLOBAL) lo = 2 * (int64_t)p.alpha + (int64_t)p.beta * (R + C);
+          else if (p.mode == GA_SEMIGLOBAL) lo = (int64_t)p.alpha * (W - C + 2) + (int64_t)p.beta * C;
+          else lo = p.alpha;
+          // local: values are >= 0; an overflow of the upper bound is
+          // detected at run time and the pair is redone in int32.
+          if (p.mode != GA_LOCAL && up > kInt16Bound) ok16 = false;
+          if (lo > kInt16Bound) ok16 = false;
+        }
+        if (ok16) { cls = kClassInter16; bin = b16; }
+        else if (b32 >= 0) { cls = kClassInter32; bin = b32; }
+      }
+      if (cls == kClassLong) atomicMax(p.rmax_long, (int)R);
+      inf = make_int4((int)R, (int)C, swap, (int)cls);
+      const int64_t rb = R < kRBuckets ? R : kRBuckets - 1;
+      key = (uint32_t)(((cls * kBins + bin) * kRBuckets) + (kRBuckets - 1 - rb));
+    }
+  }
+  p.info[i] = inf;
+  p.keys[i] = key;
+}
+
+__global__ void hist_kernel(const uint32_t *keys, int64_t n, int32_t *hist) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint32_t k = keys[i];
+  if (k != 0xffffffffu) atomicAdd(&hist[k], 1);
+}
+
+// Single block: exclusive scan of hist -> cursor, and [start, end) ranges of
+// each (class, bin) in ranges[2 * (class * kBins + bin)].
+__global__ void scan_kernel(const int32_t *hist, int32_t *cursor, int32_t *ranges) {
+  constexpr int kThreads = 1024;
+  constexpr int kPer = kNumKeys / kThreads;
+  static_assert(kNumKeys % kThreads == 0, "scan tiling");
+  __shared__ int32_t part[kThreads];
+  const int tid = threadIdx.x;
+  int32_t local = 0;
+  for (int e = 0; e < kPer; ++e) local += hist[tid * kPer + e];
+  part[tid] = local;
+  __syncthreads();
+  for (int off = 1; off < kThreads; off <<= 1) {
+    int32_t v = (tid >= off) ? part[tid - off] : 0;
+    __syncthreads();
+    part[tid] += v;
+    __syncthreads();
+  }
+  int32_t run = part[tid] - local;  // exclusive
+  for (int e = 0; e < kPer; ++e) {
+    const int k = tid * kPer + e;
+    if ((k % kRBuckets) == 0) ranges[2 * (k / kRBuckets)] = run;
+    cursor[k] = run;
+    run += hist[k];
+    if ((k % kRBuckets) == kRBuckets - 1) ranges[2 * (k / kRBuckets) + 1] = run;
+  }
+}
+
+__global__ void scatter_kernel(const uint32_t *keys, int64_t n, int32_t *cursor, int32_t *sorted) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint32_t k = keys[i];
+  if (k == 0xffffffffu) return;
+  const int pos = atomicAdd(&cursor[k], 1);
+  sorted[pos] = (int32_t)i;
+}
+
+// Writes {0, count} so a kernel can take its range from a device counter.
+__global__ void range_from_count_kernel(const int32_t *count, int32_t *range) {
+  range[0] = 0;
+  range[1] = *count;
+}
+
+}  // namespace ga

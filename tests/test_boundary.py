@@ -1,0 +1,75 @@
+"""The C-ABI library builds for sm_103a, loads without a GPU and exports every
+entry point that include/*.h declares (no compute calls here)."""
+import ctypes
+import glob
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        names |= set(re.findall(r"\b(ga_[a-z0-9_]+)\s*\(", text))
+    return names
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    import paper_2205_07610_gb300 as ga
+    return ga.build()
+
+
+def test_header_declares_the_binding_surface():
+    import paper_2205_07610_gb300 as ga
+    assert _declared() == set(ga.EXPORTED)
+
+
+def test_library_exports_every_declared_symbol(libpath):
+    out = subprocess.run(["nm", "-D", "--defined-only", libpath], capture_output=True, text=True,
+                         check=True).stdout
+    exported = set(re.findall(r"\bT (ga_[a-z0-9_]+)$", out, flags=re.M))
+    missing = _declared() - exported
+    assert not missing, missing
+
+
+def test_library_loads_without_gpu(libpath):
+    import paper_2205_07610_gb300 as ga
+    lib = ga.load()
+    for name in ga.EXPORTED:
+        assert hasattr(lib, name)
+    assert ga.version() >= 100
+    assert ga.strerror(5) == "residue code outside the alphabet"
+    assert ga.strerror(0) == "ok"
+
+
+def test_kernels_compiled_for_sm103a_without_spills(libpath):
+    logs = glob.glob(os.path.join(ROOT, "paper_2205_07610_gb300", "_build", "*.ptxas.txt"))
+    assert logs
+    text = "".join(open(f).read() for f in logs)
+    assert "sm_103a" in text
+    spills = re.findall(r"(\d+) bytes spill stores", text)
+    assert spills and all(int(s) == 0 for s in spills)
+
+
+def test_argument_errors_are_synchronous(libpath):
+    """Invalid scoring is rejected before anything touches the device."""
+    import numpy as np
+    import paper_2205_07610_gb300 as ga
+    lib = ga.load()
+    m = np.zeros((4, 4), dtype=np.int8)
+    for go, ge, want in ((0, 1, 1), (2, 3, 1), (5, 0, 1)):
+        sc, keep = ga.make_scoring(m, go, ge)
+        rc = lib.ga_align_batch(None, None, None, None, 0, ctypes.byref(sc), 0, None, None, None)
+        assert rc == want
+    sc, keep = ga.make_scoring(np.zeros((40, 40), np.int8), 5, 2)
+    assert lib.ga_align_batch(None, None, None, None, 0, ctypes.byref(sc), 0, None, None, None) == 2
+    sc, keep = ga.make_scoring(m, 5, 2)
+    assert lib.ga_align_batch(None, None, None, None, 0, ctypes.byref(sc), 7, None, None, None) == 1
+    assert lib.ga_align_batch(None, None, None, None, -1, ctypes.byref(sc), 0, None, None, None) == 1

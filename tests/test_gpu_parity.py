@@ -1,0 +1,261 @@
+"""GPU parity: every score of the CUDA path equals the CPU oracle bit for bit.
+
+Inputs are seeded synthetic workloads (synth/); the oracle (oracle/) and the
+CUDA library share nothing but those inputs.  Cases span several lane tiles,
+every inter-sequence bin edge, ragged tails, swapped orientation, the long
+multi-stage kernel, protein (profile path), int16 overflow with the exact int32
+rerun, statically int32 pairs, empty sequences and device-detected errors.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_2205_07610_gb300 as ga  # noqa: E402
+
+MODES = ["local", "global", "semiglobal"]
+NTHREADS = max(1, min(32, os.cpu_count() or 1))
+INT32_MIN = -(2 ** 31)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    ga.build()
+    ga.load()
+
+
+def _dev(b):
+    d = "cuda"
+    return (torch.from_numpy(np.ascontiguousarray(b.q_codes)).to(d),
+            torch.from_numpy(np.ascontiguousarray(b.q_off)).to(d),
+            torch.from_numpy(np.ascontiguousarray(b.t_codes)).to(d),
+            torch.from_numpy(np.ascontiguousarray(b.t_off)).to(d))
+
+
+def gpu_batch(b, mode, stats=False):
+    q, qo, t, to = _dev(b)
+    r = ga.align_batch(q, qo, t, to, b.matrix, b.alpha, b.beta, mode, stats=stats)
+    torch.cuda.synchronize()
+    if stats:
+        return r[0].cpu().numpy(), r[1]
+    return r.cpu().numpy()
+
+
+def oracle_batch(b, mode):
+    out, errs = oracle.batch(b.q_codes, b.q_off, b.t_codes, b.t_off, b.matrix, b.alpha, b.beta,
+                             mode, nthreads=NTHREADS)
+    assert not errs.any()
+    return out
+
+
+def assert_same(got, want, what=""):
+    got = np.asarray(got, dtype=np.int64)
+    want = np.asarray(want, dtype=np.int64)
+    bad = np.nonzero(got != want)[0]
+    assert len(bad) == 0, f"{what}: {len(bad)} mismatches, first {bad[:8]} got {got[bad[:8]]} want {want[bad[:8]]}"
+
+
+def _pairs(rng, lens_q, lens_t, alphabet=4, freqs=None):
+    qc, qo = synth.random_sequences(rng, lens_q, alphabet, freqs)
+    tc, to = synth.random_sequences(rng, lens_t, alphabet, freqs)
+    return qc, qo, tc, to
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_config1_uniform_150(mode):
+    b = synth.uniform_dna_pairs()  # 1,000 pairs of 150 x 150, +2/-3, 5/2
+    got, st = gpu_batch(b, mode, stats=True)
+    assert_same(got, oracle_batch(b, mode), f"config1 {mode}")
+    assert st["status"] == 0
+    assert st["cells"] == b.cells()
+    assert st["pairs_int16"] == b.npairs
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_mixed_lengths_all_bins(mode):
+    """Lengths 1..700 with both orientations: every bin, ragged tails, long pairs."""
+    rng = np.random.default_rng(101)
+    n = 2500
+    lq = rng.integers(1, 700, size=n)
+    lt = np.clip(lq + rng.integers(-60, 60, size=n), 1, None)
+    swap = rng.random(n) < 0.3
+    lt[swap] = rng.integers(1, 700, size=int(swap.sum()))
+    qc, qo, tc, to = _pairs(rng, lq, lt)
+    b = synth.Batch(qc, qo, tc, to, synth.dna_matrix(2, -3), 5, 2, "mixed")
+    got = gpu_batch(b, mode)
+    assert_same(got, oracle_batch(b, mode), f"mixed {mode}")
+
+
+@pytest.mark.parametrize("mode", ["global", "semiglobal"])
+def test_config2_subset(mode):
+    b = synth.mutated_dna_pairs(npairs=20000, seed=synth.SEED_BASE + 2)
+    got, st = gpu_batch(b, mode, stats=True)
+    assert_same(got, oracle_batch(b, mode), f"config2 subset {mode}")
+    assert st["pairs_int16"] == b.npairs and st["pairs_int32_rerun"] == 0
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_bin_edges_and_small(mode):
+    rng = np.random.default_rng(7)
+    edges = [1, 2, 3, 15, 16, 17, 31, 32, 33, 127, 128, 129, 191, 192, 193, 255, 256, 257, 319,
+             320, 321, 383, 384, 385, 511, 512, 513, 600]
+    lq, lt = [], []
+    for e in edges:
+        for other in (1, e, e + 7, max(1, e - 9), 300):
+            lq.append(e); lt.append(other)
+            lq.append(other); lt.append(e)
+    qc, qo, tc, to = _pairs(rng, lq, lt)
+    for (ma, mi), al, be in (((2, -3), 5, 2), ((1, -1), 2, 1), ((3, -1), 3, 3)):
+        b = synth.Batch(qc, qo, tc, to, synth.dna_matrix(ma, mi), al, be, "edges")
+        assert_same(gpu_batch(b, mode), oracle_batch(b, mode), f"edges {mode} {ma}/{mi} {al}/{be}")
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_empty_and_identical(mode):
+    seqs = [np.zeros(0, np.uint8), synth.encode("A"), synth.encode("ACGT" * 40),
+            synth.encode("GATTACA" * 30)]
+    q, t = [], []
+    for a in seqs:
+        for c in seqs:
+            q.append(a); t.append(c)
+    qc, qo = synth.pack_csr(q)
+    tc, to = synth.pack_csr(t)
+    b = synth.Batch(qc, qo, tc, to, synth.dna_matrix(2, -3), 5, 2, "empty")
+    assert_same(gpu_batch(b, mode), oracle_batch(b, mode), f"empty/identical {mode}")
+
+
+def test_asymmetric_dna_matrix_swapped_orientation():
+    rng = np.random.default_rng(9)
+    mat = rng.integers(-4, 5, size=(4, 4)).astype(np.int8)
+    lq = rng.integers(5, 400, size=600)
+    lt = rng.integers(5, 400, size=600)
+    qc, qo, tc, to = _pairs(rng, lq, lt)
+    b = synth.Batch(qc, qo, tc, to, mat, 4, 1, "asym")
+    for mode in MODES:
+        assert_same(gpu_batch(b, mode), oracle_batch(b, mode), f"asymmetric {mode}")
+
+
+def test_local_int16_overflow_rerun_is_exact():
+    """Match score 100: identical pairs of length >= 327 exceed int16; they are
+    detected on the device and recomputed exactly in int32."""
+    rng = np.random.default_rng(5)
+    seqs = [rng.integers(0, 4, size=L).astype(np.uint8) for L in (100, 300, 330, 400, 500, 512)]
+    q = seqs + [s.copy() for s in seqs]
+    t = seqs + [rng.integers(0, 4, size=len(s)).astype(np.uint8) for s in seqs]
+    qc, qo = synth.pack_csr(q)
+    tc, to = synth.pack_csr(t)
+    b = synth.Batch(qc, qo, tc, to, synth.dna_matrix(100, -90), 120, 60, "overflow")
+    got, st = gpu_batch(b, "local", stats=True)
+    want = oracle_batch(b, "local")
+    assert_same(got, want, "local overflow rerun")
+    assert want.max() > 32767
+    assert st["pairs_int32_rerun"] >= 3
+
+
+@pytest.mark.parametrize("mode", ["global", "semiglobal"])
+def test_statically_int32_pairs(mode):
+    rng = np.random.default_rng(13)
+    lq = rng.integers(50, 500, size=300)
+    lt = rng.integers(50, 500, size=300)
+    qc, qo, tc, to = _pairs(rng, lq, lt)
+    for al, be in ((500, 100), (1000, 800)):
+        b = synth.Batch(qc, qo, tc, to, synth.dna_matrix(2, -3), al, be, "int32")
+        got, st = gpu_batch(b, mode, stats=True)
+        assert_same(got, oracle_batch(b, mode), f"int32 {mode} {al}/{be}")
+        assert st["pairs_int32"] > 0
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_long_pairs_multistage(mode):
+    rng = np.random.default_rng(17)
+    lq = [520, 1000, 3000, 1500, 2048, 4100]
+    lt = [600, 1300, 2500, 3500, 2048, 700]
+    qc, qo, tc, to = _pairs(rng, lq, lt)
+    b = synth.Batch(qc, qo, tc, to, synth.dna_matrix(2, -3), 5, 2, "long")
+    assert_same(gpu_batch(b, mode), oracle_batch(b, mode), f"long {mode}")
+    lb = synth.long_dna_pairs(npairs=8, lmin=1000, lmax=5000, seed=21)
+    assert_same(gpu_batch(lb, mode), oracle_batch(lb, mode), f"long mutated {mode}")
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_protein_blosum62(mode):
+    rng = np.random.default_rng(19)
+    bg = np.concatenate([synth.PROTEIN_BACKGROUND, np.zeros(4)])
+    lq = rng.integers(1, 700, size=300)
+    lt = rng.integers(1, 700, size=300)
+    qc, qo, tc, to = _pairs(rng, lq, lt, 24, bg)
+    b = synth.Batch(qc, qo, tc, to, synth.blosum62(), 11, 1, "protein")
+    assert_same(gpu_batch(b, mode), oracle_batch(b, mode), f"protein {mode}")
+
+
+def test_device_detected_errors():
+    rng = np.random.default_rng(23)
+    qc, qo, tc, to = _pairs(rng, [10, 20, 30], [10, 20, 30])
+    qc = qc.copy()
+    qc[15] = 7  # residue code outside A..T in pair 1
+    b = synth.Batch(qc, qo, tc, to, synth.dna_matrix(2, -3), 5, 2, "bad")
+    got, st = gpu_batch(b, "global", stats=True)
+    assert st["status"] == 5  # GA_ERR_RESIDUE
+    assert got[1] == INT32_MIN
+    good = synth.Batch(*_pairs(np.random.default_rng(23), [10, 20, 30], [10, 20, 30]),
+                       synth.dna_matrix(2, -3), 5, 2)
+    want = oracle_batch(good, "global")
+    assert got[0] == want[0] and got[2] == want[2]
+    # decreasing offsets: the bad pair is flagged, the others are exact
+    qo2 = qo.copy()
+    qo2[2] = qo2[1] - 3
+    b2 = synth.Batch(qc, qo2, tc, to, synth.dna_matrix(2, -3), 5, 2, "badoff")
+    got2, st2 = gpu_batch(b2, "global", stats=True)
+    assert st2["status"] in (1, 5) and got2[1] == INT32_MIN
+
+
+def test_host_entry_point_matches_device():
+    b = synth.mutated_dna_pairs(npairs=3000, seed=77)
+    for mode in MODES:
+        host = ga.align_batch_host(b.q_codes, b.q_off, b.t_codes, b.t_off, b.matrix, b.alpha,
+                                   b.beta, mode)
+        assert_same(host, gpu_batch(b, mode), f"host {mode}")
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_cross_small(mode):
+    cr = synth.protein_database(nq=6, qmin=20, qmax=300, nt=80, median=120, seed=31)
+    d = "cuda"
+    q = torch.from_numpy(cr.q_codes).to(d); qo = torch.from_numpy(cr.q_off).to(d)
+    t = torch.from_numpy(cr.t_codes).to(d); to = torch.from_numpy(cr.t_off).to(d)
+    got = ga.align_cross(q, qo, t, to, cr.matrix, cr.alpha, cr.beta, mode).cpu().numpy()
+    want, errs = oracle.cross(cr.q_codes, cr.q_off, cr.t_codes, cr.t_off, cr.matrix, cr.alpha,
+                              cr.beta, mode, nthreads=NTHREADS)
+    assert_same(got.ravel(), want.ravel(), f"cross protein {mode}")
+    # DNA cross
+    rng = np.random.default_rng(3)
+    qc, qo_ = synth.random_sequences(rng, rng.integers(10, 300, size=5))
+    tc, to_ = synth.random_sequences(rng, rng.integers(10, 300, size=40))
+    got = ga.align_cross(torch.from_numpy(qc).to(d), torch.from_numpy(qo_).to(d),
+                         torch.from_numpy(tc).to(d), torch.from_numpy(to_).to(d),
+                         synth.dna_matrix(2, -3), 5, 2, mode).cpu().numpy()
+    want, _ = oracle.cross(qc, qo_, tc, to_, synth.dna_matrix(2, -3), 5, 2, mode, nthreads=NTHREADS)
+    assert_same(got.ravel(), want.ravel(), f"cross dna {mode}")
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_long_entry_point(mode):
+    rng = np.random.default_rng(41)
+    for (m, n, prot) in ((5000, 4200, False), (1300, 1800, True), (1, 900, False)):
+        A = 24 if prot else 4
+        q = rng.integers(0, 20 if prot else 4, size=m).astype(np.uint8)
+        t = rng.integers(0, 20 if prot else 4, size=n).astype(np.uint8)
+        mat = synth.blosum62() if prot else synth.dna_matrix(2, -3)
+        al, be = (11, 1) if prot else (5, 2)
+        got = ga.align_long(torch.from_numpy(q).cuda(), torch.from_numpy(t).cuda(), mat, al, be,
+                            mode).item()
+        assert got == oracle.score(q, t, mat, al, be, mode), (m, n, prot, mode)
