@@ -1,0 +1,332 @@
+#!/usr/bin/env python
+"""Benchmark of the score-only Gotoh alignment hot path on GB300.
+
+Workload (one "step"): 1M DNA pairs, |Q| ~ U{100..300}, S = Q with 5 %
+substitutions and 1 % indels (geometric length, mean 2), scored in global AND
+semi-global mode (+2/-3, gap open 5, extend 2) through ga_align_batch.  The
+metric is GCUPS: full-DP cells (sum of m*n, both modes) per second.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Multi-GPU (torchrun, one process per GPU): every rank aligns its own seeded
+batch of the same shape (weak scaling, no data-path collective); the step time
+is the max over ranks and `value` counts the cells of all ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+# int16 operations per cell in the paper's count for global / semi-global
+# affine alignment (Sec. 4.2: 4 max + 3 add/sub); local adds 2.
+OPS_PER_CELL = 7
+PEAK_SM_MHZ = 2070.0     # maximum SM clock of a GB300
+N_SM = 152
+LANES_PER_SM = 128       # 4 SM sub-partitions x 32 lanes, one integer op each per clock
+SIMD = 2                 # int16x2: two cells per lane-op
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--npairs", type=int, default=1_000_000)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0,
+                    help="target CPU time of the bounded oracle sample")
+    return ap.parse_args()
+
+
+def workload(npairs: int, rank: int):
+    return synth.mutated_dna_pairs(npairs=npairs, seed=synth.SEED_BASE + 2 + 1000 * rank)
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms during a region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        try:
+            for line in open(self.path):
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        finally:
+            try:
+                os.unlink(self.path)
+            except OSError:
+                pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no-samples"], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def cpu_baseline(b, seconds: float):
+    """The oracle as it stands, on a bounded sample of the same workload."""
+    import oracle
+    nthreads = os.cpu_count() or 1
+    probe = min(b.npairs, 2000)
+    sub = b.subset(np.arange(probe))
+    t0 = time.perf_counter()
+    for mode in ("global", "semiglobal"):
+        oracle.batch(sub.q_codes, sub.q_off, sub.t_codes, sub.t_off, sub.matrix, sub.alpha,
+                     sub.beta, mode, nthreads=nthreads)
+    dt = max(time.perf_counter() - t0, 1e-6)
+    k = int(min(b.npairs, max(probe, probe * seconds / dt)))
+    sub = b.subset(np.arange(k))
+    t0 = time.perf_counter()
+    for mode in ("global", "semiglobal"):
+        oracle.batch(sub.q_codes, sub.q_off, sub.t_codes, sub.t_off, sub.matrix, sub.alpha,
+                     sub.beta, mode, nthreads=nthreads)
+    dt = time.perf_counter() - t0
+    cells = 2 * sub.cells()
+    return {"value": cells / dt / 1e9, "unit": "GCUPS", "cores": nthreads, "kind": "oracle",
+            "sample": f"first {k} of {b.npairs} pairs, global+semiglobal, {dt:.1f} s"}
+
+
+def run_reference(args, rank: int):
+    if rank != 0:
+        return
+    b = workload(args.npairs, 0)
+    import oracle
+    nthreads = os.cpu_count() or 1
+    # per step: a bounded sample sized so the whole run stays within minutes
+    per_step = max(1, args.cpu_seconds / max(1, args.steps + args.warmup) * 2)
+    probe = min(b.npairs, 1000)
+    sub = b.subset(np.arange(probe))
+    t0 = time.perf_counter()
+    oracle.batch(sub.q_codes, sub.q_off, sub.t_codes, sub.t_off, sub.matrix, 5, 2, "global",
+                 nthreads=nthreads)
+    dt = max(time.perf_counter() - t0, 1e-6)
+    k = int(min(b.npairs, max(probe, probe * per_step / (2 * dt))))
+    sub = b.subset(np.arange(k))
+
+    def step():
+        for mode in ("global", "semiglobal"):
+            oracle.batch(sub.q_codes, sub.q_off, sub.t_codes, sub.t_off, sub.matrix, sub.alpha,
+                         sub.beta, mode, nthreads=nthreads)
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    dt = time.perf_counter() - t0
+    cells = 2 * sub.cells() * args.steps
+    value = cells / dt / 1e9
+    line = {
+        "impl": "reference", "metric": "GCUPS", "value": value, "unit": "GCUPS", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+        "data": "synthetic",
+        "config": {"workload": "dna-mutated-pairs L~U{100..300}, 5% sub, 1% indel; global+semiglobal",
+                   "npairs": args.npairs, "parallelism": "host threads"},
+        "cpu_baseline": {"value": value, "unit": "GCUPS", "cores": nthreads, "kind": "oracle",
+                         "sample": f"first {k} of {b.npairs} pairs per step"},
+        "e2e": {"value": value, "unit": "GCUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+
+    import torch
+    import paper_2205_07610_gb300 as ga
+
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    ga.build()
+    ga.load()
+
+    b = workload(args.npairs, rank)
+    cells_mode = b.cells()
+    step_cells = 2 * cells_mode
+    q = torch.from_numpy(b.q_codes).to(dev)
+    qo = torch.from_numpy(b.q_off).to(dev)
+    t = torch.from_numpy(b.t_codes).to(dev)
+    to = torch.from_numpy(b.t_off).to(dev)
+    s_glob = torch.empty(b.npairs, dtype=torch.int32, device=dev)
+    s_semi = torch.empty(b.npairs, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step(stats=False):
+        r1 = ga.align_batch(q, qo, t, to, b.matrix, b.alpha, b.beta, "global", scores=s_glob,
+                            stream=stream, stats=stats)
+        r2 = ga.align_batch(q, qo, t, to, b.matrix, b.alpha, b.beta, "semiglobal", scores=s_semi,
+                            stream=stream, stats=stats)
+        return (r1[1], r2[1]) if stats else None
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    for _ in range(max(args.warmup, 0)):
+        step()
+    torch.cuda.synchronize(dev)
+
+    # ---- timed region: K steps, events on the launching stream ----------
+    sts = []
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local_rank) as clk:
+        barrier()
+        torch.cuda.synchronize(dev)
+        ev0.record(stream)
+        for _ in range(args.steps):
+            sts.append(step(stats=True))
+        ev1.record(stream)
+        torch.cuda.synchronize(dev)
+        barrier()
+    ms = ev0.elapsed_time(ev1)
+    clocks = clk.summary()
+    if dist is not None:
+        tms = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(tms, op=dist.ReduceOp.MAX)
+        ms = float(tms.item())
+    ms_per_step = ms / args.steps
+    value = step_cells * world * args.steps / (ms / 1e3) / 1e9
+
+    status = [s["status"] for pair in sts for s in pair]
+    dp_ms = sum(s["dp_ms"] for pair in sts for s in pair)
+    dp_launches = sum(s["dp_launches"] for pair in sts for s in pair)
+    launches = sum(s["launches"] for pair in sts for s in pair)
+    int16_pairs = sum(s["pairs_int16"] for pair in sts for s in pair)
+
+    # ---- roofline of the dominant kernel (packed int16x2 inter-sequence DP)
+    sm_mhz = clocks.get("sm_mhz") or PEAK_SM_MHZ
+    peak_ops = N_SM * LANES_PER_SM * SIMD * PEAK_SM_MHZ * 1e6           # int16 ops / s
+    alg_ops = step_cells * args.steps * OPS_PER_CELL
+    achieved_ops = alg_ops / (dp_ms / 1e3) if dp_ms > 0 else 0.0
+    roofline = {
+        "bound": "alu", "achieved": achieved_ops / 1e12, "peak": peak_ops / 1e12,
+        "unit": "Tops/s (int16, 7 ops per cell)", "frac": achieved_ops / peak_ops,
+        "traffic": None,
+        "kernel": "ka_kernel<CellS16x2> (inter-sequence, packed int16x2)",
+        "dp_gcups": step_cells * args.steps / (dp_ms / 1e3) / 1e9 if dp_ms > 0 else None,
+        "dp_launches_per_step": dp_launches / args.steps,
+        "peak_gcups_at_7_ops": peak_ops / OPS_PER_CELL / 1e9,
+        "peak_basis": f"{N_SM} SM x {LANES_PER_SM} lanes x {SIMD} (int16x2) x {PEAK_SM_MHZ:.0f} MHz",
+        "sm_mhz_measured": sm_mhz,
+    }
+
+    # ---- end to end through the host entry point (pinned buffers) ---------
+    e2e = None
+    if not args.no_e2e:
+        hq = torch.from_numpy(b.q_codes).pin_memory()
+        hqo = torch.from_numpy(b.q_off).pin_memory()
+        ht = torch.from_numpy(b.t_codes).pin_memory()
+        hto = torch.from_numpy(b.t_off).pin_memory()
+        hs1 = torch.empty(b.npairs, dtype=torch.int32).pin_memory()
+        hs2 = torch.empty(b.npairs, dtype=torch.int32).pin_memory()
+
+        def hstep():
+            ga.align_batch_host(hq, hqo, ht, hto, b.matrix, b.alpha, b.beta, "global", scores=hs1,
+                                stream=stream)
+            ga.align_batch_host(hq, hqo, ht, hto, b.matrix, b.alpha, b.beta, "semiglobal",
+                                scores=hs2, stream=stream)
+        hstep()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            hstep()
+        barrier()
+        et = time.perf_counter() - t0
+        if dist is not None:
+            tt = torch.tensor([et], device=dev, dtype=torch.float64)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            et = float(tt.item())
+        assert torch.equal(hs1, s_glob.cpu()) and torch.equal(hs2, s_semi.cpu())
+        h2d = 2 * (hq.numel() + ht.numel() + 8 * (hqo.numel() + hto.numel()))
+        e2e = {"value": step_cells * world * args.steps / et / 1e9, "unit": "GCUPS",
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(2 * 4 * b.npairs)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(b, args.cpu_seconds)
+
+    if rank == 0:
+        line = {
+            "metric": "GCUPS", "value": value, "unit": "GCUPS", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "int16x2", "data": "synthetic",
+            "config": {
+                "workload": "dna-mutated-pairs L~U{100..300}, 5% sub, 1% indel; global+semiglobal",
+                "npairs_per_gpu": b.npairs, "cells_per_step_per_gpu": step_cells,
+                "scoring": "+2/-3, gap open 5, extend 2",
+                "parallelism": f"pairs sharded, {world} independent rank(s)",
+                "l2": "inputs larger than L2 (2 x 200 MB raw codes re-read each step)",
+            },
+            "clocks": clocks, "roofline": roofline, "e2e": e2e, "cpu_baseline": cpu,
+            "gpu_launches": launches, "dp_status": max(status) if status else 0,
+            "pairs_int16_per_step": int16_pairs / args.steps,
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -102,6 +102,10 @@ typedef struct {
     int64_t band_retries;      /* ga_align_banded: band doublings, all pairs */
     int64_t banded_cells;      /* ga_align_banded: cells evaluated in bands */
     float kernel_ms;           /* device time of the whole call (events) */
+    float dp_ms;               /* device time of the DP kernels alone (events
+                                  around each DP launch, summed) */
+    int32_t dp_launches;       /* DP kernel launches of the call */
+    int32_t launches;          /* all kernel launches of the call */
     int32_t status;            /* GA_OK or the first device-detected error */
 } ga_stats;
 

@@ -41,7 +41,8 @@ class Stats(ctypes.Structure):
                 ("pairs_int16", ctypes.c_int64), ("pairs_int32", ctypes.c_int64),
                 ("pairs_int32_rerun", ctypes.c_int64), ("band_retries", ctypes.c_int64),
                 ("banded_cells", ctypes.c_int64), ("kernel_ms", ctypes.c_float),
-                ("status", ctypes.c_int32)]
+                ("dp_ms", ctypes.c_float), ("dp_launches", ctypes.c_int32),
+                ("launches", ctypes.c_int32), ("status", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -137,11 +137,41 @@ struct Call {
   Alloc al;
   Small *small = nullptr;
   int32_t *hist = nullptr, *cursor = nullptr;
-  cudaError_t err = cudaSuccess;
   int64_t pairs = 0, pairs16 = 0, pairs32 = 0;
+  // Launch accounting and per-DP-launch device timing (stats requested).
+  bool timing = false;
+  int launches = 0, dp_launches = 0;
+  std::vector<cudaEvent_t> dp_ev;
   explicit Call(cudaStream_t st) : s(st), al(st) {}
-
-  int fail() { return al.failed ? GA_ERR_OOM : GA_ERR_CUDA; }
+  ~Call() {
+    for (cudaEvent_t e : dp_ev) cudaEventDestroy(e);
+  }
+  void dp_begin() {
+    ++launches;
+    ++dp_launches;
+    if (!timing) return;
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) == cudaSuccess) {
+      dp_ev.push_back(e);
+      cudaEventRecord(e, s);
+    }
+  }
+  void dp_end() {
+    if (!timing) return;
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) == cudaSuccess) {
+      dp_ev.push_back(e);
+      cudaEventRecord(e, s);
+    }
+  }
+  float dp_ms() const {
+    float tot = 0.f;
+    for (size_t i = 0; i + 1 < dp_ev.size(); i += 2) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, dp_ev[i], dp_ev[i + 1]) == cudaSuccess) tot += ms;
+    }
+    return tot;
+  }
 };
 
 int setup(Call &c) {
@@ -177,6 +207,7 @@ int prepare_set(Call &c, const uint8_t *codes, const int64_t *off, int64_t nseq,
   const int wpb = 8;
   const int64_t blocks = (nseq + wpb - 1) / wpb;
   pack_kernel<<<(unsigned)blocks, 32 * wpb, 0, c.s>>>(codes, off, nseq, total, c.sc.A, *packed, *bad);
+  ++c.launches;
   if (cudaGetLastError() != cudaSuccess) return GA_ERR_CUDA;
   return GA_OK;
 }
@@ -228,6 +259,7 @@ int run_chunk(Call &c, const SetView &Q, const SetView &T, int64_t npairs, int64
   hist_kernel<<<nb, tb, 0, c.s>>>(keys, npairs, c.hist);
   scan_kernel<<<1, 1024, 0, c.s>>>(c.hist, c.cursor, c.small->ranges);
   scatter_kernel<<<nb, tb, 0, c.s>>>(keys, npairs, c.cursor, sorted);
+  c.launches += 4;
   if (cudaGetLastError() != cudaSuccess) return GA_ERR_CUDA;
 
   Readback *rb = (Readback *)pinned_scratch();
@@ -277,6 +309,7 @@ int run_chunk(Call &c, const SetView &Q, const SetView &T, int64_t npairs, int64
       const int64_t want = (ntasks + (kKaThreads / 32) - 1) / (kKaThreads / 32);
       const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)c.nsm * std::max(occ, 1)));
       cudaError_t e;
+      c.dp_begin();
       if (cls == 0) {
         e = c.mode == GA_LOCAL ? launch_ka16_local(bin, ka, grid, c.s)
           : c.mode == GA_GLOBAL ? launch_ka16_global(bin, ka, grid, c.s)
@@ -286,6 +319,7 @@ int run_chunk(Call &c, const SetView &Q, const SetView &T, int64_t npairs, int64
           : c.mode == GA_GLOBAL ? launch_ka32_global(bin, ka, grid, c.s)
                                 : launch_ka32_semi(bin, ka, grid, c.s);
       }
+      c.dp_end();
       if (e != cudaSuccess) return GA_ERR_CUDA;
     }
   }
@@ -334,6 +368,7 @@ int run_chunk(Call &c, const SetView &Q, const SetView &T, int64_t npairs, int64
       kb.nt = nt;
       kb.q0 = q0;
       cudaError_t e;
+      c.dp_begin();
       if (profile)
         e = c.mode == GA_LOCAL ? launch_kb_local_prof(kb, grid, smem, c.s)
           : c.mode == GA_GLOBAL ? launch_kb_global_prof(kb, grid, smem, c.s)
@@ -342,6 +377,7 @@ int run_chunk(Call &c, const SetView &Q, const SetView &T, int64_t npairs, int64
         e = c.mode == GA_LOCAL ? launch_kb_local_sel(kb, grid, smem, c.s)
           : c.mode == GA_GLOBAL ? launch_kb_global_sel(kb, grid, smem, c.s)
                                 : launch_kb_semi_sel(kb, grid, smem, c.s);
+      c.dp_end();
       if (e != cudaSuccess) return GA_ERR_CUDA;
     }
   }
@@ -361,8 +397,11 @@ int run_chunk(Call &c, const SetView &Q, const SetView &T, int64_t npairs, int64
       ka.task_counter = &c.small->counters[counter++];
       const int bin = kKaNumBins - 1;
       const int occ = blocks_per_sm_ka32_local(bin);
-      if (launch_ka32_local(bin, ka, c.nsm * std::max(occ, 1), c.s) != cudaSuccess)
-        return GA_ERR_CUDA;
+      c.launches += 2;
+      c.dp_begin();
+      const cudaError_t e = launch_ka32_local(bin, ka, c.nsm * std::max(occ, 1), c.s);
+      c.dp_end();
+      if (e != cudaSuccess) return GA_ERR_CUDA;
     }
   }
   return GA_OK;
@@ -384,6 +423,9 @@ int finish(Call &c, ga_stats *st, cudaEvent_t e0, cudaEvent_t e1, int64_t pairs)
   st->pairs_int32 = c.pairs32;
   st->pairs_int32_rerun = rb->rerun_total;
   st->kernel_ms = ms;
+  st->dp_ms = c.dp_ms();
+  st->dp_launches = c.dp_launches;
+  st->launches = c.launches;
   st->status = rb->status;
   return GA_OK;
 }
@@ -414,6 +456,7 @@ int batch_impl(const uint8_t *q_codes, const int64_t *q_off, const uint8_t *t_co
   int rc = check_scoring(scoring, &c.sc);
   if (rc) return rc;
   c.mode = mode;
+  c.timing = stats != nullptr;
   Events ev(stats != nullptr, c.s);
   if ((rc = setup(c))) return rc;
   SetView Q{q_codes, q_off, nullptr, nullptr}, T{t_codes, t_off, nullptr, nullptr};
@@ -488,6 +531,7 @@ int ga_align_cross(const uint8_t *q_codes, const int64_t *q_off, int64_t nq, con
   int rc = check_scoring(scoring, &c.sc);
   if (rc) return rc;
   c.mode = mode;
+  c.timing = stats != nullptr;
   Events ev(stats != nullptr, c.s);
   if ((rc = setup(c))) return rc;
   if (nq == 0 || nt == 0) return finish(c, stats, ev.e0, ev.e1, 0);

@@ -126,7 +126,9 @@ __device__ __forceinline__ void ka_run_task(const KAParams &p, int lane, int tas
     int h0 = 0;
     if constexpr (MODE == kModeGlobal) h0 = ::max(-alpha - beta * col, kNeg);  // H(0, col+1)
     H[j] = Cell::splat(h0);
-    E[j] = Cell::splat(kNeg);  // E(0, .) = -inf, so E(1, .) = H(0, .) - alpha
+    // E holds E(i, .) of the row about to be computed: E(1, j) =
+    // max(E(0, j) - beta, H(0, j) - alpha) with E(0, j) = -inf.
+    E[j] = Cell::splat(::max(h0 - alpha, kNeg));
   }
   // Lane 0 starts row 1 at iteration 0 with H(1,0) on its left and H(0,0)=0
   // on its diagonal.  Lane t > 0 starts row 1 at iteration t; its diagonal
@@ -137,7 +139,8 @@ __device__ __forceinline__ void ka_run_task(const KAParams &p, int lane, int tas
   const int hb0 = (MODE == kModeGlobal) ? -alpha : 0;  // H(1,0)
   T Hdiag = Cell::splat(hd0);
   T Hleft = Cell::splat(t == 0 ? hb0 : hd0);
-  T Fin = Cell::splat(kNeg);
+  // Lane 0's F(r, 1) = max(F(r, 0) - beta, H(r, 0) - alpha), F(r, 0) = -inf.
+  T Fin = Cell::splat(t == 0 ? hb0 - alpha : kNeg);
   T hb = Cell::splat(hb0);  // lane 0: H(r,0) of its current row
   const T nbeta_b = Cell::splat((MODE == kModeGlobal) ? -beta : 0);
   const T NAc = Cell::splat(-alpha);
@@ -216,7 +219,7 @@ __device__ __forceinline__ void ka_run_task(const KAParams &p, int lane, int tas
     hb = Cell::add(hb, nbeta_b);
     if (t == 0) {
       Hleft = hb;
-      Fin = NEGV;
+      Fin = Cell::add(hb, NAc);
     }
   }
 

@@ -110,7 +110,7 @@ __global__ void __launch_bounds__(128) kb_kernel(const __grid_constant__ KBParam
         }
         if constexpr (MODE == kModeSemi) na[j] = (col == C - 1) ? 0 : -alpha;
         H[j] = (MODE == kModeGlobal) ? ::max(-alpha - beta * col, kNeg) : 0;  // H(0, col+1)
-        E[j] = kNeg;
+        E[j] = ::max(H[j] - alpha, kNeg);  // E(1, col+1) = H(0, col+1) - alpha
       }
       if constexpr (PROFILE) {
         // P[c][x] = sigma(row residue c, column residue x); pad row c = A
@@ -131,9 +131,9 @@ __global__ void __launch_bounds__(128) kb_kernel(const __grid_constant__ KBParam
       // ---- boundary of the stage's left edge --------------------------
       auto left_row = [&](int r) -> int2 {  // (H(r, col0), F(r, col0+1))
         int2 v;
-        if (s == 0) {
+        if (s == 0) {  // column 0: H(r, 0) and F(r, 1) = H(r, 0) - alpha
           v.x = (MODE == kModeGlobal) ? ((r == 0) ? 0 : ::max(-alpha - beta * (r - 1), kNeg)) : 0;
-          v.y = kNeg;
+          v.y = ::max(v.x - alpha, kNeg);
         } else {
           v = in_ring[(r - 1) & 63];
         }

@@ -90,9 +90,11 @@ def test_mixed_lengths_all_bins(mode):
     swap = rng.random(n) < 0.3
     lt[swap] = rng.integers(1, 700, size=int(swap.sum()))
     qc, qo, tc, to = _pairs(rng, lq, lt)
-    b = synth.Batch(qc, qo, tc, to, synth.dna_matrix(2, -3), 5, 2, "mixed")
-    got = gpu_batch(b, mode)
-    assert_same(got, oracle_batch(b, mode), f"mixed {mode}")
+    # cheap gaps make paths through the row-0 / column-0 borders optimal often
+    for (ma, mi), al, be in (((2, -3), 5, 2), ((2, -3), 1, 1), ((1, -4), 2, 1)):
+        b = synth.Batch(qc, qo, tc, to, synth.dna_matrix(ma, mi), al, be, "mixed")
+        got = gpu_batch(b, mode)
+        assert_same(got, oracle_batch(b, mode), f"mixed {mode} {ma}/{mi} {al}/{be}")
 
 
 @pytest.mark.parametrize("mode", ["global", "semiglobal"])
@@ -180,8 +182,9 @@ def test_long_pairs_multistage(mode):
     lq = [520, 1000, 3000, 1500, 2048, 4100]
     lt = [600, 1300, 2500, 3500, 2048, 700]
     qc, qo, tc, to = _pairs(rng, lq, lt)
-    b = synth.Batch(qc, qo, tc, to, synth.dna_matrix(2, -3), 5, 2, "long")
-    assert_same(gpu_batch(b, mode), oracle_batch(b, mode), f"long {mode}")
+    for (ma, mi), al, be in (((2, -3), 5, 2), ((2, -3), 1, 1)):
+        b = synth.Batch(qc, qo, tc, to, synth.dna_matrix(ma, mi), al, be, "long")
+        assert_same(gpu_batch(b, mode), oracle_batch(b, mode), f"long {mode} {al}/{be}")
     lb = synth.long_dna_pairs(npairs=8, lmin=1000, lmax=5000, seed=21)
     assert_same(gpu_batch(lb, mode), oracle_batch(lb, mode), f"long mutated {mode}")
 
@@ -193,8 +196,9 @@ def test_protein_blosum62(mode):
     lq = rng.integers(1, 700, size=300)
     lt = rng.integers(1, 700, size=300)
     qc, qo, tc, to = _pairs(rng, lq, lt, 24, bg)
-    b = synth.Batch(qc, qo, tc, to, synth.blosum62(), 11, 1, "protein")
-    assert_same(gpu_batch(b, mode), oracle_batch(b, mode), f"protein {mode}")
+    for al, be in ((11, 1), (2, 1)):
+        b = synth.Batch(qc, qo, tc, to, synth.blosum62(), al, be, "protein")
+        assert_same(gpu_batch(b, mode), oracle_batch(b, mode), f"protein {mode} {al}/{be}")
 
 
 def test_device_detected_errors():
