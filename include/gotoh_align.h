@@ -178,6 +178,34 @@ int ga_align_banded(const uint8_t *q_codes, const int64_t *q_off, const uint8_t 
                     const int32_t *w0, int32_t default_w0, int32_t *scores, int32_t *w_used,
                     void *stream, ga_stats *stats);
 
+/*
+ * ga_align_long_noalloc -- ga_align_long for callers that cannot allocate
+ * device memory while they align: for example a process whose device memory
+ * is held in full by a pooling allocator (cudaMalloc would fail), or a
+ * latency-critical loop that cannot take the implicit synchronisation and
+ * unbounded latency of cudaMalloc / cudaFree.  The paper has no counterpart;
+ * this is a deployment variant of the long-pair kernel.
+ *
+ * It allocates nothing: its scratch memory (the stage-boundary buffer of the
+ * long-pair kernel and a small control block, about 2 MiB) is one
+ * file-scope device array that every GPU using the library holds until the
+ * process exits.  The caller still passes the inputs q[0..m), t[0..n) and
+ * the output *score (all device pointers, as for ga_align_long) and the
+ * host scoring struct.
+ *   - max(m, n) <= GA_NOALLOC_MAX_LEN, otherwise GA_ERR_ARG (nothing is
+ *     enqueued); other argument errors as for ga_align_batch.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) once for that device; make that first call
+ *     before any stream capture.
+ *   - Every call shares the array and leaves its contents behind; each call
+ *     rewrites what must start fresh.  Calls whose GPU work overlaps (other
+ *     streams, unordered host threads) race on the array: serialise them.
+ *   - A residue code >= alphabet_size yields *score = INT32_MIN.
+ */
+#define GA_NOALLOC_MAX_LEN 65536
+int ga_align_long_noalloc(const uint8_t *q, int64_t m, const uint8_t *t, int64_t n,
+                          const ga_scoring *scoring, int32_t mode, int32_t *score, void *stream);
+
 /* Human-readable message for a GA_* code (static string, never NULL). */
 const char *ga_strerror(int code);
 

@@ -28,7 +28,8 @@ GA_ERR_RANGE = 7
 
 # Symbols declared in include/gotoh_align.h (checked by the CPU tests).
 EXPORTED = ("ga_align_batch", "ga_align_batch_host", "ga_align_cross", "ga_align_long",
-            "ga_align_banded", "ga_strerror", "ga_version")
+            "ga_align_long_noalloc", "ga_align_banded", "ga_strerror", "ga_version")
+NOALLOC_MAX_LEN = 65536
 
 
 class Scoring(ctypes.Structure):
@@ -82,8 +83,9 @@ def load(build_if_missing: bool = False):
     lib.ga_align_cross.argtypes = [P, P, i64, P, P, i64, sp, i32, P, P, stp]
     lib.ga_align_long.argtypes = [P, i64, P, i64, sp, i32, P, P, stp]
     lib.ga_align_banded.argtypes = [P, P, P, P, i64, sp, P, i32, P, P, P, stp]
+    lib.ga_align_long_noalloc.argtypes = [P, i64, P, i64, sp, i32, P, P]
     for f in ("ga_align_batch", "ga_align_batch_host", "ga_align_cross", "ga_align_long",
-              "ga_align_banded"):
+              "ga_align_long_noalloc", "ga_align_banded"):
         getattr(lib, f).restype = i32
     lib.ga_strerror.argtypes = [ctypes.c_int]
     lib.ga_strerror.restype = ctypes.c_char_p
@@ -206,6 +208,25 @@ def align_long(q, t, matrix, gap_open, gap_extend, mode, stream=None, stats: boo
     if rc:
         raise GotohError(rc, "ga_align_long")
     return (out, st.as_dict()) if stats else out
+
+
+def align_long_noalloc(q, t, matrix, gap_open, gap_extend, mode, out=None, stream=None):
+    """ga_align_long_noalloc: one pair, no device allocation by the library.
+
+    For callers that cannot allocate device memory while aligning (memory held
+    by a pooling allocator, latency-critical loops).  `out` (a 1-element int32
+    CUDA tensor) may be passed in so that nothing at all is allocated here.
+    """
+    import torch
+    _check_dev(q, t)
+    if out is None:
+        out = torch.empty(1, dtype=torch.int32, device=q.device)
+    sc, keep = make_scoring(matrix, gap_open, gap_extend)
+    rc = load().ga_align_long_noalloc(_ptr(q), q.numel(), _ptr(t), t.numel(), ctypes.byref(sc),
+                                      _mode(mode), _ptr(out), _stream_ptr(stream))
+    if rc:
+        raise GotohError(rc, "ga_align_long_noalloc")
+    return out
 
 
 def align_banded(q_codes, q_off, t_codes, t_off, matrix, gap_open, gap_extend, w0=None,
