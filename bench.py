@@ -42,7 +42,7 @@ SIMD = 2                 # int16x2: two cells per lane-op
 def parse_args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--npairs", type=int, default=1_000_000)
@@ -60,7 +60,7 @@ def workload(npairs: int, rank: int):
 class ClockSampler:
     """nvidia-smi clocks / throttle reasons sampled every 200 ms during a region."""
 
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
@@ -68,6 +68,14 @@ class ClockSampler:
         self.dev = device_index
         self.proc = None
         self.path = None
+        self.t0 = None
+        self.t1 = None
+
+    def mark_start(self):
+        self.t0 = time.time()
+
+    def mark_end(self):
+        self.t1 = time.time()
 
     def __enter__(self):
         fd, self.path = tempfile.mkstemp(suffix=".csv")
@@ -90,26 +98,37 @@ class ClockSampler:
                 self.proc.kill()
 
     def summary(self):
+        import datetime
         rows = []
         try:
             for line in open(self.path):
                 parts = [p.strip() for p in line.split(",")]
-                if len(parts) >= 9:
-                    rows.append(parts)
+                if len(parts) < 10:
+                    continue
+                try:
+                    ts = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                except ValueError:
+                    ts = None
+                rows.append((ts, parts[1:]))
         finally:
             try:
                 os.unlink(self.path)
             except OSError:
                 pass
-        if not rows:
+        inside = [r for ts, r in rows
+                  if ts is not None and self.t0 is not None and self.t0 - 0.25 <= ts <= self.t1 + 0.25]
+        used = inside if inside else [r for _, r in rows]
+        if not used:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no-samples"], "samples": 0}
-        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
-        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        sm = [float(r[1]) for r in used if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in used if r[2].replace(".", "").isdigit()]
+        pw = [float(r[3]) for r in used if r[3].replace(".", "").isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        reasons = sorted({names[k] for r in used for k in range(4) if r[5 + k].lower() == "active"})
         return {"sm_mhz": float(np.median(sm)) if sm else None,
                 "sm_max_mhz": max(smax) if smax else None, "reasons": reasons,
-                "samples": len(rows)}
+                "power_w_max": max(pw) if pw else None,
+                "samples": len(used), "samples_in_timed_region": len(inside)}
 
 
 def cpu_baseline(b, seconds: float):
@@ -222,22 +241,25 @@ def main():
         if dist is not None:
             dist.barrier()
 
-    for _ in range(max(args.warmup, 0)):
-        step()
-    torch.cuda.synchronize(dev)
-
-    # ---- timed region: K steps, events on the launching stream ----------
+    # ---- warm-up, then the timed region: K steps, events on the launching
+    # stream; nvidia-smi samples clocks from before the warm-up on and only
+    # the samples inside the timed window are reported.
     sts = []
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     with ClockSampler(local_rank) as clk:
+        for _ in range(max(args.warmup, 0)):
+            step()
+        torch.cuda.synchronize(dev)
         barrier()
         torch.cuda.synchronize(dev)
+        clk.mark_start()
         ev0.record(stream)
         for _ in range(args.steps):
             sts.append(step(stats=True))
         ev1.record(stream)
         torch.cuda.synchronize(dev)
+        clk.mark_end()
         barrier()
     ms = ev0.elapsed_time(ev1)
     clocks = clk.summary()
