@@ -9,13 +9,13 @@ costs gap_open + (k-1) * gap_extend).
 """
 from ._binding import (LOCAL, GLOBAL, SEMIGLOBAL, EXPORTED, GotohError, Scoring, Stats,
                        align_banded, align_batch, align_batch_host, align_cross, align_long,
-                       align_long_noalloc, NOALLOC_MAX_LEN,
+                       align_long_noalloc, NOALLOC_MAX_LEN, PROBES, probe_issue_rate,
                        lib_path, load, make_scoring, strerror, version)
 from .build import build
 
 __all__ = [
     "LOCAL", "GLOBAL", "SEMIGLOBAL", "EXPORTED", "GotohError", "Scoring", "Stats", "align_banded",
     "align_batch", "align_batch_host", "align_cross", "align_long", "align_long_noalloc",
-    "NOALLOC_MAX_LEN", "lib_path", "load",
+    "NOALLOC_MAX_LEN", "PROBES", "probe_issue_rate", "lib_path", "load",
     "make_scoring", "strerror", "version", "build",
 ]

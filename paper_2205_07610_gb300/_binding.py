@@ -28,7 +28,11 @@ GA_ERR_RANGE = 7
 
 # Symbols declared in include/gotoh_align.h (checked by the CPU tests).
 EXPORTED = ("ga_align_batch", "ga_align_batch_host", "ga_align_cross", "ga_align_long",
-            "ga_align_long_noalloc", "ga_align_banded", "ga_strerror", "ga_version")
+            "ga_align_long_noalloc", "ga_align_banded", "ga_strerror", "ga_version",
+            "ga_probe_issue_rate")
+PROBES = {"vadd2": 0, "vmaxs2": 1, "viaddmax_s16x2": 2, "vimax3_s16x2": 3,
+          "viaddmax_s16x2_relu": 4, "prmt": 5, "iadd": 6, "imax": 7, "viaddmax_s32": 8,
+          "vimax3_s32": 9, "imad": 10, "lop3": 11, "hadd2": 12, "hmax2": 13, "cell": 14}
 NOALLOC_MAX_LEN = 65536
 
 
@@ -87,12 +91,30 @@ def load(build_if_missing: bool = False):
     for f in ("ga_align_batch", "ga_align_batch_host", "ga_align_cross", "ga_align_long",
               "ga_align_long_noalloc", "ga_align_banded"):
         getattr(lib, f).restype = i32
+    lib.ga_probe_issue_rate.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                        ctypes.POINTER(ctypes.c_float),
+                                        ctypes.POINTER(ctypes.c_double)]
+    lib.ga_probe_issue_rate.restype = ctypes.c_int
     lib.ga_strerror.argtypes = [ctypes.c_int]
     lib.ga_strerror.restype = ctypes.c_char_p
     lib.ga_version.argtypes = []
     lib.ga_version.restype = ctypes.c_int
     _lib = lib
     return lib
+
+
+def probe_issue_rate(op: str, iters: int = 1024, blocks: int = 0, threads: int = 256):
+    """(ms, lane_ops) of one timed launch of an issue-rate probe (gotoh_probe.h)."""
+    if blocks <= 0:
+        import torch
+        blocks = 8 * torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    ms = ctypes.c_float(0)
+    ops = ctypes.c_double(0)
+    rc = load().ga_probe_issue_rate(PROBES[op], int(iters), int(blocks), int(threads),
+                                    ctypes.byref(ms), ctypes.byref(ops))
+    if rc:
+        raise RuntimeError(f"ga_probe_issue_rate({op}) failed: {rc}")
+    return float(ms.value), float(ops.value)
 
 
 def strerror(code: int) -> str:
