@@ -3,6 +3,7 @@
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "ga_launch.h"
@@ -64,16 +65,52 @@ int check_scoring(const ga_scoring *sc, Scoring *out) {
   return GA_OK;
 }
 
+// The library's own stream-ordered memory pool per device.  Its release
+// threshold keeps freed workspace mapped between calls, so a call does not
+// pay for mapping and unmapping hundreds of MB at every synchronisation (the
+// device's default pool returns memory to the driver at each sync).  The
+// pool is created on first use per device and lives until the process ends.
+std::mutex g_pool_mu;
+cudaMemPool_t g_pool[64] = {};
+
+cudaMemPool_t pool_for_current_device() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  std::lock_guard<std::mutex> lock(g_pool_mu);
+  if (!g_pool[dev]) {
+    cudaMemPoolProps props{};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.handleTypes = cudaMemHandleTypeNone;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t p = nullptr;
+    if (cudaMemPoolCreate(&p, &props) != cudaSuccess) return nullptr;
+    uint64_t keep = ~0ull;
+    cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &keep);
+    g_pool[dev] = p;
+  }
+  return g_pool[dev];
+}
+
+cudaError_t pool_malloc(void **p, size_t bytes, cudaStream_t s) {
+  cudaMemPool_t pool = pool_for_current_device();
+  return pool ? cudaMallocFromPoolAsync(p, bytes, pool, s) : cudaMallocAsync(p, bytes, s);
+}
+
 // Device allocations of one call, released stream-ordered.
 struct Alloc {
   cudaStream_t s;
+  cudaMemPool_t pool;
   std::vector<void *> ptrs;
   bool failed = false;
-  explicit Alloc(cudaStream_t st) : s(st) {}
+  explicit Alloc(cudaStream_t st) : s(st), pool(pool_for_current_device()) {}
   template <class T>
   T *get(size_t n) {
     void *p = nullptr;
-    if (cudaMallocAsync(&p, n * sizeof(T) + 256, s) != cudaSuccess) {
+    const size_t bytes = n * sizeof(T) + 256;
+    const cudaError_t e = pool ? cudaMallocFromPoolAsync(&p, bytes, pool, s)
+                               : cudaMallocAsync(&p, bytes, s);
+    if (e != cudaSuccess) {
       failed = true;
       return nullptr;
     }
@@ -499,11 +536,11 @@ int ga_align_batch_host(const uint8_t *q_codes, const int64_t *q_off, const uint
     cudaFreeAsync(dq, s); cudaFreeAsync(dt, s); cudaFreeAsync(dqo, s);
     cudaFreeAsync(dto, s); cudaFreeAsync(ds, s);
   };
-  if (cudaMallocAsync((void **)&dq, (size_t)qn + 16, s) != cudaSuccess ||
-      cudaMallocAsync((void **)&dt, (size_t)tn + 16, s) != cudaSuccess ||
-      cudaMallocAsync((void **)&dqo, sizeof(int64_t) * (size_t)(npairs + 1), s) != cudaSuccess ||
-      cudaMallocAsync((void **)&dto, sizeof(int64_t) * (size_t)(npairs + 1), s) != cudaSuccess ||
-      cudaMallocAsync((void **)&ds, sizeof(int32_t) * (size_t)(npairs + 1), s) != cudaSuccess) {
+  if (pool_malloc((void **)&dq, (size_t)qn + 16, s) != cudaSuccess ||
+      pool_malloc((void **)&dt, (size_t)tn + 16, s) != cudaSuccess ||
+      pool_malloc((void **)&dqo, sizeof(int64_t) * (size_t)(npairs + 1), s) != cudaSuccess ||
+      pool_malloc((void **)&dto, sizeof(int64_t) * (size_t)(npairs + 1), s) != cudaSuccess ||
+      pool_malloc((void **)&ds, sizeof(int32_t) * (size_t)(npairs + 1), s) != cudaSuccess) {
     cleanup();
     return GA_ERR_OOM;
   }
@@ -560,7 +597,7 @@ int ga_align_long(const uint8_t *q, int64_t m, const uint8_t *t, int64_t n, cons
   if (m < 0 || n < 0 || !score || (m > 0 && !q) || (n > 0 && !t)) return GA_ERR_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   int64_t *off = nullptr;
-  if (cudaMallocAsync((void **)&off, 4 * sizeof(int64_t), s) != cudaSuccess) return GA_ERR_OOM;
+  if (pool_malloc((void **)&off, 4 * sizeof(int64_t), s) != cudaSuccess) return GA_ERR_OOM;
   fill_off_kernel<<<1, 1, 0, s>>>(off, 0, m);
   fill_off_kernel<<<1, 1, 0, s>>>(off + 2, 0, n);
   const uint8_t *qq = q ? q : (const uint8_t *)off, *tt = t ? t : (const uint8_t *)off;

@@ -55,6 +55,7 @@ struct CellS16x2 {
     return __viaddmax_s16x2_relu(a, b, c);
   }
   static __device__ __forceinline__ T max3(T a, T b, T c) { return __vimax3_s16x2(a, b, c); }
+  static __device__ __forceinline__ T max3_relu(T a, T b, T c) { return __vimax3_s16x2_relu(a, b, c); }
   static __device__ __forceinline__ T splat(int v) { return splat2(v); }
 };
 
@@ -67,6 +68,7 @@ struct CellS32 {
     return __viaddmax_s32_relu(a, b, c);
   }
   static __device__ __forceinline__ T max3(T a, T b, T c) { return __vimax3_s32(a, b, c); }
+  static __device__ __forceinline__ T max3_relu(T a, T b, T c) { return __vimax3_s32_relu(a, b, c); }
   static __device__ __forceinline__ T splat(int v) { return v; }
 };
 

@@ -5,17 +5,21 @@
 // it receives from its left neighbour H(i, j0-1) folded into F(i, j0)
 // (Fin) and the diagonal H(i-1, j0-1) (Hdiag), and updates in place:
 //
-//   pass 1 (right to left):  H_j <- max(H_{j-1} + sigma(i, j), E_j)
-//                            (H_{j-1} still holds row i-1; for local mode
-//                             the fused op also clamps at nu = 0)
-//   pass 2 (left to right):  H_j <- max(H_j, F)                  (Eq. H)
+//   pass 1 (right to left):  H_j <- H_{j-1} + sigma(i, j)    (H_{j-1} still
+//                                                             holds row i-1)
+//   pass 2 (left to right):  H_j <- max(H_j, E_j, F)         (Eq. H; local
+//                                                             mode also 0)
 //                            A   <- H_j - alpha
-//                            E_j <- max(E_j - beta, A)           (Eq. E, row i+1)
-//                            F   <- max(F - beta, A)             (Eq. F, col j+1)
+//                            E_j <- max(E_j - beta, A)       (Eq. E, row i+1)
+//                            F   <- max(F - beta, A)         (Eq. F, col j+1)
 //
-// Each register update is 5 DPX/SIMD ops plus the sigma lookup.  On exit
-// H holds row i, E holds E(i+1, .), and the returned F is F(i, j0+K) for the
-// right neighbour.
+// Pipe balance on sm_103a: the packed add runs on the FMA pipe, the max /
+// fused add-max / byte-permute ops on the ALU pipe, each at 16 lanes per
+// clock per SM sub-partition.  Per register this is 2 FMA-pipe ops (the two
+// adds) and 4 ALU-pipe ops (3-way max, two fused add-max, the sigma prmt),
+// against the 7 scalar ops per cell of the paper's count (Sec. 4.2).  On
+// exit H holds row i, E holds E(i+1, .), and the returned F is F(i, j0+K)
+// for the right neighbour.
 #pragma once
 
 #include <type_traits>
@@ -59,18 +63,12 @@ __device__ __forceinline__ typename Cell::T dp_row(typename Cell::T (&H)[K], typ
                                                     SigFn SIG, NaFn NA) {
   using T = typename Cell::T;
 #pragma unroll
-  for (int j = K - 1; j >= 1; --j) {
-    T sg = SIG(j);
-    H[j] = (MODE == kModeLocal) ? Cell::addmax_relu(H[j - 1], sg, E[j]) : Cell::addmax(H[j - 1], sg, E[j]);
-  }
-  {
-    T sg = SIG(0);
-    H[0] = (MODE == kModeLocal) ? Cell::addmax_relu(Hdiag, sg, E[0]) : Cell::addmax(Hdiag, sg, E[0]);
-  }
+  for (int j = K - 1; j >= 1; --j) H[j] = Cell::add(H[j - 1], SIG(j));
+  H[0] = Cell::add(Hdiag, SIG(0));
   T F = Fin;
 #pragma unroll
   for (int j = 0; j < K; ++j) {
-    H[j] = Cell::max(H[j], F);
+    H[j] = (MODE == kModeLocal) ? Cell::max3_relu(H[j], E[j], F) : Cell::max3(H[j], E[j], F);
     T A = Cell::add(H[j], NA(j));
     E[j] = Cell::addmax(E[j], NB, A);
     F = Cell::addmax(F, NB, A);

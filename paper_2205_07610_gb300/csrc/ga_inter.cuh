@@ -54,9 +54,35 @@ struct KAParams {
   int64_t nt, q0;            // cross chunk: pair p = (q0 + p/nt, p%nt); batch: nt = 0
 };
 
+// Per-group state that the hot loop needs only every G iterations (ring
+// refill) or once (results) lives in shared memory, not in registers.
+struct KAGroupDesc {
+  const uint32_t *rowseq[2];  // packed words of each half's row sequence
+  int R[2];                   // rows of each half (0: no pair)
+  int tab[2];                 // table word offset: 0 (rows = query) or 8
+  int pad[2];
+};
+
+// Minimum resident blocks per SM requested from ptxas (__launch_bounds__):
+// the highest occupancy at which each (cell type, mode, K) instantiation
+// still compiles without register spills on sm_103a (found by compiling
+// every combination; the global-mode kernels need the most registers).
+template <class Cell, int MODE, int K>
+struct KAMinBlocks {
+  static constexpr int kIdx = K <= 8 ? 0 : K <= 12 ? 1 : K <= 16 ? 2 : K <= 20 ? 3 : K <= 24 ? 4 : 5;
+  static constexpr int kPacked[3][6] = {{8, 8, 6, 6, 5, 4},   // local
+                                         {6, 5, 4, 4, 3, 1},   // global
+                                         {8, 6, 5, 4, 3, 1}};  // semi-global
+  static constexpr int kScalar[3][6] = {{8, 8, 6, 6, 5, 4},
+                                         {8, 5, 4, 4, 3, 1},
+                                         {8, 6, 5, 4, 4, 3}};
+  static constexpr int value = CellInfo<Cell>::kPacked ? kPacked[MODE][kIdx] : kScalar[MODE][kIdx];
+};
+
 template <class Cell, int MODE, int G, int K>
 __device__ __forceinline__ void ka_run_task(const KAParams &p, int lane, int task,
-                                            uint2 *ring /* [4G] of this group */) {
+                                            uint2 *ring /* [4G] of this group */,
+                                            KAGroupDesc *desc, uint32_t *evbuf /* [2][K] */) {
   using T = typename Cell::T;
   constexpr bool kPacked = CellInfo<Cell>::kPacked;
   constexpr int kHalves = CellInfo<Cell>::kHalves;
@@ -71,26 +97,33 @@ __device__ __forceinline__ void ka_run_task(const KAParams &p, int lane, int tas
   const int base = p.range[0] + task * kPairsPerTask;
 
   // ---- the pairs of this group (half 0 = low, half 1 = high) ----------
-  int id[2] = {-1, -1}, R[2] = {0, 0}, C[2] = {0, 0}, sw[2] = {0, 0};
-  int64_t roww[2] = {0, 0}, colw[2] = {0, 0};
+  int id[2] = {-1, -1}, R[2] = {0, 0}, C[2] = {0, 0};
+  const uint32_t *colseq[2] = {nullptr, nullptr};
 #pragma unroll
   for (int h = 0; h < kHalves; ++h) {
-    int s = base + g * kHalves + h;
+    const int s = base + g * kHalves + h;
+    const uint32_t *rowseq = nullptr;
+    int sw = 0;
     if (s < end) {
-      int pid = p.sorted[s];
-      int4 inf = p.info[pid];
-      id[h] = pid; R[h] = inf.x; C[h] = inf.y; sw[h] = inf.z;
+      const int pid = p.sorted[s];
+      const int4 inf = p.info[pid];
+      id[h] = pid; R[h] = inf.x; C[h] = inf.y; sw = inf.z;
       const int64_t qi = p.nt ? p.q0 + pid / p.nt : pid, ti = p.nt ? pid % p.nt : pid;
-      const int64_t qw = p.q_off[qi] / 16 + qi, tw = p.t_off[ti] / 16 + ti;
-      roww[h] = sw[h] ? tw : qw;  // rows: the longer sequence
-      colw[h] = sw[h] ? qw : tw;
+      const uint32_t *qs = p.packed_q + (p.q_off[qi] / 16 + qi);
+      const uint32_t *ts = p.packed_t + (p.t_off[ti] / 16 + ti);
+      rowseq = sw ? ts : qs;  // rows: the longer sequence
+      colseq[h] = sw ? qs : ts;
+    }
+    if (t == 0) {
+      desc->rowseq[h] = rowseq;
+      desc->R[h] = R[h];
+      desc->tab[h] = sw ? 8 : 0;
     }
   }
-  const uint32_t *rowbase[2], *colbase[2];
-#pragma unroll
-  for (int h = 0; h < 2; ++h) {
-    rowbase[h] = sw[h] ? p.packed_t : p.packed_q;
-    colbase[h] = sw[h] ? p.packed_q : p.packed_t;
+  if (kHalves == 1 && t == 0) {
+    desc->rowseq[1] = nullptr;
+    desc->R[1] = 0;
+    desc->tab[1] = 0;
   }
   const int Rtask = __reduce_max_sync(0xffffffffu, (unsigned)max(R[0], R[1]));
 
@@ -105,7 +138,7 @@ __device__ __forceinline__ void ka_run_task(const KAParams &p, int lane, int tas
     uint32_t s = 0;
 #pragma unroll
     for (int h = 0; h < kHalves; ++h) {
-      const int c = (col < C[h]) ? packed_code(colbase[h], colw[h], col) : -1;
+      const int c = (col < C[h]) ? (int)((__ldg(colseq[h] + (col >> 4)) >> (2 * (col & 15))) & 3u) : -1;
       if constexpr (kPacked) {
         const uint32_t n0 = (c >= 0) ? (uint32_t)(c + 4 * h) : (uint32_t)(8 + 4 * h);
         const uint32_t n1 = (c >= 0) ? (uint32_t)(c + 4 * h + 8) : (uint32_t)(8 + 4 * h);
@@ -130,6 +163,8 @@ __device__ __forceinline__ void ka_run_task(const KAParams &p, int lane, int tas
     // max(E(0, j) - beta, H(0, j) - alpha) with E(0, j) = -inf.
     E[j] = Cell::splat(::max(h0 - alpha, kNeg));
   }
+  // Which half ends on which row, and (global) which lane owns column n.
+  const int own0 = (C[0] - 1) / K, own1 = (C[1] - 1) / K;
   // Lane 0 starts row 1 at iteration 0 with H(1,0) on its left and H(0,0)=0
   // on its diagonal.  Lane t > 0 starts row 1 at iteration t; its diagonal
   // is the left tile's row-0 value H(0, t*K), which Hleft carries until the
@@ -147,22 +182,23 @@ __device__ __forceinline__ void ka_run_task(const KAParams &p, int lane, int tas
   const T NB = Cell::splat(-beta);
   const T NEGV = Cell::splat(kNeg);
   T best = Cell::splat(0);
-  int res[2] = {0, 0};
-  bool got[2] = {false, false};
+  T rmax = Cell::splat(0);  // semi: packed max over the row m of each half
 
   // ---- row table words: ring of 4G rows, refilled a batch of G ahead --
-  auto table_word = [&](int h, int r) -> uint32_t {
-    if (r > R[h] || r < 1) return 0u;
-    const int code = packed_code(rowbase[h], roww[h], r - 1);
-    return p.tables[(sw[h] ? 8 : 0) + code];
-  };
   auto fill_batch = [&](int b) {
     const int r = b * G + 1 + t;
-    uint2 v;
-    v.x = table_word(0, r);
-    v.y = kPacked ? table_word(1, r) : 0u;
+    uint2 v = make_uint2(0u, 0u);
+#pragma unroll
+    for (int h = 0; h < kHalves; ++h) {
+      if (r <= desc->R[h]) {
+        const uint32_t w = __ldg(desc->rowseq[h] + ((r - 1) >> 4));
+        const uint32_t tw = p.tables[desc->tab[h] + ((w >> (2 * ((r - 1) & 15))) & 3u)];
+        if (h == 0) v.x = tw; else v.y = tw;
+      }
+    }
     ring[r & (kRing - 1)] = v;
   };
+  __syncwarp();
   fill_batch(0);
   fill_batch(1);
   __syncwarp();
@@ -187,24 +223,24 @@ __device__ __forceinline__ void ka_run_task(const KAParams &p, int lane, int tas
       Hout = H[K - 1];
       if constexpr (MODE != kModeLocal) {
         if (r == R[0] || r == R[1]) {
+          if constexpr (MODE == kModeGlobal) {
+            // the lane owning column n parks its row in shared memory
 #pragma unroll
-          for (int h = 0; h < kHalves; ++h) {
-            if (r != R[h]) continue;
-            if constexpr (MODE == kModeGlobal) {
-              const int o = C[h] - 1 - t * K;  // column n in this tile?
-              if (o >= 0 && o < K) {
-                T v = H[0];
+            for (int h = 0; h < kHalves; ++h)
+              if (r == R[h] && t == (h ? own1 : own0)) {
 #pragma unroll
-                for (int j = 1; j < K; ++j)
-                  if (j == o) v = H[j];
-                res[h] = cell_get<Cell>(v, h);
-                got[h] = true;
+                for (int j = 0; j < K; ++j) evbuf[h * K + j] = (uint32_t)H[j];
               }
-            } else {
-              int mx = 0;
+          } else {
+            T m = H[0];
 #pragma unroll
-              for (int j = 0; j < K; ++j) mx = ::max(mx, cell_get<Cell>(H[j], h));
-              res[h] = mx;
+            for (int j = 1; j + 1 < K; j += 2) m = Cell::max3(m, H[j], H[j + 1]);
+            if ((K & 1) == 0) m = Cell::max(m, H[K - 1]);
+            if constexpr (kPacked) {
+              const uint32_t keep = (r == R[0] ? 0x0000ffffu : 0u) | (r == R[1] ? 0xffff0000u : 0u);
+              rmax = (T)((uint32_t)Cell::max(rmax, m) & keep | (uint32_t)rmax & ~keep);
+            } else {
+              rmax = Cell::max(rmax, m);
             }
           }
         }
@@ -222,17 +258,20 @@ __device__ __forceinline__ void ka_run_task(const KAParams &p, int lane, int tas
       Fin = Cell::add(hb, NAc);
     }
   }
+  __syncwarp();
 
   // ---- results ----------------------------------------------------------
 #pragma unroll
   for (int h = 0; h < kHalves; ++h) {
     int v = 0;
     if constexpr (MODE == kModeLocal) v = group_max<G>(cell_get<Cell>(best, h));
-    else if constexpr (MODE == kModeSemi) v = group_max<G>(res[h]);
-    else v = res[h];
+    else if constexpr (MODE == kModeSemi) v = group_max<G>(cell_get<Cell>(rmax, h));
     if (id[h] < 0) continue;
     if constexpr (MODE == kModeGlobal) {
-      if (got[h]) p.scores[id[h]] = v;
+      if (t == 0) {
+        const uint32_t w = evbuf[h * K + (C[h] - 1) % K];
+        p.scores[id[h]] = cell_get<Cell>((T)w, h);
+      }
     } else if (t == 0) {
       if (kPacked && MODE == kModeLocal && v >= 32767 - p.sigma_max_pos) {
         const int slot = atomicAdd(p.rerun_count, 1);
@@ -242,13 +281,16 @@ __device__ __forceinline__ void ka_run_task(const KAParams &p, int lane, int tas
       }
     }
   }
+  __syncwarp();
 }
 
 template <class Cell, int MODE, int G, int K>
-__global__ void __launch_bounds__(128) ka_kernel(const __grid_constant__ KAParams p) {
+__global__ void __launch_bounds__(128, KAMinBlocks<Cell, MODE, K>::value) ka_kernel(const __grid_constant__ KAParams p) {
   constexpr int kWarps = 4;
   constexpr int kGroups = 32 / G;
   __shared__ uint2 ring_s[kWarps][kGroups][4 * G];
+  __shared__ KAGroupDesc desc_s[kWarps][kGroups];
+  __shared__ uint32_t evbuf_s[kWarps][kGroups][MODE == kModeGlobal ? 2 * K : 1];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int npairs = p.range[1] - p.range[0];
   constexpr int kPairsPerTask = CellInfo<Cell>::kHalves * kGroups;
@@ -258,7 +300,8 @@ __global__ void __launch_bounds__(128) ka_kernel(const __grid_constant__ KAParam
     if (lane == 0) task = atomicAdd(p.task_counter, 1);
     task = __shfl_sync(0xffffffffu, task, 0);
     if (task >= ntasks) break;
-    ka_run_task<Cell, MODE, G, K>(p, lane, task, ring_s[warp][lane / G]);
+    ka_run_task<Cell, MODE, G, K>(p, lane, task, ring_s[warp][lane / G], &desc_s[warp][lane / G],
+                                  evbuf_s[warp][lane / G]);
   }
 }
 
