@@ -70,12 +70,12 @@ struct KAGroupDesc {
 template <class Cell, int MODE, int K>
 struct KAMinBlocks {
   static constexpr int kIdx = K <= 8 ? 0 : K <= 12 ? 1 : K <= 16 ? 2 : K <= 20 ? 3 : K <= 24 ? 4 : 5;
-  static constexpr int kPacked[3][6] = {{8, 8, 6, 6, 5, 4},   // local
-                                         {6, 5, 4, 4, 3, 1},   // global
-                                         {8, 6, 5, 4, 3, 1}};  // semi-global
+  static constexpr int kPacked[3][6] = {{8, 8, 6, 6, 4, 3},   // local
+                                         {8, 6, 5, 4, 3, 1},   // global
+                                         {8, 6, 4, 4, 3, 3}};  // semi-global
   static constexpr int kScalar[3][6] = {{8, 8, 6, 6, 5, 4},
-                                         {8, 5, 4, 4, 3, 1},
-                                         {8, 6, 5, 4, 4, 3}};
+                                         {8, 8, 6, 5, 4, 1},
+                                         {8, 6, 5, 3, 3, 1}};
   static constexpr int value = CellInfo<Cell>::kPacked ? kPacked[MODE][kIdx] : kScalar[MODE][kIdx];
 };
 
@@ -203,15 +203,29 @@ __device__ __forceinline__ void ka_run_task(const KAParams &p, int lane, int tas
   fill_batch(1);
   __syncwarp();
 
-  const int nit = Rtask + G - 1;
-  for (int it = 0; it < nit; ++it) {
-    if ((it % G) == 0) {
-      fill_batch(it / G + 2);  // rows needed from iteration it + 2G on
-      __syncwarp();
+  // Event window: iterations in which some lane of the warp reaches the
+  // last row of one of its pairs (global: read H(m,n); semi: row-m max).
+  int rlo = 1 << 30, rhi = 0;
+#pragma unroll
+  for (int h = 0; h < kHalves; ++h)
+    if (R[h] > 0) {
+      rlo = ::min(rlo, R[h]);
+      rhi = ::max(rhi, R[h]);
     }
+  const int ev_lo = (int)__reduce_min_sync(0xffffffffu, (unsigned)rlo) - 1;
+  const int ev_hi = (int)__reduce_max_sync(0xffffffffu, (unsigned)rhi) + G - 2;
+
+  // One wavefront step.  GENERAL: lanes may be outside [1, Rtask] (the
+  // first G-1 iterations) or at the last row of a pair (event window).
+  // Outside those the step runs without checks: rows beyond a pair's end
+  // use the all-zero table word, so the lanes that run past Rtask during
+  // the drain compute pad rows that no real cell reads and that can never
+  // raise a running max.
+  auto step = [&](int it, auto general_tag) {
+    constexpr bool GENERAL = decltype(general_tag)::value;
     const int r = it - t + 1;
     T Hout, Fout;
-    if ((unsigned)(r - 1) < (unsigned)Rtask) {
+    if (!GENERAL || (unsigned)(r - 1) < (unsigned)Rtask) {
       const uint2 tw = ring[r & (kRing - 1)];
       Fout = dp_row<Cell, MODE, K>(
           H, E, Hdiag, Fin, NB, best,
@@ -221,7 +235,7 @@ __device__ __forceinline__ void ka_run_task(const KAParams &p, int lane, int tas
             else return NAc;
           });
       Hout = H[K - 1];
-      if constexpr (MODE != kModeLocal) {
+      if constexpr (GENERAL && MODE != kModeLocal) {
         if (r == R[0] || r == R[1]) {
           if constexpr (MODE == kModeGlobal) {
             // the lane owning column n parks its row in shared memory
@@ -238,7 +252,7 @@ __device__ __forceinline__ void ka_run_task(const KAParams &p, int lane, int tas
             if ((K & 1) == 0) m = Cell::max(m, H[K - 1]);
             if constexpr (kPacked) {
               const uint32_t keep = (r == R[0] ? 0x0000ffffu : 0u) | (r == R[1] ? 0xffff0000u : 0u);
-              rmax = (T)((uint32_t)Cell::max(rmax, m) & keep | (uint32_t)rmax & ~keep);
+              rmax = (T)(((uint32_t)Cell::max(rmax, m) & keep) | ((uint32_t)rmax & ~keep));
             } else {
               rmax = Cell::max(rmax, m);
             }
@@ -256,6 +270,35 @@ __device__ __forceinline__ void ka_run_task(const KAParams &p, int lane, int tas
     if (t == 0) {
       Hleft = hb;
       Fin = Cell::add(hb, NAc);
+    }
+  };
+
+  // Segments of warp-uniform kind between refills (every G iterations).
+  const int nit = Rtask + G - 1;
+  int it = 0;
+  while (it < nit) {
+    if ((it % G) == 0) {
+      fill_batch(it / G + 2);  // rows needed from iteration it + 2G on
+      __syncwarp();
+    }
+    int stop = ::min(nit, (it / G + 1) * G);
+    bool general;
+    if (it < G - 1) {
+      stop = ::min(stop, G - 1);
+      general = true;
+    } else if (MODE != kModeLocal && it < ev_lo) {
+      stop = ::min(stop, ev_lo);
+      general = false;
+    } else if (MODE != kModeLocal && it <= ev_hi) {
+      stop = ::min(stop, ev_hi + 1);
+      general = true;
+    } else {
+      general = false;
+    }
+    if (general) {
+      for (; it < stop; ++it) step(it, std::true_type{});
+    } else {
+      for (; it < stop; ++it) step(it, std::false_type{});
     }
   }
   __syncwarp();
