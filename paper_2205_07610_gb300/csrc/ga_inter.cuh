@@ -69,19 +69,22 @@ struct KAGroupDesc {
 // every combination; the global-mode kernels need the most registers).
 template <class Cell, int MODE, int K>
 struct KAMinBlocks {
-  static constexpr int kIdx = K <= 8 ? 0 : K <= 12 ? 1 : K <= 16 ? 2 : K <= 20 ? 3 : K <= 24 ? 4 : 5;
-  static constexpr int kPacked[3][6] = {{8, 8, 6, 6, 4, 3},   // local
-                                         {8, 6, 5, 4, 3, 1},   // global
-                                         {8, 6, 4, 4, 3, 3}};  // semi-global
-  static constexpr int kScalar[3][6] = {{8, 8, 6, 6, 5, 4},
-                                         {8, 8, 6, 5, 4, 1},
-                                         {8, 6, 5, 3, 3, 1}};
+  // columns per lane:                  8  10  12  14  16  18  20  24  32
+  static constexpr int kKs[9] = {8, 10, 12, 14, 16, 18, 20, 24, 32};
+  static constexpr int kIdx = K <= 8 ? 0 : K <= 10 ? 1 : K <= 12 ? 2 : K <= 14 ? 3 : K <= 16 ? 4
+                            : K <= 18 ? 5 : K <= 20 ? 6 : K <= 24 ? 7 : 8;
+  static constexpr int kPacked[3][9] = {{8, 8, 8, 8, 6, 6, 6, 5, 4},   // local
+                                         {8, 8, 6, 6, 5, 4, 4, 3, 3},   // global
+                                         {8, 8, 6, 6, 4, 5, 4, 4, 3}};  // semi-global
+  static constexpr int kScalar[3][9] = {{8, 8, 8, 8, 6, 6, 6, 5, 4},
+                                         {8, 8, 8, 5, 6, 5, 4, 3, 1},
+                                         {8, 6, 6, 5, 5, 4, 4, 3, 3}};
   static constexpr int value = CellInfo<Cell>::kPacked ? kPacked[MODE][kIdx] : kScalar[MODE][kIdx];
 };
 
 template <class Cell, int MODE, int G, int K>
 __device__ __forceinline__ void ka_run_task(const KAParams &p, int lane, int task,
-                                            uint2 *ring /* [4G] of this group */,
+                                            uint2 *ring /* [5G]: 4G-row ring + mirror of its first G rows */,
                                             KAGroupDesc *desc, uint32_t *evbuf /* [2][K] */) {
   using T = typename Cell::T;
   constexpr bool kPacked = CellInfo<Cell>::kPacked;
@@ -196,7 +199,9 @@ __device__ __forceinline__ void ka_run_task(const KAParams &p, int lane, int tas
         if (h == 0) v.x = tw; else v.y = tw;
       }
     }
-    ring[r & (kRing - 1)] = v;
+    const int slot = r & (kRing - 1);
+    ring[slot] = v;
+    if (slot < G) ring[slot + kRing] = v;  // mirror: any G consecutive rows are contiguous
   };
   __syncwarp();
   fill_batch(0);
@@ -221,12 +226,12 @@ __device__ __forceinline__ void ka_run_task(const KAParams &p, int lane, int tas
   // use the all-zero table word, so the lanes that run past Rtask during
   // the drain compute pad rows that no real cell reads and that can never
   // raise a running max.
-  auto step = [&](int it, auto general_tag) {
+  auto step = [&](int it, const uint2 *rp, auto general_tag) {
     constexpr bool GENERAL = decltype(general_tag)::value;
     const int r = it - t + 1;
     T Hout, Fout;
     if (!GENERAL || (unsigned)(r - 1) < (unsigned)Rtask) {
-      const uint2 tw = ring[r & (kRing - 1)];
+      const uint2 tw = *rp;
       Fout = dp_row<Cell, MODE, K>(
           H, E, Hdiag, Fin, NB, best,
           [&](int j) -> T { return (T)prmt(tw.x, tw.y, (uint32_t)sel[j]); },
@@ -266,10 +271,15 @@ __device__ __forceinline__ void ka_run_task(const KAParams &p, int lane, int tas
     Hdiag = Hleft;
     Hleft = __shfl_up_sync(0xffffffffu, Hout, 1, G);
     Fin = __shfl_up_sync(0xffffffffu, Fout, 1, G);
-    hb = Cell::add(hb, nbeta_b);
-    if (t == 0) {
-      Hleft = hb;
-      Fin = Cell::add(hb, NAc);
+    if constexpr (MODE == kModeGlobal) {
+      hb = Cell::add(hb, nbeta_b);
+      if (t == 0) {
+        Hleft = hb;
+        Fin = Cell::add(hb, NAc);
+      }
+    } else if (t == 0) {  // local / semi-global: H(r,0) = 0, F(r,1) = -alpha
+      Hleft = Cell::splat(0);
+      Fin = NAc;
     }
   };
 
@@ -295,10 +305,13 @@ __device__ __forceinline__ void ka_run_task(const KAParams &p, int lane, int tas
     } else {
       general = false;
     }
+    // this lane's ring entries of the segment are contiguous (mirrored ring)
+    const uint2 *rp = ring + ((it - t + 1) & (kRing - 1));
     if (general) {
-      for (; it < stop; ++it) step(it, std::true_type{});
+      for (; it < stop; ++it, ++rp) step(it, rp, std::true_type{});
     } else {
-      for (; it < stop; ++it) step(it, std::false_type{});
+#pragma unroll 2
+      for (; it < stop; ++it, ++rp) step(it, rp, std::false_type{});
     }
   }
   __syncwarp();
@@ -331,7 +344,7 @@ template <class Cell, int MODE, int G, int K>
 __global__ void __launch_bounds__(128, KAMinBlocks<Cell, MODE, K>::value) ka_kernel(const __grid_constant__ KAParams p) {
   constexpr int kWarps = 4;
   constexpr int kGroups = 32 / G;
-  __shared__ uint2 ring_s[kWarps][kGroups][4 * G];
+  __shared__ uint2 ring_s[kWarps][kGroups][5 * G];
   __shared__ KAGroupDesc desc_s[kWarps][kGroups];
   __shared__ uint32_t evbuf_s[kWarps][kGroups][MODE == kModeGlobal ? 2 * K : 1];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;

@@ -17,7 +17,7 @@
 
 namespace ga {
 
-constexpr int kBins = 8;
+constexpr int kBins = 12;
 constexpr int kRBuckets = 4096;
 constexpr int kClassesSorted = 3;  // inter16, inter32, long
 constexpr int kNumKeys = kClassesSorted * kBins * kRBuckets;
