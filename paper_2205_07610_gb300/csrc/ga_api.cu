@@ -145,6 +145,7 @@ struct Small {
   int32_t ranges[2 * kClassesSorted * kBins];
   int32_t counters[64];
   int32_t rerun_range[2];
+  int32_t scan_partials[kScanTiles];
 };
 
 struct Readback {
@@ -294,9 +295,11 @@ int run_chunk(Call &c, const SetView &Q, const SetView &T, int64_t npairs, int64
   const unsigned nb = (unsigned)((npairs + tb - 1) / tb);
   plan_kernel<<<nb, tb, 0, c.s>>>(pp);
   hist_kernel<<<nb, tb, 0, c.s>>>(keys, npairs, c.hist);
-  scan_kernel<<<1, 1024, 0, c.s>>>(c.hist, c.cursor, c.small->ranges);
+  scan_partials_kernel<<<kScanTiles, kScanTile, 0, c.s>>>(c.hist, c.small->scan_partials);
+  scan_apply_kernel<<<kScanTiles, kScanTile, 0, c.s>>>(c.hist, c.small->scan_partials, c.cursor,
+                                                       c.small->ranges);
   scatter_kernel<<<nb, tb, 0, c.s>>>(keys, npairs, c.cursor, sorted);
-  c.launches += 4;
+  c.launches += 5;
   if (cudaGetLastError() != cudaSuccess) return GA_ERR_CUDA;
 
   Readback *rb = (Readback *)pinned_scratch();

@@ -18,7 +18,7 @@
 namespace ga {
 
 constexpr int kBins = 12;
-constexpr int kRBuckets = 4096;
+constexpr int kRBuckets = 2048;  // exact rows below 1536, then 64-row steps
 constexpr int kClassesSorted = 3;  // inter16, inter32, long
 constexpr int kNumKeys = kClassesSorted * kBins * kRBuckets;
 
@@ -52,9 +52,20 @@ struct PlanParams {
   int32_t *rmax_long;         // max rows over long-class pairs
 };
 
+// 2-bit codes of the 4 bytes of x (low 2 bits of each byte) in 8 bits.
+__device__ __forceinline__ uint32_t pack4(uint32_t x) {
+  uint32_t y = x & 0x03030303u;
+  y = (y | (y >> 6)) & 0x000f000fu;
+  return (y | (y >> 12)) & 0xffu;
+}
+
 // Warp per sequence: validate codes < A, pack 2-bit (if packed != nullptr).
 // A sequence whose offsets are decreasing or leave [0, total] (total =
 // off[nseq], the size of the code buffer) is flagged and never touched.
+// Each lane produces one 16-residue word at a time from five aligned 32-bit
+// loads (coalesced across the warp) realigned with funnel shifts; near the
+// end of the buffer, or for a code buffer that is not 4-byte aligned, it
+// falls back to byte loads.
 __global__ void pack_kernel(const uint8_t *codes, const int64_t *off, int64_t nseq, int64_t total,
                             int A, uint32_t *packed, uint8_t *bad) {
   const int64_t k = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -68,20 +79,46 @@ __global__ void pack_kernel(const uint8_t *codes, const int64_t *off, int64_t ns
   }
   const int64_t word0 = start / 16 + k;
   const int64_t nwords = (len + 15) / 16;
-  unsigned mx = 0;
+  const bool aligned_base = (reinterpret_cast<uintptr_t>(codes) & 3u) == 0;
+  uint32_t mx = 0;  // byte-wise max of the codes seen
   for (int64_t w = lane; w < nwords; w += 32) {
-    uint32_t word = 0;
-    const int64_t b = start + w * 16;
+    const int64_t s0 = start + w * 16;
+    const int nb = (int)(len - w * 16 < 16 ? len - w * 16 : 16);
+    uint32_t x[4];
+    const int64_t a = s0 & ~(int64_t)3;
+    if (aligned_base && a + 20 <= total) {
+      const uint32_t *pa = reinterpret_cast<const uint32_t *>(codes + a);
+      uint32_t v[5];
 #pragma unroll
-    for (int i = 0; i < 16; ++i) {
-      if (w * 16 + i < len) {
-        const unsigned c = codes[b + i];
-        mx = max(mx, c);
-        word |= (c & 3u) << (2 * i);
+      for (int i = 0; i < 5; ++i) v[i] = __ldg(pa + i);
+      const unsigned sh = (unsigned)(s0 & 3) * 8u;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) x[i] = __funnelshift_r(v[i], v[i + 1], sh);
+    } else {
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        uint32_t acc = 0;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int64_t idx = s0 + 4 * i + j;
+          if (4 * i + j < nb) acc |= (uint32_t)codes[idx] << (8 * j);
+        }
+        x[i] = acc;
       }
+    }
+    uint32_t word = 0;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int valid = nb - 4 * i;  // bytes of x[i] inside the sequence
+      const uint32_t keep = valid >= 4 ? 0xffffffffu : (valid <= 0 ? 0u : (0xffffffffu >> (8 * (4 - valid))));
+      const uint32_t xi = x[i] & keep;
+      mx = __vmaxu4(mx, xi);
+      word |= pack4(xi) << (8 * i);
     }
     if (packed) packed[word0 + w] = word;
   }
+  mx = __vmaxu4(mx, mx >> 16);
+  mx = __vmaxu4(mx, mx >> 8) & 0xffu;
   mx = __reduce_max_sync(0xffffffffu, mx);
   if (lane == 0) bad[k] = (len > 0 && mx >= (unsigned)A) ? 1 : 0;
 }
@@ -90,10 +127,8 @@ __device__ __forceinline__ int global_gap(int alpha, int beta, int64_t len) {
   return len == 0 ? 0 : -(int)(alpha + beta * (len - 1));
 }
 
-// Thread per pair (batch) or per (query, target) combination (cross).
-__global__ void plan_kernel(PlanParams p) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= p.npairs) return;
+// One pair (batch) or (query, target) combination (cross chunk).
+__device__ __forceinline__ void plan_one(const PlanParams &p, int64_t i, unsigned long long &my_cells) {
   const int64_t qi = p.nt ? p.q0 + i / p.nt : i;
   const int64_t ti = p.nt ? i % p.nt : i;
   const int64_t m = p.q_off[qi + 1] - p.q_off[qi];
@@ -117,7 +152,7 @@ __global__ void plan_kernel(PlanParams p) {
       p.scores[i] = INT32_MIN;
       set_status(p.status, GA_ERR_RANGE);
     } else {
-      atomicAdd(p.cells, (unsigned long long)(m * n));
+      my_cells = (unsigned long long)(m * n);
       uint32_t cls = kClassLong;
       int bin = 0;
       if (p.dna) {
@@ -145,12 +180,22 @@ __global__ void plan_kernel(PlanParams p) {
       }
       if (cls == kClassLong) atomicMax(p.rmax_long, (int)R);
       inf = make_int4((int)R, (int)C, swap, (int)cls);
-      const int64_t rb = R < kRBuckets ? R : kRBuckets - 1;
+      const int64_t rb = R < 1536 ? R : (1536 + ((R - 1536) >> 6) < kRBuckets - 1 ? 1536 + ((R - 1536) >> 6) : kRBuckets - 1);
       key = (uint32_t)(((cls * kBins + bin) * kRBuckets) + (kRBuckets - 1 - rb));
     }
   }
   p.info[i] = inf;
   p.keys[i] = key;
+}
+
+__global__ void plan_kernel(PlanParams p) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  unsigned long long my_cells = 0;
+  if (i < p.npairs) plan_one(p, i, my_cells);
+  // one atomic per warp for the cell count
+#pragma unroll
+  for (int off = 16; off >= 1; off >>= 1) my_cells += __shfl_xor_sync(0xffffffffu, my_cells, off);
+  if ((threadIdx.x & 31) == 0 && my_cells) atomicAdd(p.cells, my_cells);
 }
 
 __global__ void hist_kernel(const uint32_t *keys, int64_t n, int32_t *hist) {
@@ -160,32 +205,70 @@ __global__ void hist_kernel(const uint32_t *keys, int64_t n, int32_t *hist) {
   if (k != 0xffffffffu) atomicAdd(&hist[k], 1);
 }
 
-// Single block: exclusive scan of hist -> cursor, and [start, end) ranges of
-// each (class, bin) in ranges[2 * (class * kBins + bin)].
-__global__ void scan_kernel(const int32_t *hist, int32_t *cursor, int32_t *ranges) {
-  constexpr int kThreads = 1024;
-  constexpr int kPer = kNumKeys / kThreads;
-  static_assert(kNumKeys % kThreads == 0, "scan tiling");
-  __shared__ int32_t part[kThreads];
-  const int tid = threadIdx.x;
-  int32_t local = 0;
-  for (int e = 0; e < kPer; ++e) local += hist[tid * kPer + e];
-  part[tid] = local;
+// Exclusive scan of hist -> cursor and the [start, end) range of every
+// (class, bin) in ranges[2 * (class * kBins + bin)], in two launches over
+// tiles of 1024 buckets: per-tile totals, then per-tile scans offset by the
+// totals of the tiles before.
+constexpr int kScanTile = 1024;
+constexpr int kScanTiles = kNumKeys / kScanTile;
+static_assert(kNumKeys % kScanTile == 0, "scan tiling");
+
+__device__ __forceinline__ int32_t block_sum_1024(int32_t v, int32_t *sm) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  v = __reduce_add_sync(0xffffffffu, (unsigned)v);
+  if (lane == 0) sm[warp] = v;
   __syncthreads();
-  for (int off = 1; off < kThreads; off <<= 1) {
-    int32_t v = (tid >= off) ? part[tid - off] : 0;
-    __syncthreads();
-    part[tid] += v;
-    __syncthreads();
+  int32_t tot = 0;
+  if (warp == 0) {
+    tot = __reduce_add_sync(0xffffffffu, (unsigned)sm[lane]);
+    if (lane == 0) sm[32] = tot;
   }
-  int32_t run = part[tid] - local;  // exclusive
-  for (int e = 0; e < kPer; ++e) {
-    const int k = tid * kPer + e;
-    if ((k % kRBuckets) == 0) ranges[2 * (k / kRBuckets)] = run;
-    cursor[k] = run;
-    run += hist[k];
-    if ((k % kRBuckets) == kRBuckets - 1) ranges[2 * (k / kRBuckets) + 1] = run;
+  __syncthreads();
+  return sm[32];
+}
+
+__global__ void scan_partials_kernel(const int32_t *hist, int32_t *partials) {
+  __shared__ int32_t sm[33];
+  const int32_t v = hist[blockIdx.x * kScanTile + threadIdx.x];
+  const int32_t tot = block_sum_1024(v, sm);
+  if (threadIdx.x == 0) partials[blockIdx.x] = tot;
+}
+
+__global__ void scan_apply_kernel(const int32_t *hist, const int32_t *partials, int32_t *cursor,
+                                  int32_t *ranges) {
+  __shared__ int32_t wsum[32];
+  __shared__ int32_t base_s;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (warp == 0) {
+    int32_t acc = 0;
+    for (int b = lane; b < (int)blockIdx.x; b += 32) acc += partials[b];
+    acc = (int32_t)__reduce_add_sync(0xffffffffu, (unsigned)acc);
+    if (lane == 0) base_s = acc;
   }
+  const int k = blockIdx.x * kScanTile + threadIdx.x;
+  const int32_t v = hist[k];
+  int32_t incl = v;  // inclusive warp scan
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int32_t u = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += u;
+  }
+  if (lane == 31) wsum[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    int32_t w = wsum[lane], wi = w;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int32_t u = __shfl_up_sync(0xffffffffu, wi, o);
+      if (lane >= o) wi += u;
+    }
+    wsum[lane] = wi - w;  // exclusive over warps
+  }
+  __syncthreads();
+  const int32_t excl = base_s + wsum[warp] + incl - v;
+  cursor[k] = excl;
+  if ((k % kRBuckets) == 0) ranges[2 * (k / kRBuckets)] = excl;
+  if ((k % kRBuckets) == kRBuckets - 1) ranges[2 * (k / kRBuckets) + 1] = excl + v;
 }
 
 __global__ void scatter_kernel(const uint32_t *keys, int64_t n, int32_t *cursor, int32_t *sorted) {
