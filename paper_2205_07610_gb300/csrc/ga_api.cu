@@ -146,6 +146,7 @@ struct Small {
   int32_t counters[64];
   int32_t rerun_range[2];
   int32_t scan_partials[kScanTiles];
+  int32_t invalid_q, invalid_t;
 };
 
 struct Readback {
@@ -228,7 +229,7 @@ int setup(Call &c) {
 
 // Validate + pack one sequence set.  Reads back the total residue count.
 int prepare_set(Call &c, const uint8_t *codes, const int64_t *off, int64_t nseq, uint32_t **packed,
-                uint8_t **bad) {
+                uint8_t **bad, int32_t *invalid) {
   *bad = c.al.get<uint8_t>((size_t)nseq + 1);
   *packed = nullptr;
   if (c.al.failed) return GA_ERR_OOM;
@@ -239,12 +240,18 @@ int prepare_set(Call &c, const uint8_t *codes, const int64_t *off, int64_t nseq,
     return GA_ERR_CUDA;
   const int64_t total = std::max<int64_t>(h[0], 0);
   if (c.dna) {
-    *packed = c.al.get<uint32_t>((size_t)(total / 16 + nseq + 2));
+    *packed = c.al.get<uint32_t>((size_t)(total / 16 + 2));
     if (c.al.failed) return GA_ERR_OOM;
   }
-  const int wpb = 8;
-  const int64_t blocks = (nseq + wpb - 1) / wpb;
-  pack_kernel<<<(unsigned)blocks, 32 * wpb, 0, c.s>>>(codes, off, nseq, total, c.sc.A, *packed, *bad);
+  const int64_t nwords = (total + 15) / 16;
+  const int64_t pblocks = std::min<int64_t>((nwords + 255) / 256, (int64_t)c.nsm * 16);
+  if (nwords > 0) {
+    flat_pack_kernel<<<(unsigned)std::max<int64_t>(pblocks, 1), 256, 0, c.s>>>(codes, total, c.sc.A,
+                                                                               *packed, invalid);
+    ++c.launches;
+  }
+  validate_kernel<<<(unsigned)((nseq + 255) / 256), 256, 0, c.s>>>(codes, off, nseq, total, c.sc.A,
+                                                                   invalid, *bad);
   ++c.launches;
   if (cudaGetLastError() != cudaSuccess) return GA_ERR_CUDA;
   return GA_OK;
@@ -500,8 +507,8 @@ int batch_impl(const uint8_t *q_codes, const int64_t *q_off, const uint8_t *t_co
   Events ev(stats != nullptr, c.s);
   if ((rc = setup(c))) return rc;
   SetView Q{q_codes, q_off, nullptr, nullptr}, T{t_codes, t_off, nullptr, nullptr};
-  if ((rc = prepare_set(c, q_codes, q_off, npairs, &Q.packed, &Q.bad))) return rc;
-  if ((rc = prepare_set(c, t_codes, t_off, npairs, &T.packed, &T.bad))) return rc;
+  if ((rc = prepare_set(c, q_codes, q_off, npairs, &Q.packed, &Q.bad, &c.small->invalid_q))) return rc;
+  if ((rc = prepare_set(c, t_codes, t_off, npairs, &T.packed, &T.bad, &c.small->invalid_t))) return rc;
   uint32_t *keys = c.al.get<uint32_t>((size_t)npairs);
   int4 *info = c.al.get<int4>((size_t)npairs);
   int32_t *sorted = c.al.get<int32_t>((size_t)npairs);
@@ -576,8 +583,8 @@ int ga_align_cross(const uint8_t *q_codes, const int64_t *q_off, int64_t nq, con
   if ((rc = setup(c))) return rc;
   if (nq == 0 || nt == 0) return finish(c, stats, ev.e0, ev.e1, 0);
   SetView Q{q_codes, q_off, nullptr, nullptr}, T{t_codes, t_off, nullptr, nullptr};
-  if ((rc = prepare_set(c, q_codes, q_off, nq, &Q.packed, &Q.bad))) return rc;
-  if ((rc = prepare_set(c, t_codes, t_off, nt, &T.packed, &T.bad))) return rc;
+  if ((rc = prepare_set(c, q_codes, q_off, nq, &Q.packed, &Q.bad, &c.small->invalid_q))) return rc;
+  if ((rc = prepare_set(c, t_codes, t_off, nt, &T.packed, &T.bad, &c.small->invalid_t))) return rc;
   const int64_t kChunk = 1 << 22;
   const int64_t qpc = std::max<int64_t>(1, std::min<int64_t>(nq, kChunk / nt));
   const int64_t cap = qpc * nt;

@@ -95,9 +95,11 @@ __device__ __forceinline__ int group_max(int v) {
   return v;
 }
 
-__device__ __forceinline__ int packed_code(const uint32_t *base, int64_t word0, int idx) {
-  uint32_t w = __ldg(base + word0 + (idx >> 4));
-  return (int)((w >> (2 * (idx & 15))) & 3u);
+// 2-bit code of the residue at position pos of a flat packed stream
+// (residue x of the code buffer lives in word x / 16, bits 2*(x % 16)).
+__device__ __forceinline__ int packed_code(const uint32_t *base, int64_t pos) {
+  const uint32_t w = __ldg(base + (pos >> 4));
+  return (int)((w >> (2 * (int)(pos & 15))) & 3u);
 }
 
 }  // namespace ga

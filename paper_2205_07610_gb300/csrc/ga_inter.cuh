@@ -36,7 +36,7 @@
 namespace ga {
 
 struct KAParams {
-  const uint32_t *packed_q;  // 2-bit codes, sequence k starts at word q_off[k]/16 + k
+  const uint32_t *packed_q;  // flat 2-bit codes: residue x in word x/16
   const uint32_t *packed_t;
   const int64_t *q_off;
   const int64_t *t_off;
@@ -57,28 +57,29 @@ struct KAParams {
 // Per-group state that the hot loop needs only every G iterations (ring
 // refill) or once (results) lives in shared memory, not in registers.
 struct KAGroupDesc {
-  const uint32_t *rowseq[2];  // packed words of each half's row sequence
-  int R[2];                   // rows of each half (0: no pair)
-  int tab[2];                 // table word offset: 0 (rows = query) or 8
-  int pad[2];
+  const uint32_t *rowbase[2];  // packed stream holding each half's row sequence
+  int64_t rowpos[2];           // position of its first residue in that stream
+  int R[2];                    // rows of each half (0: no pair)
+  int tab[2];                  // table word offset: 0 (rows = query) or 8
 };
 
 // Minimum resident blocks per SM requested from ptxas (__launch_bounds__):
 // the highest occupancy at which each (cell type, mode, K) instantiation
-// still compiles without register spills on sm_103a (found by compiling
-// every combination; the global-mode kernels need the most registers).
+// still compiles without register spills on sm_103a, as printed by
+// `python -m paper_2205_07610_gb300.occupancy_sweep` (rerun after changing
+// the kernel).
 template <class Cell, int MODE, int K>
 struct KAMinBlocks {
   // columns per lane:                  8  10  12  14  16  18  20  24  32
   static constexpr int kKs[9] = {8, 10, 12, 14, 16, 18, 20, 24, 32};
   static constexpr int kIdx = K <= 8 ? 0 : K <= 10 ? 1 : K <= 12 ? 2 : K <= 14 ? 3 : K <= 16 ? 4
                             : K <= 18 ? 5 : K <= 20 ? 6 : K <= 24 ? 7 : 8;
-  static constexpr int kPacked[3][9] = {{8, 8, 8, 8, 6, 6, 6, 5, 4},   // local
-                                         {8, 8, 6, 6, 5, 4, 4, 3, 3},   // global
-                                         {8, 8, 6, 6, 4, 5, 4, 4, 3}};  // semi-global
-  static constexpr int kScalar[3][9] = {{8, 8, 8, 8, 6, 6, 6, 5, 4},
-                                         {8, 8, 8, 5, 6, 5, 4, 3, 1},
-                                         {8, 6, 6, 5, 5, 4, 4, 3, 3}};
+  static constexpr int kPacked[3][9] = {{8, 6, 6, 8, 6, 6, 5, 4, 3},   // local
+                                         {8, 8, 5, 5, 5, 4, 4, 3, 1},   // global
+                                         {8, 8, 5, 4, 4, 3, 3, 1, 1}};  // semi-global
+  static constexpr int kScalar[3][9] = {{8, 8, 8, 8, 6, 6, 5, 4, 3},
+                                         {8, 6, 6, 6, 6, 5, 5, 1, 1},
+                                         {8, 8, 6, 5, 5, 4, 3, 3, 1}};
   static constexpr int value = CellInfo<Cell>::kPacked ? kPacked[MODE][kIdx] : kScalar[MODE][kIdx];
 };
 
@@ -101,30 +102,35 @@ __device__ __forceinline__ void ka_run_task(const KAParams &p, int lane, int tas
 
   // ---- the pairs of this group (half 0 = low, half 1 = high) ----------
   int id[2] = {-1, -1}, R[2] = {0, 0}, C[2] = {0, 0};
-  const uint32_t *colseq[2] = {nullptr, nullptr};
+  const uint32_t *colbase[2] = {p.packed_t, p.packed_t};
+  int64_t colpos[2] = {0, 0};
 #pragma unroll
   for (int h = 0; h < kHalves; ++h) {
     const int s = base + g * kHalves + h;
-    const uint32_t *rowseq = nullptr;
+    const uint32_t *rowbase = p.packed_q;
+    int64_t rowpos = 0;
     int sw = 0;
     if (s < end) {
       const int pid = p.sorted[s];
       const int4 inf = p.info[pid];
       id[h] = pid; R[h] = inf.x; C[h] = inf.y; sw = inf.z;
       const int64_t qi = p.nt ? p.q0 + pid / p.nt : pid, ti = p.nt ? pid % p.nt : pid;
-      const uint32_t *qs = p.packed_q + (p.q_off[qi] / 16 + qi);
-      const uint32_t *ts = p.packed_t + (p.t_off[ti] / 16 + ti);
-      rowseq = sw ? ts : qs;  // rows: the longer sequence
-      colseq[h] = sw ? qs : ts;
+      const int64_t qs = p.q_off[qi], ts = p.t_off[ti];
+      rowbase = sw ? p.packed_t : p.packed_q;  // rows: the longer sequence
+      rowpos = sw ? ts : qs;
+      colbase[h] = sw ? p.packed_q : p.packed_t;
+      colpos[h] = sw ? qs : ts;
     }
     if (t == 0) {
-      desc->rowseq[h] = rowseq;
+      desc->rowbase[h] = rowbase;
+      desc->rowpos[h] = rowpos;
       desc->R[h] = R[h];
       desc->tab[h] = sw ? 8 : 0;
     }
   }
   if (kHalves == 1 && t == 0) {
-    desc->rowseq[1] = nullptr;
+    desc->rowbase[1] = p.packed_q;
+    desc->rowpos[1] = 0;
     desc->R[1] = 0;
     desc->tab[1] = 0;
   }
@@ -141,7 +147,7 @@ __device__ __forceinline__ void ka_run_task(const KAParams &p, int lane, int tas
     uint32_t s = 0;
 #pragma unroll
     for (int h = 0; h < kHalves; ++h) {
-      const int c = (col < C[h]) ? (int)((__ldg(colseq[h] + (col >> 4)) >> (2 * (col & 15))) & 3u) : -1;
+      const int c = (col < C[h]) ? packed_code(colbase[h], colpos[h] + col) : -1;
       if constexpr (kPacked) {
         const uint32_t n0 = (c >= 0) ? (uint32_t)(c + 4 * h) : (uint32_t)(8 + 4 * h);
         const uint32_t n1 = (c >= 0) ? (uint32_t)(c + 4 * h + 8) : (uint32_t)(8 + 4 * h);
@@ -188,14 +194,17 @@ __device__ __forceinline__ void ka_run_task(const KAParams &p, int lane, int tas
   T rmax = Cell::splat(0);  // semi: packed max over the row m of each half
 
   // ---- row table words: ring of 4G rows, refilled a batch of G ahead --
+  // The descriptor is re-read (volatile) at every refill so that the
+  // compiler cannot keep it in registers across the hot loop.
+  const volatile KAGroupDesc *vdesc = desc;
   auto fill_batch = [&](int b) {
     const int r = b * G + 1 + t;
     uint2 v = make_uint2(0u, 0u);
 #pragma unroll
     for (int h = 0; h < kHalves; ++h) {
-      if (r <= desc->R[h]) {
-        const uint32_t w = __ldg(desc->rowseq[h] + ((r - 1) >> 4));
-        const uint32_t tw = p.tables[desc->tab[h] + ((w >> (2 * ((r - 1) & 15))) & 3u)];
+      if (r <= vdesc->R[h]) {
+        const uint32_t tw = p.tables[vdesc->tab[h] + packed_code((const uint32_t *)vdesc->rowbase[h],
+                                                                 vdesc->rowpos[h] + (r - 1))];
         if (h == 0) v.x = tw; else v.y = tw;
       }
     }

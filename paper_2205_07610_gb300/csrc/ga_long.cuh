@@ -25,7 +25,7 @@
 namespace ga {
 
 struct KBParams {
-  const uint32_t *packed_q;  // 2-bit codes (alphabets of <= 4), else unused
+  const uint32_t *packed_q;  // flat 2-bit codes (alphabets of <= 4), else unused
   const uint32_t *packed_t;
   const uint8_t *q_codes;    // raw codes (profile path)
   const uint8_t *t_codes;
@@ -81,8 +81,8 @@ __global__ void __launch_bounds__(128) kb_kernel(const __grid_constant__ KBParam
     const int R = inf.x, C = inf.y, sw = inf.z;
     const int64_t qi = p.nt ? p.q0 + pid / p.nt : pid, ti = p.nt ? pid % p.nt : pid;
     const int64_t qs = p.q_off[qi], ts = p.t_off[ti];
-    const int64_t roww = sw ? (ts / 16 + ti) : (qs / 16 + qi);
-    const int64_t colw = sw ? (qs / 16 + qi) : (ts / 16 + ti);
+    const int64_t rowpos = sw ? ts : qs;  // first residue in the flat packed stream
+    const int64_t colpos = sw ? qs : ts;
     const uint32_t *rowbase = sw ? p.packed_t : p.packed_q;
     const uint32_t *colbase = sw ? p.packed_q : p.packed_t;
     const uint8_t *rowraw = sw ? p.t_codes + ts : p.q_codes + qs;
@@ -103,7 +103,7 @@ __global__ void __launch_bounds__(128) kb_kernel(const __grid_constant__ KBParam
       for (int j = 0; j < K; ++j) {
         const int col = col0 + t * K + j;
         if constexpr (!PROFILE) {
-          const int c = (col < C) ? packed_code(colbase, colw, col) : -1;
+          const int c = (col < C) ? packed_code(colbase, colpos + col) : -1;
           const uint32_t n0 = (c >= 0) ? (uint32_t)c : 8u;
           const uint32_t n1 = (c >= 0) ? (uint32_t)(c + 8) : 8u;
           sel[j] = (T)(n0 | (n1 << 4) | (n1 << 8) | (n1 << 12));
@@ -150,7 +150,7 @@ __global__ void __launch_bounds__(128) kb_kernel(const __grid_constant__ KBParam
         uint32_t v;
         if (r > R) v = PROFILE ? (uint32_t)p.A : 0u;
         else if constexpr (PROFILE) v = rowraw[r - 1];
-        else v = p.tables[(sw ? 8 : 0) + packed_code(rowbase, roww, r - 1)];
+        else v = p.tables[(sw ? 8 : 0) + packed_code(rowbase, rowpos + r - 1)];
         row_ring[r & 127] = v;
       };
       load_batch(0);

@@ -59,68 +59,59 @@ __device__ __forceinline__ uint32_t pack4(uint32_t x) {
   return (y | (y >> 12)) & 0xffu;
 }
 
-// Warp per sequence: validate codes < A, pack 2-bit (if packed != nullptr).
-// A sequence whose offsets are decreasing or leave [0, total] (total =
-// off[nseq], the size of the code buffer) is flagged and never touched.
-// Each lane produces one 16-residue word at a time from five aligned 32-bit
-// loads (coalesced across the warp) realigned with funnel shifts; near the
-// end of the buffer, or for a code buffer that is not 4-byte aligned, it
-// falls back to byte loads.
-__global__ void pack_kernel(const uint8_t *codes, const int64_t *off, int64_t nseq, int64_t total,
-                            int A, uint32_t *packed, uint8_t *bad) {
-  const int64_t k = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  const int lane = threadIdx.x & 31;
-  if (k >= nseq) return;
-  const int64_t start = off[k], end = off[k + 1];
-  const int64_t len = end - start;
-  if (len < 0 || start < 0 || end > total) {
-    if (lane == 0) bad[k] = 2;
-    return;
-  }
-  const int64_t word0 = start / 16 + k;
-  const int64_t nwords = (len + 15) / 16;
-  const bool aligned_base = (reinterpret_cast<uintptr_t>(codes) & 3u) == 0;
-  uint32_t mx = 0;  // byte-wise max of the codes seen
-  for (int64_t w = lane; w < nwords; w += 32) {
-    const int64_t s0 = start + w * 16;
-    const int nb = (int)(len - w * 16 < 16 ? len - w * 16 : 16);
+// Flat 2-bit packing of the whole code buffer (residue x -> word x/16),
+// one thread per word with a 16-byte load; any code >= A anywhere raises
+// *invalid (per-sequence validation then runs its slow path).
+__global__ void flat_pack_kernel(const uint8_t *codes, int64_t total, int A, uint32_t *packed,
+                                 int32_t *invalid) {
+  const int64_t nwords = (total + 15) / 16;
+  const bool aligned16 = (reinterpret_cast<uintptr_t>(codes) & 15u) == 0;
+  const uint32_t A4 = (uint32_t)A * 0x01010101u;
+  bool bad = false;
+  for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < nwords;
+       w += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t s0 = w * 16;
     uint32_t x[4];
-    const int64_t a = s0 & ~(int64_t)3;
-    if (aligned_base && a + 20 <= total) {
-      const uint32_t *pa = reinterpret_cast<const uint32_t *>(codes + a);
-      uint32_t v[5];
-#pragma unroll
-      for (int i = 0; i < 5; ++i) v[i] = __ldg(pa + i);
-      const unsigned sh = (unsigned)(s0 & 3) * 8u;
-#pragma unroll
-      for (int i = 0; i < 4; ++i) x[i] = __funnelshift_r(v[i], v[i + 1], sh);
+    if (aligned16 && s0 + 16 <= total) {
+      const uint4 v = __ldg(reinterpret_cast<const uint4 *>(codes + s0));
+      x[0] = v.x; x[1] = v.y; x[2] = v.z; x[3] = v.w;
     } else {
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
         uint32_t acc = 0;
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          const int64_t idx = s0 + 4 * i + j;
-          if (4 * i + j < nb) acc |= (uint32_t)codes[idx] << (8 * j);
-        }
-        x[i] = acc;
+        for (int j = 0; j < 4; ++j)
+          if (s0 + 4 * i + j < total) acc |= (uint32_t)codes[s0 + 4 * i + j] << (8 * j);
+        x[i] = acc;  // bytes past the end are 0, a valid code
       }
     }
     uint32_t word = 0;
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-      const int valid = nb - 4 * i;  // bytes of x[i] inside the sequence
-      const uint32_t keep = valid >= 4 ? 0xffffffffu : (valid <= 0 ? 0u : (0xffffffffu >> (8 * (4 - valid))));
-      const uint32_t xi = x[i] & keep;
-      mx = __vmaxu4(mx, xi);
-      word |= pack4(xi) << (8 * i);
+      bad |= __vcmpgeu4(x[i], A4) != 0u;
+      word |= pack4(x[i]) << (8 * i);
     }
-    if (packed) packed[word0 + w] = word;
+    if (packed) packed[w] = word;
   }
-  mx = __vmaxu4(mx, mx >> 16);
-  mx = __vmaxu4(mx, mx >> 8) & 0xffu;
-  mx = __reduce_max_sync(0xffffffffu, mx);
-  if (lane == 0) bad[k] = (len > 0 && mx >= (unsigned)A) ? 1 : 0;
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(invalid, 1);
+}
+
+// Thread per sequence: 0 ok, 1 residue code >= A, 2 offsets decreasing or
+// outside [0, total].  Residues are scanned only when the packing pass saw
+// an invalid code somewhere.
+__global__ void validate_kernel(const uint8_t *codes, const int64_t *off, int64_t nseq,
+                                int64_t total, int A, const int32_t *invalid, uint8_t *bad) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nseq) return;
+  const int64_t s = off[k], e = off[k + 1];
+  uint8_t b = 0;
+  if (s < 0 || e < s || e > total) {
+    b = 2;
+  } else if (*invalid) {
+    for (int64_t x = s; x < e; ++x)
+      if (codes[x] >= (unsigned)A) { b = 1; break; }
+  }
+  bad[k] = b;
 }
 
 __device__ __forceinline__ int global_gap(int alpha, int beta, int64_t len) {
