@@ -62,6 +62,12 @@ def _load():
         lib.oracle_matrix.argtypes = [u8p, i64, u8p, i64, i32p, i32, i64, i64, i32, i64p, i32p]
         lib.oracle_score_banded.restype = i64
         lib.oracle_score_banded.argtypes = [u8p, i64, u8p, i64, i32p, i32, i64, i64, i64, i64, i32p]
+        lib.oracle_score_blockband.restype = i64
+        lib.oracle_score_blockband.argtypes = [u8p, i64, u8p, i64, i32p, i32, i64, i64, i64, i64,
+                                               i64, i32p]
+        lib.oracle_banded_doubling_blocks.restype = i64
+        lib.oracle_banded_doubling_blocks.argtypes = [u8p, i64, u8p, i64, i32p, i32, i64, i64,
+                                                      i64, i64, i64p, i64p, i32p]
         lib.oracle_band_ub.restype = i64
         lib.oracle_band_ub.argtypes = [i64, i64, i64, i64, i64, i64]
         lib.oracle_banded_doubling.restype = i64
@@ -148,6 +154,37 @@ def score_banded(q, s, matrix, alpha, beta, lo, hi) -> int:
     if err.value:
         raise OracleError(_ERRS.get(err.value, str(err.value)))
     return int(r)
+
+
+def score_blockband(q, s, matrix, alpha, beta, lo, hi, block) -> int:
+    """Global score on the band [lo, hi] rounded out to blocks of `block` columns."""
+    lib = _load()
+    q, qp = _u8(q)
+    s, sp = _u8(s)
+    sig, sgp, A = _sigma(matrix)
+    err = ctypes.c_int32(0)
+    r = lib.oracle_score_blockband(qp, len(q), sp, len(s), sgp, A, int(alpha), int(beta),
+                                   int(lo), int(hi), int(block), ctypes.byref(err))
+    if err.value:
+        raise OracleError(_ERRS.get(err.value, str(err.value)))
+    return int(r)
+
+
+def banded_doubling_blocks(q, s, matrix, alpha, beta, w0, block):
+    """(score, w_used, retries) of band doubling on block-rounded regions."""
+    lib = _load()
+    q, qp = _u8(q)
+    s, sp = _u8(s)
+    sig, sgp, A = _sigma(matrix)
+    err = ctypes.c_int32(0)
+    w = ctypes.c_int64(0)
+    t = ctypes.c_int64(0)
+    r = lib.oracle_banded_doubling_blocks(qp, len(q), sp, len(s), sgp, A, int(alpha), int(beta),
+                                          int(w0), int(block), ctypes.byref(w), ctypes.byref(t),
+                                          ctypes.byref(err))
+    if err.value:
+        raise OracleError(_ERRS.get(err.value, str(err.value)))
+    return int(r), int(w.value), int(t.value)
 
 
 def band_ub(m, n, sigma_max, alpha, beta, d) -> int:

@@ -63,10 +63,33 @@ static inline int64_t max2(int64_t a, int64_t b) { return a > b ? a : b; }
  * an argument or residue error returns 0 and sets *err.
  * lo/hi restrict the DP to diagonals lo <= j-i <= hi when banded != 0.
  */
+/*
+ * Region of a banded DP.  block == 0: the band itself, cells with
+ * lo <= j-i <= hi (row-0 / column-0 initialisation cells included on the
+ * same rule).  block == K > 0: the band rounded out to blocks of K columns
+ * (columns bK+1 .. bK+K): for i, j >= 1 the cell is in the region when
+ * max(1, bK+1-hi) <= i <= min(m, bK+K-lo); a row-0 cell (0, j) when its
+ * block's rows start at 1; a column-0 cell (i, 0) when -i >= lo.  The block
+ * region contains the band, so the band certificate (a bound on every path
+ * that leaves [lo, hi]) holds for it as well.
+ */
+static int in_region(int64_t i, int64_t j, int64_t m, int64_t lo, int64_t hi, int64_t block)
+{
+    if (block <= 0) return (j - i) >= lo && (j - i) <= hi;
+    if (j == 0) return -i >= lo;
+    int64_t b = (j - 1) / block;
+    int64_t r0 = b * block + 1 - hi;
+    if (r0 < 1) r0 = 1;
+    int64_t r1 = b * block + block - lo;
+    if (r1 > m) r1 = m;
+    if (i == 0) return r0 == 1;
+    return i >= r0 && i <= r1;
+}
+
 static int64_t oracle_core(const uint8_t *q, int64_t m, const uint8_t *s, int64_t n,
                            const int32_t *sigma, int32_t A, int64_t alpha, int64_t beta,
                            int32_t mode, int32_t flags, int banded, int64_t lo, int64_t hi,
-                           int64_t *Hout, int32_t *err)
+                           int64_t block, int64_t *Hout, int32_t *err)
 {
     *err = ORACLE_OK;
     if (m < 0 || n < 0 || A <= 0 || mode < 0 || mode > 2 || (m > 0 && !q) || (n > 0 && !s) || !sigma) {
@@ -93,7 +116,7 @@ static int64_t oracle_core(const uint8_t *q, int64_t m, const uint8_t *s, int64_
         return 0;
     }
 
-#define IN_BAND(i, j) (!banded || (((j) - (i)) >= lo && ((j) - (i)) <= hi))
+#define IN_BAND(i, j) (!banded || in_region((i), (j), m, lo, hi, block))
 
     /* Row 0 (paper's initialisation tables). */
     Hprev[0] = IN_BAND(0, 0) ? 0 : NEG;           /* H(0,0) = 0 */
@@ -167,14 +190,14 @@ int64_t oracle_score_ex(const uint8_t *q, int64_t m, const uint8_t *s, int64_t n
                         const int32_t *sigma, int32_t A, int64_t alpha, int64_t beta,
                         int32_t mode, int32_t flags, int32_t *err)
 {
-    return oracle_core(q, m, s, n, sigma, A, alpha, beta, mode, flags, 0, 0, 0, NULL, err);
+    return oracle_core(q, m, s, n, sigma, A, alpha, beta, mode, flags, 0, 0, 0, 0, NULL, err);
 }
 
 int64_t oracle_score(const uint8_t *q, int64_t m, const uint8_t *s, int64_t n,
                      const int32_t *sigma, int32_t A, int64_t alpha, int64_t beta,
                      int32_t mode, int32_t *err)
 {
-    return oracle_core(q, m, s, n, sigma, A, alpha, beta, mode, 0, 0, 0, 0, NULL, err);
+    return oracle_core(q, m, s, n, sigma, A, alpha, beta, mode, 0, 0, 0, 0, 0, NULL, err);
 }
 
 /* Score plus the full (m+1) x (n+1) H matrix, row-major (small inputs). */
@@ -182,7 +205,7 @@ int64_t oracle_matrix(const uint8_t *q, int64_t m, const uint8_t *s, int64_t n,
                       const int32_t *sigma, int32_t A, int64_t alpha, int64_t beta,
                       int32_t mode, int64_t *Hout, int32_t *err)
 {
-    return oracle_core(q, m, s, n, sigma, A, alpha, beta, mode, 0, 0, 0, 0, Hout, err);
+    return oracle_core(q, m, s, n, sigma, A, alpha, beta, mode, 0, 0, 0, 0, 0, Hout, err);
 }
 
 /* Global score restricted to diagonals lo <= j-i <= hi (-inf outside). */
@@ -190,7 +213,16 @@ int64_t oracle_score_banded(const uint8_t *q, int64_t m, const uint8_t *s, int64
                             const int32_t *sigma, int32_t A, int64_t alpha, int64_t beta,
                             int64_t lo, int64_t hi, int32_t *err)
 {
-    return oracle_core(q, m, s, n, sigma, A, alpha, beta, ORACLE_GLOBAL, 0, 1, lo, hi, NULL, err);
+    return oracle_core(q, m, s, n, sigma, A, alpha, beta, ORACLE_GLOBAL, 0, 1, lo, hi, 0, NULL, err);
+}
+
+/* Global score on the band [lo, hi] rounded out to blocks of `block` columns. */
+int64_t oracle_score_blockband(const uint8_t *q, int64_t m, const uint8_t *s, int64_t n,
+                               const int32_t *sigma, int32_t A, int64_t alpha, int64_t beta,
+                               int64_t lo, int64_t hi, int64_t block, int32_t *err)
+{
+    return oracle_core(q, m, s, n, sigma, A, alpha, beta, ORACLE_GLOBAL, 0, 1, lo, hi, block, NULL,
+                       err);
 }
 
 /*
@@ -218,9 +250,31 @@ int64_t oracle_band_ub(int64_t m, int64_t n, int64_t sigma_max, int64_t alpha, i
  * accepted w, the number of retries and the number of banded cells
  * evaluated over all attempts.
  */
+static int64_t doubling_core(const uint8_t *q, int64_t m, const uint8_t *s, int64_t n,
+                             const int32_t *sigma, int32_t A, int64_t alpha, int64_t beta,
+                             int64_t w0, int64_t block, int64_t *w_used, int64_t *retries,
+                             int32_t *err);
+
 int64_t oracle_banded_doubling(const uint8_t *q, int64_t m, const uint8_t *s, int64_t n,
                                const int32_t *sigma, int32_t A, int64_t alpha, int64_t beta,
                                int64_t w0, int64_t *w_used, int64_t *retries, int32_t *err)
+{
+    return doubling_core(q, m, s, n, sigma, A, alpha, beta, w0, 0, w_used, retries, err);
+}
+
+/* Band doubling on block-rounded regions (the GPU's region shape). */
+int64_t oracle_banded_doubling_blocks(const uint8_t *q, int64_t m, const uint8_t *s, int64_t n,
+                                      const int32_t *sigma, int32_t A, int64_t alpha,
+                                      int64_t beta, int64_t w0, int64_t block, int64_t *w_used,
+                                      int64_t *retries, int32_t *err)
+{
+    return doubling_core(q, m, s, n, sigma, A, alpha, beta, w0, block, w_used, retries, err);
+}
+
+static int64_t doubling_core(const uint8_t *q, int64_t m, const uint8_t *s, int64_t n,
+                             const int32_t *sigma, int32_t A, int64_t alpha, int64_t beta,
+                             int64_t w0, int64_t block, int64_t *w_used, int64_t *retries,
+                             int32_t *err)
 {
     int64_t smax = GA_ORACLE_NEG;
     for (int32_t a = 0; a < A * A; ++a) smax = max2(smax, sigma[a]);
@@ -230,7 +284,8 @@ int64_t oracle_banded_doubling(const uint8_t *q, int64_t m, const uint8_t *s, in
     for (;;) {
         int64_t lo = (dn < 0 ? dn : 0) - w;
         int64_t hi = (dn > 0 ? dn : 0) + w;
-        int64_t sc = oracle_score_banded(q, m, s, n, sigma, A, alpha, beta, lo, hi, err);
+        int64_t sc = oracle_core(q, m, s, n, sigma, A, alpha, beta, ORACLE_GLOBAL, 0, 1, lo, hi,
+                                 block, NULL, err);
         if (*err) return 0;
         int covers = (lo <= -m) && (hi >= n);
         int64_t ub = GA_ORACLE_NEG;

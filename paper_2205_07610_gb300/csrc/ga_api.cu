@@ -6,6 +6,7 @@
 #include <mutex>
 #include <vector>
 
+#include "ga_banded.cuh"
 #include "ga_launch.h"
 #include "ga_prep.cuh"
 
@@ -147,6 +148,8 @@ struct Small {
   int32_t rerun_range[2];
   int32_t scan_partials[kScanTiles];
   int32_t invalid_q, invalid_t;
+  unsigned long long band_retries, band_cells;
+  int32_t max_rows;
 };
 
 struct Readback {
@@ -616,14 +619,114 @@ int ga_align_long(const uint8_t *q, int64_t m, const uint8_t *t, int64_t n, cons
   return rc;
 }
 
+__global__ void fill_i32_kernel(int32_t *p, int64_t n, int32_t v) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) p[i] = v;
+}
+
 int ga_align_banded(const uint8_t *q_codes, const int64_t *q_off, const uint8_t *t_codes,
                     const int64_t *t_off, int64_t npairs, const ga_scoring *scoring, const int32_t *w0,
                     int32_t default_w0, int32_t *scores, int32_t *w_used, void *stream, ga_stats *stats) {
-  (void)w0;
-  (void)default_w0;
-  (void)w_used;
-  // Placeholder until the banded kernel lands: exact full-DP global scores.
-  return batch_impl(q_codes, q_off, t_codes, t_off, npairs, scoring, GA_GLOBAL, scores, stream, stats, 0);
+  if (npairs < 0 || default_w0 < 0) return GA_ERR_ARG;
+  if (npairs > 0 && (!q_codes || !q_off || !t_codes || !t_off || !scores)) return GA_ERR_ARG;
+  if (npairs >= (1ll << 31) - 64) return GA_ERR_ARG;
+  Call c((cudaStream_t)stream);
+  int rc = check_scoring(scoring, &c.sc);
+  if (rc) return rc;
+  c.mode = GA_GLOBAL;
+  if (c.sc.A > 4) {
+    // Larger alphabets: exact full DP, no band (w_used = -1).
+    rc = batch_impl(q_codes, q_off, t_codes, t_off, npairs, scoring, GA_GLOBAL, scores, stream, stats, 0);
+    if (!rc && w_used && npairs > 0) {
+      fill_i32_kernel<<<(unsigned)((npairs + 255) / 256), 256, 0, c.s>>>(w_used, npairs, -1);
+      if (cudaGetLastError() != cudaSuccess) rc = GA_ERR_CUDA;
+    }
+    return rc;
+  }
+  c.timing = stats != nullptr;
+  Events ev(stats != nullptr, c.s);
+  if ((rc = setup(c))) return rc;
+  if (npairs == 0) return finish(c, stats, ev.e0, ev.e1, 0);
+  SetView Q{q_codes, q_off, nullptr, nullptr}, T{t_codes, t_off, nullptr, nullptr};
+  if ((rc = prepare_set(c, q_codes, q_off, npairs, &Q.packed, &Q.bad, &c.small->invalid_q))) return rc;
+  if ((rc = prepare_set(c, t_codes, t_off, npairs, &T.packed, &T.bad, &c.small->invalid_t))) return rc;
+  uint32_t *keys = c.al.get<uint32_t>((size_t)npairs);
+  int32_t *sorted = c.al.get<int32_t>((size_t)npairs);
+  if (c.al.failed) return GA_ERR_OOM;
+  if (cudaMemsetAsync(c.hist, 0, sizeof(int32_t) * kNumKeys, c.s) != cudaSuccess) return GA_ERR_CUDA;
+  BandPlanParams bp{};
+  bp.q_off = q_off;
+  bp.t_off = t_off;
+  bp.npairs = npairs;
+  bp.qbad = Q.bad;
+  bp.tbad = T.bad;
+  bp.w0 = w0;
+  bp.default_w0 = default_w0;
+  bp.alpha = c.sc.alpha;
+  bp.beta = c.sc.beta;
+  bp.scores = scores;
+  bp.w_used = w_used;
+  bp.keys = keys;
+  bp.status = &c.small->status;
+  bp.cells = &c.small->cells;
+  bp.max_rows = &c.small->max_rows;
+  const unsigned nb = (unsigned)((npairs + 255) / 256);
+  band_plan_kernel<<<nb, 256, 0, c.s>>>(bp);
+  hist_kernel<<<nb, 256, 0, c.s>>>(keys, npairs, c.hist);
+  scan_partials_kernel<<<kScanTiles, kScanTile, 0, c.s>>>(c.hist, c.small->scan_partials);
+  scan_apply_kernel<<<kScanTiles, kScanTile, 0, c.s>>>(c.hist, c.small->scan_partials, c.cursor,
+                                                       c.small->ranges);
+  scatter_kernel<<<nb, 256, 0, c.s>>>(keys, npairs, c.cursor, sorted);
+  c.launches += 5;
+  if (cudaGetLastError() != cudaSuccess) return GA_ERR_CUDA;
+  int32_t *h = (int32_t *)pinned_scratch();
+  if (cudaMemcpyAsync(h, &c.small->max_rows, sizeof(int32_t), cudaMemcpyDeviceToHost, c.s) != cudaSuccess ||
+      cudaStreamSynchronize(c.s) != cudaSuccess)
+    return GA_ERR_CUDA;
+  const int max_rows = h[0];
+  if (max_rows > 0) {
+    const int occ = std::max(blocks_per_sm_kc(), 1);
+    const int64_t want = (npairs + kKcWarps - 1) / kKcWarps;
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)c.nsm * occ));
+    const int64_t stride = (int64_t)max_rows + 128;
+    int2 *bnd = c.al.get<int2>((size_t)grid * kKcWarps * (size_t)stride);
+    if (c.al.failed) return GA_ERR_OOM;
+    KCParams kc{};
+    kc.packed_q = Q.packed;
+    kc.packed_t = T.packed;
+    kc.q_off = q_off;
+    kc.t_off = t_off;
+    kc.order = sorted;
+    kc.range = c.small->ranges;  // class 0, bin 0: every non-trivial pair
+    kc.task_counter = &c.small->counters[0];
+    std::memcpy(kc.tables, c.sc.tables, sizeof(kc.tables));
+    kc.alpha = c.sc.alpha;
+    kc.beta = c.sc.beta;
+    kc.sigma_max_pos = std::max(c.sc.smax, 0);
+    kc.w0 = w0;
+    kc.default_w0 = default_w0;
+    kc.scores = scores;
+    kc.w_used = w_used;
+    kc.retries = &c.small->band_retries;
+    kc.cells = &c.small->band_cells;
+    kc.bnd = bnd;
+    kc.bnd_stride = stride;
+    c.dp_begin();
+    const cudaError_t e = launch_kc(kc, grid, c.s);
+    c.dp_end();
+    if (e != cudaSuccess) return GA_ERR_CUDA;
+  }
+  rc = finish(c, stats, ev.e0, ev.e1, npairs);
+  if (!rc && stats) {
+    unsigned long long *hb = (unsigned long long *)pinned_scratch();
+    if (cudaMemcpyAsync(hb, &c.small->band_retries, 2 * sizeof(unsigned long long),
+                        cudaMemcpyDeviceToHost, c.s) != cudaSuccess ||
+        cudaStreamSynchronize(c.s) != cudaSuccess)
+      return GA_ERR_CUDA;
+    stats->band_retries = (int64_t)hb[0];
+    stats->banded_cells = (int64_t)hb[1];
+  }
+  return rc;
 }
 
 const char *ga_strerror(int code) {

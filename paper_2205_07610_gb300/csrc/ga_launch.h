@@ -19,6 +19,10 @@ constexpr int kKaThreads = 128;
 
 // Long kernel: 32 lanes x 16 columns per stage.
 constexpr int kKbK = 16;
+// Banded kernel: 32 lanes x 16 columns per stage, 16-column band blocks.
+constexpr int kKcK = 16;
+constexpr int kKcThreads = 128;
+constexpr int kKcWarps = kKcThreads / 32;
 constexpr int kKbThreads = 128;
 constexpr int kKbWarps = kKbThreads / 32;
 
@@ -43,6 +47,10 @@ GA_KB_DECLARE(kb_semi_sel)
 GA_KB_DECLARE(kb_local_prof)
 GA_KB_DECLARE(kb_global_prof)
 GA_KB_DECLARE(kb_semi_prof)
+
+struct KCParams;
+cudaError_t launch_kc(const KCParams &p, int grid, cudaStream_t s);
+int blocks_per_sm_kc();
 
 #define GA_KA_OCC(CELL, MODE, K)                                                             \
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, ka_kernel<CELL, MODE, kKaG, K>, kKaThreads, 0)

@@ -189,6 +189,62 @@ __global__ void plan_kernel(PlanParams p) {
   if ((threadIdx.x & 31) == 0 && my_cells) atomicAdd(p.cells, my_cells);
 }
 
+// Banded path: invalid / empty pairs are finished here, the others are
+// keyed by estimated work m * (|n-m| + 2 w0 + 1), largest first.
+struct BandPlanParams {
+  const int64_t *q_off;
+  const int64_t *t_off;
+  int64_t npairs;
+  const uint8_t *qbad;
+  const uint8_t *tbad;
+  const int32_t *w0;
+  int32_t default_w0;
+  int32_t alpha, beta;
+  int32_t *scores;
+  int32_t *w_used;
+  uint32_t *keys;
+  int32_t *status;
+  unsigned long long *cells;
+  int32_t *max_rows;
+};
+
+__global__ void band_plan_kernel(BandPlanParams p) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  unsigned long long my_cells = 0;
+  if (i < p.npairs) {
+    const int64_t m = p.q_off[i + 1] - p.q_off[i], n = p.t_off[i + 1] - p.t_off[i];
+    int w = p.w0 ? p.w0[i] : p.default_w0;
+    if (w < 0) w = 0;
+    uint32_t key = 0xffffffffu;
+    if (p.qbad[i] || p.tbad[i] || m < 0 || n < 0) {
+      p.scores[i] = INT32_MIN;
+      if (p.w_used) p.w_used[i] = -1;
+      set_status(p.status, (p.qbad[i] == 2 || p.tbad[i] == 2) ? GA_ERR_ARG : GA_ERR_RESIDUE);
+    } else if (m >= (1ll << 30) || n >= (1ll << 30) ||
+               2 * (int64_t)p.alpha + (int64_t)p.beta * (m + n) + 127 * (m < n ? m : n) >= (1ll << 30)) {
+      p.scores[i] = INT32_MIN;
+      if (p.w_used) p.w_used[i] = -1;
+      set_status(p.status, GA_ERR_RANGE);
+    } else if (m == 0 || n == 0) {
+      p.scores[i] = global_gap(p.alpha, p.beta, m + n);
+      if (p.w_used) p.w_used[i] = w;
+    } else {
+      my_cells = (unsigned long long)(m * n);
+      atomicMax(p.max_rows, (int)m);
+      const int64_t d = n - m;
+      const unsigned long long est =
+          (unsigned long long)m * (unsigned long long)((d < 0 ? -d : d) + 2 * (int64_t)w + 1);
+      const int lg = 63 - __clzll((long long)est);
+      const int bucket = lg >= 5 ? lg * 32 + (int)((est >> (lg - 5)) & 31u) : (int)est;
+      key = (uint32_t)(kRBuckets - 1 - ::min(bucket, kRBuckets - 1));
+    }
+    p.keys[i] = key;
+  }
+#pragma unroll
+  for (int off = 16; off >= 1; off >>= 1) my_cells += __shfl_xor_sync(0xffffffffu, my_cells, off);
+  if ((threadIdx.x & 31) == 0 && my_cells) atomicAdd(p.cells, my_cells);
+}
+
 __global__ void hist_kernel(const uint32_t *keys, int64_t n, int32_t *hist) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;

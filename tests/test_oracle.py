@@ -275,3 +275,66 @@ def test_band_doubling_is_exact():
             # one below the minimum does not certify: doubling must move on
             sc2, w2, tries2 = oracle.banded_doubling(q, t, b.matrix, 5, 2, wmin - 1)
             assert tries2 >= 1 and sc2 == full
+
+
+def _in_block_region(i, j, m, lo, hi, K):
+    # the band [lo, hi] rounded out to blocks of K columns (written from the
+    # definition independently of the C predicate)
+    if j == 0:
+        return -i >= lo
+    b = (j - 1) // K
+    first = max(1, b * K + 1 - hi)
+    last = min(m, b * K + K - lo)
+    if i == 0:
+        return first == 1
+    return first <= i <= last
+
+
+def _brute_region(q, s, sig, alpha, beta, member):
+    al = brute.alignments(len(q), len(s))
+    sc = brute.global_scores(q, s, sig, alpha, beta)
+    best = None
+    for k, ops in enumerate(al):
+        i = j = 0
+        ok = member(0, 0)
+        for op in ops:
+            i += op in "MD"
+            j += op in "MI"
+            ok = ok and member(i, j)
+        if ok:
+            best = int(sc[k]) if best is None else max(best, int(sc[k]))
+    return best
+
+
+def test_block_region_vs_path_restricted_brute():
+    rng = np.random.default_rng(43)
+    sig = synth.dna_matrix(2, -3)
+    for _ in range(60):
+        m, n = rng.integers(1, 6, size=2)
+        q, s = _dna(rng, m), _dna(rng, n)
+        dn = n - m
+        w = int(rng.integers(0, 3))
+        lo, hi = min(0, dn) - w, max(0, dn) + w
+        K = int(rng.integers(1, 4))
+        want = _brute_region(q, s, sig, 5, 2, lambda i, j: _in_block_region(i, j, m, lo, hi, K))
+        assert oracle.score_blockband(q, s, sig, 5, 2, lo, hi, K) == want
+
+
+def test_block_region_contains_band_and_certifies_no_later():
+    b = synth.long_dna_pairs(npairs=10, lmin=80, lmax=250, seed=12)
+    for p in range(b.npairs):
+        q = b.q_codes[b.q_off[p]:b.q_off[p + 1]]
+        t = b.t_codes[b.t_off[p]:b.t_off[p + 1]]
+        m, n = len(q), len(t)
+        full = oracle.score(q, t, b.matrix, 5, 2, "global")
+        for w in (0, 3, 10):
+            lo, hi = min(0, n - m) - w, max(0, n - m) + w
+            strict = oracle.score_banded(q, t, b.matrix, 5, 2, lo, hi)
+            block = oracle.score_blockband(q, t, b.matrix, 5, 2, lo, hi, 16)
+            assert strict <= block <= full
+        assert oracle.score_blockband(q, t, b.matrix, 5, 2, -m, n, 16) == full
+        for w0 in (0, 4, 32):
+            sc, w_used, _ = oracle.banded_doubling_blocks(q, t, b.matrix, 5, 2, w0, 16)
+            sc2, w_strict, _ = oracle.banded_doubling(q, t, b.matrix, 5, 2, w0)
+            assert sc == full == sc2
+            assert w0 <= w_used <= max(w_strict, w0)
