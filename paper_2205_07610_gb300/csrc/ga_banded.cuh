@@ -178,8 +178,8 @@ __global__ void __launch_bounds__(128) kc_kernel(const __grid_constant__ KCParam
             __syncwarp();
             load_batch(it / 32 + 1);
             fill_rows(it / 32 + 2);
-            if (it >= 64) {  // flush lane-31 rows r_lo + it - 63 .. r_lo + it - 32
-              const int r = r_lo + it - 63 + t;
+            if (it >= 64) {  // flush lane-31 rows r_lo + it - 64 .. r_lo + it - 33
+              const int r = r_lo + it - 64 + t;
               bnd[r] = out_ring[(r - r_lo) & 63];
             }
             __syncwarp();
