@@ -54,7 +54,27 @@ def parse_args():
 
 
 def workload(npairs: int, rank: int):
-    return synth.mutated_dna_pairs(npairs=npairs, seed=synth.SEED_BASE + 2 + 1000 * rank)
+    """Each rank aligns its own seeded batch of the same shape (weak scaling)."""
+    return synth.mutated_dna_pairs(npairs=npairs, seed=shard_seed(rank))
+
+
+def shard_seed(rank: int) -> int:
+    return synth.SEED_BASE + 2 + 1000 * rank
+
+
+def reduce_max(value: float, dist=None, device=None) -> float:
+    """Max over ranks (a step lasts as long as its slowest rank)."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_gcups(cells_per_rank_step: int, world: int, steps: int, max_ms: float) -> float:
+    """Cells of all ranks over the slowest rank's time, in GCUPS."""
+    return cells_per_rank_step * world * steps / (max_ms / 1e3) / 1e9
 
 
 class ClockSampler:
@@ -261,14 +281,10 @@ def main():
         torch.cuda.synchronize(dev)
         clk.mark_end()
         barrier()
-    ms = ev0.elapsed_time(ev1)
+    ms = reduce_max(ev0.elapsed_time(ev1), dist, dev)
     clocks = clk.summary()
-    if dist is not None:
-        tms = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(tms, op=dist.ReduceOp.MAX)
-        ms = float(tms.item())
     ms_per_step = ms / args.steps
-    value = step_cells * world * args.steps / (ms / 1e3) / 1e9
+    value = whole_job_gcups(step_cells, world, args.steps, ms)
 
     status = [s["status"] for pair in sts for s in pair]
     dp_ms = sum(s["dp_ms"] for pair in sts for s in pair)
@@ -314,11 +330,7 @@ def main():
         for _ in range(args.steps):
             hstep()
         barrier()
-        et = time.perf_counter() - t0
-        if dist is not None:
-            tt = torch.tensor([et], device=dev, dtype=torch.float64)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            et = float(tt.item())
+        et = reduce_max(time.perf_counter() - t0, dist, dev)
         assert torch.equal(hs1, s_glob.cpu()) and torch.equal(hs2, s_semi.cpu())
         h2d = 2 * (hq.numel() + ht.numel() + 8 * (hqo.numel() + hto.numel()))
         e2e = {"value": step_cells * world * args.steps / et / 1e9, "unit": "GCUPS",
