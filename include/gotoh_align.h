@@ -169,9 +169,18 @@ int ga_align_long(const uint8_t *q, int64_t m, const uint8_t *t, int64_t n,
  *     UB(d) = max(sigma_max,0) * (m+n-g)/2 - (alpha*r + beta*(g-r)),
  *     g = |d| + |d-(n-m)| gap residues in r >= 1 (2 outside the main
  *     diagonals) runs.
- * Otherwise w doubles; a band covering the matrix is the full DP.
+ * Otherwise w <- max(1, 2w); a band covering the matrix is the full DP.
+ * The kernel evaluates the band rounded out to blocks of 16 target columns
+ * (block b = columns 16b+1 .. 16b+16 runs rows max(1, 16b+1-hi) ..
+ * min(m, 16b+16-lo)); the rounded region contains the band, so the bound
+ * above still certifies it, and it can only accept at a smaller w.
  *   scores : device int32[npairs] -- exact global scores
- *   w_used : device int32[npairs] or NULL -- the accepted w per pair
+ *   w_used : device int32[npairs] or NULL -- the accepted w per pair; -1
+ *            for pairs that ran as full DP (alphabets of more than 4
+ *            symbols, where no banded kernel exists)
+ *   w0     : entries < 0 are taken as 0
+ * Errors as for ga_align_batch; stats->band_retries and ->banded_cells
+ * count doublings and evaluated region cells.
  */
 int ga_align_banded(const uint8_t *q_codes, const int64_t *q_off, const uint8_t *t_codes,
                     const int64_t *t_off, int64_t npairs, const ga_scoring *scoring,
