@@ -9,6 +9,8 @@ recurrence of Sec. 2.1 of the AnySeq/GPU paper: Eqs. H, E, F and the printed
 initialisation tables).  This module compiles it with gcc on first use and
 wraps it with ctypes.  ``oracle.brute`` is an independent brute-force
 enumerator of all alignments used to pin the DP on tiny inputs.
+``oracle.band_features`` and ``oracle.mlp`` define the band predictor's pair
+features and its network (float64) and are pinned by tests/test_band_oracle.py.
 
 Every function here is parity-pinned by tests/test_oracle.py (brute force,
 closed forms, invariants, hand-worked tables); none is "parity unpinned".
@@ -75,6 +77,9 @@ def _load():
                                                i64p, i64p, i32p]
         lib.oracle_min_certified_w.restype = i64
         lib.oracle_min_certified_w.argtypes = [u8p, i64, u8p, i64, i32p, i32, i64, i64, i32p]
+        lib.oracle_min_certified_w_blocks.restype = i64
+        lib.oracle_min_certified_w_blocks.argtypes = [u8p, i64, u8p, i64, i32p, i32, i64, i64, i64,
+                                                      i32p]
         lib.oracle_batch.restype = i32
         lib.oracle_batch.argtypes = [u8p, i64p, u8p, i64p, i64, i32p, i32, i64, i64, i32, i64p,
                                      i32p, i32]
@@ -216,6 +221,20 @@ def min_certified_w(q, s, matrix, alpha, beta) -> int:
     err = ctypes.c_int32(0)
     r = lib.oracle_min_certified_w(qp, len(q), sp, len(s), sgp, A, int(alpha), int(beta),
                                    ctypes.byref(err))
+    if err.value:
+        raise OracleError(_ERRS.get(err.value, str(err.value)))
+    return int(r)
+
+
+def min_certified_w_blocks(q, s, matrix, alpha, beta, block) -> int:
+    """Smallest w whose band, rounded out to blocks of `block` columns, certifies."""
+    lib = _load()
+    q, qp = _u8(q)
+    s, sp = _u8(s)
+    sig, sgp, A = _sigma(matrix)
+    err = ctypes.c_int32(0)
+    r = lib.oracle_min_certified_w_blocks(qp, len(q), sp, len(s), sgp, A, int(alpha), int(beta),
+                                          int(block), ctypes.byref(err))
     if err.value:
         raise OracleError(_ERRS.get(err.value, str(err.value)))
     return int(r)

@@ -301,11 +301,13 @@ static int64_t doubling_core(const uint8_t *q, int64_t m, const uint8_t *s, int6
     }
 }
 
-/* Smallest w >= 0 whose band certifies (the certificate is monotone in w:
- * the banded score can only grow and the outside bound only shrink). */
-int64_t oracle_min_certified_w(const uint8_t *q, int64_t m, const uint8_t *s, int64_t n,
-                               const int32_t *sigma, int32_t A, int64_t alpha, int64_t beta,
-                               int32_t *err)
+/* Smallest w >= 0 whose band (block == 0) or block-rounded band region
+ * (block > 0) certifies, by bisection over w.  The certificate is monotone
+ * in w: the region only grows with w, so its score can only grow, and the
+ * bound of the nearest outside diagonals only shrinks. */
+static int64_t min_w_core(const uint8_t *q, int64_t m, const uint8_t *s, int64_t n,
+                          const int32_t *sigma, int32_t A, int64_t alpha, int64_t beta,
+                          int64_t block, int32_t *err)
 {
     int64_t smax = GA_ORACLE_NEG;
     for (int32_t a = 0; a < A * A; ++a) smax = max2(smax, sigma[a]);
@@ -315,7 +317,8 @@ int64_t oracle_min_certified_w(const uint8_t *q, int64_t m, const uint8_t *s, in
         int64_t w = lo_w + (hi_w - lo_w) / 2;
         int64_t lo = (dn < 0 ? dn : 0) - w;
         int64_t hi = (dn > 0 ? dn : 0) + w;
-        int64_t sc = oracle_score_banded(q, m, s, n, sigma, A, alpha, beta, lo, hi, err);
+        int64_t sc = oracle_core(q, m, s, n, sigma, A, alpha, beta, ORACLE_GLOBAL, 0, 1, lo, hi,
+                                 block, NULL, err);
         if (*err) return -1;
         int covers = (lo <= -m) && (hi >= n);
         int64_t ub = GA_ORACLE_NEG;
@@ -325,6 +328,20 @@ int64_t oracle_min_certified_w(const uint8_t *q, int64_t m, const uint8_t *s, in
         else lo_w = w + 1;
     }
     return lo_w;
+}
+
+int64_t oracle_min_certified_w(const uint8_t *q, int64_t m, const uint8_t *s, int64_t n,
+                               const int32_t *sigma, int32_t A, int64_t alpha, int64_t beta,
+                               int32_t *err)
+{
+    return min_w_core(q, m, s, n, sigma, A, alpha, beta, 0, err);
+}
+
+int64_t oracle_min_certified_w_blocks(const uint8_t *q, int64_t m, const uint8_t *s, int64_t n,
+                                      const int32_t *sigma, int32_t A, int64_t alpha,
+                                      int64_t beta, int64_t block, int32_t *err)
+{
+    return min_w_core(q, m, s, n, sigma, A, alpha, beta, block, err);
 }
 
 /* ---------------------------------------------------------------------

@@ -12,10 +12,11 @@ from .tables import (DNA_ALPHABET, PROTEIN_ALPHABET, BLOSUM62, PROTEIN_BACKGROUN
 from .workloads import (SEED_BASE, Batch, CrossBatch, Stream, pack_csr, uniform_dna_pairs,
                         mutated_dna_pairs, protein_database, long_dna_pairs, serving_stream,
                         random_sequences, mutate)
+from .band import NPARAMS as MLP_NPARAMS, mlp_init, minibatches
 
 __all__ = [
     "DNA_ALPHABET", "PROTEIN_ALPHABET", "BLOSUM62", "PROTEIN_BACKGROUND", "dna_matrix",
     "blosum62", "encode", "SEED_BASE", "Batch", "CrossBatch", "Stream", "pack_csr",
     "uniform_dna_pairs", "mutated_dna_pairs", "protein_database", "long_dna_pairs",
-    "serving_stream", "random_sequences", "mutate",
+    "serving_stream", "random_sequences", "mutate", "MLP_NPARAMS", "mlp_init", "minibatches",
 ]
