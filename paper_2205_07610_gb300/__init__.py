@@ -10,12 +10,15 @@ costs gap_open + (k-1) * gap_extend).
 from ._binding import (LOCAL, GLOBAL, SEMIGLOBAL, EXPORTED, GotohError, Scoring, Stats,
                        align_banded, align_batch, align_batch_host, align_cross, align_long,
                        align_long_noalloc, NOALLOC_MAX_LEN, PROBES, probe_issue_rate,
-                       lib_path, load, make_scoring, strerror, version)
+                       lib_path, load, make_scoring, strerror, version, BAND_NFEAT, MLP_NPARAMS,
+                       band_features, band_min_w, band_predict, mlp_forward, mlp_loss_grad,
+                       mlp_train, mlp_cast)
 from .build import build
 
 __all__ = [
     "LOCAL", "GLOBAL", "SEMIGLOBAL", "EXPORTED", "GotohError", "Scoring", "Stats", "align_banded",
     "align_batch", "align_batch_host", "align_cross", "align_long", "align_long_noalloc",
     "NOALLOC_MAX_LEN", "PROBES", "probe_issue_rate", "lib_path", "load",
-    "make_scoring", "strerror", "version", "build",
+    "make_scoring", "strerror", "version", "build", "BAND_NFEAT", "MLP_NPARAMS", "band_features",
+    "band_min_w", "band_predict", "mlp_forward", "mlp_loss_grad", "mlp_train", "mlp_cast",
 ]

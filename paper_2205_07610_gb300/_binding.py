@@ -29,7 +29,10 @@ GA_ERR_RANGE = 7
 # Symbols declared in include/gotoh_align.h (checked by the CPU tests).
 EXPORTED = ("ga_align_batch", "ga_align_batch_host", "ga_align_cross", "ga_align_long",
             "ga_align_long_noalloc", "ga_align_banded", "ga_strerror", "ga_version",
-            "ga_probe_issue_rate")
+            "ga_probe_issue_rate", "ga_band_features", "ga_band_min_w", "ga_band_predict",
+            "ga_mlp_forward", "ga_mlp_loss_grad", "ga_mlp_train", "ga_mlp_cast")
+BAND_NFEAT = 32
+MLP_NPARAMS = 6337
 PROBES = {"vadd2": 0, "vmaxs2": 1, "viaddmax_s16x2": 2, "vimax3_s16x2": 3,
           "viaddmax_s16x2_relu": 4, "prmt": 5, "iadd": 6, "imax": 7, "viaddmax_s32": 8,
           "vimax3_s32": 9, "imad": 10, "lop3": 11, "hadd2": 12, "hmax2": 13, "cell": 14}
@@ -88,8 +91,18 @@ def load(build_if_missing: bool = False):
     lib.ga_align_long.argtypes = [P, i64, P, i64, sp, i32, P, P, stp]
     lib.ga_align_banded.argtypes = [P, P, P, P, i64, sp, P, i32, P, P, P, stp]
     lib.ga_align_long_noalloc.argtypes = [P, i64, P, i64, sp, i32, P, P]
+    f32 = ctypes.c_float
+    lib.ga_band_features.argtypes = [P, P, P, P, i64, P, P, stp]
+    lib.ga_band_min_w.argtypes = [P, P, P, P, i64, sp, P, P, P, stp]
+    lib.ga_band_predict.argtypes = [P, P, P, P, i64, P, f32, P, P, P, stp]
+    lib.ga_mlp_forward.argtypes = [P, P, i64, P, P]
+    lib.ga_mlp_loss_grad.argtypes = [P, P, P, i32, P, P, P]
+    lib.ga_mlp_train.argtypes = [P, P, P, P, P, P, i64, P, i32, i32, i32, f32, f32, f32, f32, P, P]
+    lib.ga_mlp_cast.argtypes = [P, P, P]
     for f in ("ga_align_batch", "ga_align_batch_host", "ga_align_cross", "ga_align_long",
-              "ga_align_long_noalloc", "ga_align_banded"):
+              "ga_align_long_noalloc", "ga_align_banded", "ga_band_features", "ga_band_min_w",
+              "ga_band_predict", "ga_mlp_forward", "ga_mlp_loss_grad", "ga_mlp_train",
+              "ga_mlp_cast"):
         getattr(lib, f).restype = i32
     lib.ga_probe_issue_rate.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                         ctypes.POINTER(ctypes.c_float),
@@ -273,3 +286,128 @@ def align_banded(q_codes, q_off, t_codes, t_off, matrix, gap_open, gap_extend, w
     if rc:
         raise GotohError(rc, "ga_align_banded")
     return (scores, w_used, st.as_dict()) if stats else (scores, w_used)
+
+
+def _check_dtype(t, dtype, n=None, what=""):
+    _check_dev(t)
+    if t.dtype != dtype or (n is not None and t.numel() != n):
+        raise TypeError(f"{what}: expected {dtype} with {n} elements")
+
+
+def band_features(q_codes, q_off, t_codes, t_off, out=None, stream=None, stats: bool = False):
+    """float32[npairs, 32] pair features of the band predictor (DNA pairs)."""
+    import torch
+    _check_dev(q_codes, q_off, t_codes, t_off)
+    npairs = q_off.numel() - 1
+    if out is None:
+        out = torch.empty((max(npairs, 0), BAND_NFEAT), dtype=torch.float32, device=q_codes.device)
+    st = Stats()
+    rc = load().ga_band_features(_ptr(q_codes), _ptr(q_off), _ptr(t_codes), _ptr(t_off), npairs,
+                                 _ptr(out), _stream_ptr(stream), ctypes.byref(st) if stats else None)
+    if rc:
+        raise GotohError(rc, "ga_band_features")
+    return (out, st.as_dict()) if stats else out
+
+
+def band_min_w(q_codes, q_off, t_codes, t_off, matrix, gap_open, gap_extend, stream=None,
+               stats: bool = False):
+    """(w_min, scores): minimal certified band half-width per global pair, exact scores."""
+    import torch
+    _check_dev(q_codes, q_off, t_codes, t_off)
+    npairs = q_off.numel() - 1
+    dev = q_codes.device
+    w = torch.empty(max(npairs, 0), dtype=torch.int32, device=dev)
+    scores = torch.empty(max(npairs, 0), dtype=torch.int32, device=dev)
+    sc, keep = make_scoring(matrix, gap_open, gap_extend)
+    st = Stats()
+    rc = load().ga_band_min_w(_ptr(q_codes), _ptr(q_off), _ptr(t_codes), _ptr(t_off), npairs,
+                              ctypes.byref(sc), _ptr(w), _ptr(scores), _stream_ptr(stream),
+                              ctypes.byref(st) if stats else None)
+    if rc:
+        raise GotohError(rc, "ga_band_min_w")
+    return (w, scores, st.as_dict()) if stats else (w, scores)
+
+
+def band_predict(q_codes, q_off, t_codes, t_off, params_bf16, margin: float = 0.0, stream=None,
+                 stats: bool = False):
+    """(w0 int32[npairs], y float32[npairs]) from the fused features + network kernel."""
+    import torch
+    _check_dev(q_codes, q_off, t_codes, t_off)
+    _check_dtype(params_bf16, torch.int16, MLP_NPARAMS, "params_bf16")
+    npairs = q_off.numel() - 1
+    dev = q_codes.device
+    w0 = torch.empty(max(npairs, 0), dtype=torch.int32, device=dev)
+    y = torch.empty(max(npairs, 0), dtype=torch.float32, device=dev)
+    st = Stats()
+    rc = load().ga_band_predict(_ptr(q_codes), _ptr(q_off), _ptr(t_codes), _ptr(t_off), npairs,
+                                _ptr(params_bf16), float(margin), _ptr(w0), _ptr(y),
+                                _stream_ptr(stream), ctypes.byref(st) if stats else None)
+    if rc:
+        raise GotohError(rc, "ga_band_predict")
+    return (w0, y, st.as_dict()) if stats else (w0, y)
+
+
+def mlp_forward(params_bf16, x, stream=None):
+    """y[n] = net(x[n, 32]) with bf16 weights (int16 tensor of bf16 bit patterns)."""
+    import torch
+    _check_dtype(params_bf16, torch.int16, MLP_NPARAMS, "params_bf16")
+    _check_dtype(x, torch.float32, None, "x")
+    n = x.numel() // BAND_NFEAT
+    y = torch.empty(n, dtype=torch.float32, device=x.device)
+    rc = load().ga_mlp_forward(_ptr(params_bf16), _ptr(x), n, _ptr(y), _stream_ptr(stream))
+    if rc:
+        raise GotohError(rc, "ga_mlp_forward")
+    return y
+
+
+def mlp_loss_grad(params_bf16, x, target, stream=None):
+    """(loss float32[1], grad float32[6337]) of the mean squared error over all samples."""
+    import torch
+    _check_dtype(params_bf16, torch.int16, MLP_NPARAMS, "params_bf16")
+    _check_dtype(x, torch.float32, None, "x")
+    n = x.numel() // BAND_NFEAT
+    _check_dtype(target, torch.float32, n, "target")
+    grad = torch.empty(MLP_NPARAMS, dtype=torch.float32, device=x.device)
+    loss = torch.empty(1, dtype=torch.float32, device=x.device)
+    rc = load().ga_mlp_loss_grad(_ptr(params_bf16), _ptr(x), _ptr(target), n, _ptr(grad),
+                                 _ptr(loss), _stream_ptr(stream))
+    if rc:
+        raise GotohError(rc, "ga_mlp_loss_grad")
+    return loss, grad
+
+
+def mlp_train(master, params_bf16, adam_m, adam_v, x, target, batch_idx, step0: int = 0,
+              lr: float = 1e-3, beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8,
+              stream=None):
+    """Adam steps over batch_idx[steps, batch] (device int32); updates the tensors in place.
+
+    Returns the per-step minibatch losses (float32[steps], device)."""
+    import torch
+    for t, what in ((master, "master"), (adam_m, "adam_m"), (adam_v, "adam_v")):
+        _check_dtype(t, torch.float32, MLP_NPARAMS, what)
+    _check_dtype(params_bf16, torch.int16, MLP_NPARAMS, "params_bf16")
+    _check_dtype(x, torch.float32, None, "x")
+    n = x.numel() // BAND_NFEAT
+    _check_dtype(target, torch.float32, n, "target")
+    _check_dtype(batch_idx, torch.int32, None, "batch_idx")
+    steps, batch = batch_idx.shape
+    losses = torch.empty(max(steps, 1), dtype=torch.float32, device=x.device)
+    rc = load().ga_mlp_train(_ptr(master), _ptr(params_bf16), _ptr(adam_m), _ptr(adam_v), _ptr(x),
+                             _ptr(target), n, _ptr(batch_idx), int(steps), int(batch), int(step0),
+                             float(lr), float(beta1), float(beta2), float(eps), _ptr(losses),
+                             _stream_ptr(stream))
+    if rc:
+        raise GotohError(rc, "ga_mlp_train")
+    return losses[:steps]
+
+
+def mlp_cast(master, params_bf16=None, stream=None):
+    """bf16 (round to nearest even) copy of float32 parameters, as an int16 tensor."""
+    import torch
+    _check_dtype(master, torch.float32, MLP_NPARAMS, "master")
+    if params_bf16 is None:
+        params_bf16 = torch.empty(MLP_NPARAMS, dtype=torch.int16, device=master.device)
+    rc = load().ga_mlp_cast(_ptr(master), _ptr(params_bf16), _stream_ptr(stream))
+    if rc:
+        raise GotohError(rc, "ga_mlp_cast")
+    return params_bf16

@@ -6,7 +6,10 @@
 #include <mutex>
 #include <vector>
 
+#include "../../include/gotoh_band.h"
+#include "ga_band.cuh"
 #include "ga_banded.cuh"
+#include "ga_pool.h"
 #include "ga_launch.h"
 #include "ga_prep.cuh"
 
@@ -22,6 +25,38 @@ static BinTable make_bins() {
     b.w32[i] = kKaG * kKaK[i];
   }
   return b;
+}
+
+// The library's own stream-ordered memory pool per device.  Its release
+// threshold keeps freed workspace mapped between calls, so a call does not
+// pay for mapping and unmapping hundreds of MB at every synchronisation (the
+// device's default pool returns memory to the driver at each sync).  The
+// pool is created on first use per device and lives until the process ends.
+static std::mutex g_pool_mu;
+static cudaMemPool_t g_pool[64] = {};
+
+cudaMemPool_t pool_for_current_device() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  std::lock_guard<std::mutex> lock(g_pool_mu);
+  if (!g_pool[dev]) {
+    cudaMemPoolProps props{};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.handleTypes = cudaMemHandleTypeNone;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t p = nullptr;
+    if (cudaMemPoolCreate(&p, &props) != cudaSuccess) return nullptr;
+    uint64_t keep = ~0ull;
+    cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &keep);
+    g_pool[dev] = p;
+  }
+  return g_pool[dev];
+}
+
+cudaError_t pool_malloc(void **p, size_t bytes, cudaStream_t s) {
+  cudaMemPool_t pool = pool_for_current_device();
+  return pool ? cudaMallocFromPoolAsync(p, bytes, pool, s) : cudaMallocAsync(p, bytes, s);
 }
 
 namespace {
@@ -64,38 +99,6 @@ int check_scoring(const ga_scoring *sc, Scoring *out) {
     }
   }
   return GA_OK;
-}
-
-// The library's own stream-ordered memory pool per device.  Its release
-// threshold keeps freed workspace mapped between calls, so a call does not
-// pay for mapping and unmapping hundreds of MB at every synchronisation (the
-// device's default pool returns memory to the driver at each sync).  The
-// pool is created on first use per device and lives until the process ends.
-std::mutex g_pool_mu;
-cudaMemPool_t g_pool[64] = {};
-
-cudaMemPool_t pool_for_current_device() {
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
-  std::lock_guard<std::mutex> lock(g_pool_mu);
-  if (!g_pool[dev]) {
-    cudaMemPoolProps props{};
-    props.allocType = cudaMemAllocationTypePinned;
-    props.handleTypes = cudaMemHandleTypeNone;
-    props.location.type = cudaMemLocationTypeDevice;
-    props.location.id = dev;
-    cudaMemPool_t p = nullptr;
-    if (cudaMemPoolCreate(&p, &props) != cudaSuccess) return nullptr;
-    uint64_t keep = ~0ull;
-    cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &keep);
-    g_pool[dev] = p;
-  }
-  return g_pool[dev];
-}
-
-cudaError_t pool_malloc(void **p, size_t bytes, cudaStream_t s) {
-  cudaMemPool_t pool = pool_for_current_device();
-  return pool ? cudaMallocFromPoolAsync(p, bytes, pool, s) : cudaMallocAsync(p, bytes, s);
 }
 
 // Device allocations of one call, released stream-ordered.
@@ -521,6 +524,204 @@ int batch_impl(const uint8_t *q_codes, const int64_t *q_off, const uint8_t *t_co
   return finish(c, stats, ev.e0, ev.e1, npairs);
 }
 
+__global__ void fill_i32_kernel(int32_t *p, int64_t n, int32_t v) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) p[i] = v;
+}
+
+// Bracket of the minimal certified width from the doubling result w (w_used
+// of a doubling run that started at 0): w = 0 or 1 is exact, otherwise the
+// width w/2 failed, so w_min lies in [w/2 + 1, min(w, min(m, n))] (a band of
+// half-width min(m, n) covers the matrix).  Invalid pairs (w < 0) are done.
+__global__ void bisect_init_kernel(const int64_t *q_off, const int64_t *t_off, int64_t npairs,
+                                   const int32_t *w_used, int32_t *lo, int32_t *hi, int32_t *maxgap) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int gap = 0;
+  if (i < npairs) {
+    const int w = w_used[i];
+    const int64_t m = q_off[i + 1] - q_off[i], n = t_off[i + 1] - t_off[i];
+    const int cap = (int)(m < n ? m : n);
+    int l = w, h = w;
+    if (w < 0) {
+      l = h = -1;
+    } else if (w >= 2) {
+      h = w < cap ? w : cap;
+      l = w / 2 + 1 < h ? w / 2 + 1 : h;
+    }
+    lo[i] = l;
+    hi[i] = h;
+    gap = h - l;
+  }
+  gap = __reduce_max_sync(0xffffffffu, (unsigned)gap);
+  if ((threadIdx.x & 31) == 0 && gap > 0) atomicMax(maxgap, gap);
+}
+
+__global__ void bisect_final_kernel(int64_t npairs, const int32_t *lo, int32_t *w_min) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < npairs) w_min[i] = lo[i];
+}
+
+// A planned banded run (global mode, alphabets of <= 4 symbols): both sets
+// packed, pairs ordered by estimated band work, boundary buffers sized.
+struct BandRun {
+  Call &c;
+  SetView Q, T;
+  int64_t npairs;
+  uint32_t *keys = nullptr;
+  int32_t *sorted = nullptr;
+  int max_rows = 0, grid = 0, launches = 0;
+  int64_t stride = 0;
+  int2 *bnd = nullptr;
+  BandRun(Call &cc, const uint8_t *qc, const int64_t *qo, const uint8_t *tc, const int64_t *to, int64_t np)
+      : c(cc), Q{qc, qo, nullptr, nullptr}, T{tc, to, nullptr, nullptr}, npairs(np) {}
+
+  int prepare() {
+    int rc;
+    if ((rc = prepare_set(c, Q.codes, Q.off, npairs, &Q.packed, &Q.bad, &c.small->invalid_q))) return rc;
+    if ((rc = prepare_set(c, T.codes, T.off, npairs, &T.packed, &T.bad, &c.small->invalid_t))) return rc;
+    keys = c.al.get<uint32_t>((size_t)npairs);
+    sorted = c.al.get<int32_t>((size_t)npairs);
+    return c.al.failed ? GA_ERR_OOM : GA_OK;
+  }
+
+  // Validity, closed forms of empty pairs, work keys and the sorted order.
+  int plan(const int32_t *w0, int32_t default_w0, int32_t *scores, int32_t *w_used) {
+    if (cudaMemsetAsync(c.hist, 0, sizeof(int32_t) * kNumKeys, c.s) != cudaSuccess) return GA_ERR_CUDA;
+    BandPlanParams bp{};
+    bp.q_off = Q.off;
+    bp.t_off = T.off;
+    bp.npairs = npairs;
+    bp.qbad = Q.bad;
+    bp.tbad = T.bad;
+    bp.w0 = w0;
+    bp.default_w0 = default_w0;
+    bp.alpha = c.sc.alpha;
+    bp.beta = c.sc.beta;
+    bp.scores = scores;
+    bp.w_used = w_used;
+    bp.keys = keys;
+    bp.status = &c.small->status;
+    bp.cells = &c.small->cells;
+    bp.max_rows = &c.small->max_rows;
+    const unsigned nb = (unsigned)((npairs + 255) / 256);
+    band_plan_kernel<<<nb, 256, 0, c.s>>>(bp);
+    hist_kernel<<<nb, 256, 0, c.s>>>(keys, npairs, c.hist);
+    scan_partials_kernel<<<kScanTiles, kScanTile, 0, c.s>>>(c.hist, c.small->scan_partials);
+    scan_apply_kernel<<<kScanTiles, kScanTile, 0, c.s>>>(c.hist, c.small->scan_partials, c.cursor,
+                                                         c.small->ranges);
+    scatter_kernel<<<nb, 256, 0, c.s>>>(keys, npairs, c.cursor, sorted);
+    c.launches += 5;
+    if (cudaGetLastError() != cudaSuccess) return GA_ERR_CUDA;
+    int32_t *h = (int32_t *)pinned_scratch();
+    if (cudaMemcpyAsync(h, &c.small->max_rows, sizeof(int32_t), cudaMemcpyDeviceToHost, c.s) != cudaSuccess ||
+        cudaStreamSynchronize(c.s) != cudaSuccess)
+      return GA_ERR_CUDA;
+    max_rows = h[0];
+    if (max_rows > 0) {
+      const int occ = std::max(blocks_per_sm_kc(), 1);
+      const int64_t want = (npairs + kKcWarps - 1) / kKcWarps;
+      grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)c.nsm * occ));
+      stride = (int64_t)max_rows + 128;
+      bnd = c.al.get<int2>((size_t)grid * kKcWarps * (size_t)stride);
+      if (c.al.failed) return GA_ERR_OOM;
+    }
+    return GA_OK;
+  }
+
+  // One launch of the banded kernel over the planned order: band doubling
+  // (bis_lo == nullptr) or one bisection step.  Each launch takes a fresh
+  // task counter.
+  int launch(const int32_t *w0, int32_t default_w0, int32_t *scores, int32_t *w_used, int32_t *bis_lo,
+             int32_t *bis_hi) {
+    if (max_rows <= 0) return GA_OK;
+    if (launches >= 62) return GA_ERR_ARG;
+    KCParams kc{};
+    kc.packed_q = Q.packed;
+    kc.packed_t = T.packed;
+    kc.q_off = Q.off;
+    kc.t_off = T.off;
+    kc.order = sorted;
+    kc.range = c.small->ranges;  // class 0, bin 0: every non-trivial pair
+    kc.task_counter = &c.small->counters[launches++];
+    std::memcpy(kc.tables, c.sc.tables, sizeof(kc.tables));
+    kc.alpha = c.sc.alpha;
+    kc.beta = c.sc.beta;
+    kc.sigma_max_pos = std::max(c.sc.smax, 0);
+    kc.w0 = w0;
+    kc.default_w0 = default_w0;
+    kc.scores = scores;
+    kc.w_used = w_used;
+    kc.retries = &c.small->band_retries;
+    kc.cells = &c.small->band_cells;
+    kc.bnd = bnd;
+    kc.bnd_stride = stride;
+    kc.bis_lo = bis_lo;
+    kc.bis_hi = bis_hi;
+    c.dp_begin();
+    const cudaError_t e = launch_kc(kc, grid, c.s);
+    c.dp_end();
+    return e == cudaSuccess ? GA_OK : GA_ERR_CUDA;
+  }
+
+  int band_stats(ga_stats *st) {
+    unsigned long long *hb = (unsigned long long *)pinned_scratch();
+    if (cudaMemcpyAsync(hb, &c.small->band_retries, 2 * sizeof(unsigned long long),
+                        cudaMemcpyDeviceToHost, c.s) != cudaSuccess ||
+        cudaStreamSynchronize(c.s) != cudaSuccess)
+      return GA_ERR_CUDA;
+    st->band_retries = (int64_t)hb[0];
+    st->banded_cells = (int64_t)hb[1];
+    return GA_OK;
+  }
+};
+
+// Features (predict == false) or fused prediction of DNA pairs.
+int features_impl(const uint8_t *q_codes, const int64_t *q_off, const uint8_t *t_codes,
+                  const int64_t *t_off, int64_t npairs, float *features, const uint16_t *wb,
+                  float margin, int32_t *w0, float *y, void *stream, ga_stats *stats) {
+  if (npairs >= (1ll << 31) - 64) return GA_ERR_ARG;
+  Call c((cudaStream_t)stream);
+  c.sc.A = 4;  // DNA codes 0..3; residues are validated while packing
+  c.mode = GA_GLOBAL;
+  c.timing = stats != nullptr;
+  Events ev(stats != nullptr, c.s);
+  int rc;
+  if ((rc = setup(c))) return rc;
+  if (npairs == 0) return finish(c, stats, ev.e0, ev.e1, 0);
+  SetView Q{q_codes, q_off, nullptr, nullptr}, T{t_codes, t_off, nullptr, nullptr};
+  if ((rc = prepare_set(c, q_codes, q_off, npairs, &Q.packed, &Q.bad, &c.small->invalid_q))) return rc;
+  if ((rc = prepare_set(c, t_codes, t_off, npairs, &T.packed, &T.bad, &c.small->invalid_t))) return rc;
+  BandFeatParams fp{};
+  fp.packed_q = Q.packed;
+  fp.packed_t = T.packed;
+  fp.q_off = q_off;
+  fp.t_off = t_off;
+  fp.qbad = Q.bad;
+  fp.tbad = T.bad;
+  fp.npairs = npairs;
+  fp.features = features;
+  fp.wb = wb;
+  fp.margin = margin;
+  fp.y = y;
+  fp.w0 = w0;
+  fp.status = &c.small->status;
+  const size_t smem = feat_smem_bytes(wb != nullptr);
+  const bool attr_ok =  // per call: the attribute belongs to the current device
+      cudaFuncSetAttribute(band_features_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)feat_smem_bytes(true)) == cudaSuccess &&
+      cudaFuncSetAttribute(band_features_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)feat_smem_bytes(false)) == cudaSuccess;
+  if (!attr_ok) return GA_ERR_CUDA;
+  const int grid = (int)std::min<int64_t>(npairs, (int64_t)c.nsm * 4);
+  if (wb)
+    band_features_kernel<true><<<grid, kFeatThreads, smem, c.s>>>(fp);
+  else
+    band_features_kernel<false><<<grid, kFeatThreads, smem, c.s>>>(fp);
+  ++c.launches;
+  if (cudaGetLastError() != cudaSuccess) return GA_ERR_CUDA;
+  return finish(c, stats, ev.e0, ev.e1, npairs);
+}
+
 }  // namespace
 }  // namespace ga
 
@@ -619,11 +820,6 @@ int ga_align_long(const uint8_t *q, int64_t m, const uint8_t *t, int64_t n, cons
   return rc;
 }
 
-__global__ void fill_i32_kernel(int32_t *p, int64_t n, int32_t v) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) p[i] = v;
-}
-
 int ga_align_banded(const uint8_t *q_codes, const int64_t *q_off, const uint8_t *t_codes,
                     const int64_t *t_off, int64_t npairs, const ga_scoring *scoring, const int32_t *w0,
                     int32_t default_w0, int32_t *scores, int32_t *w_used, void *stream, ga_stats *stats) {
@@ -647,86 +843,76 @@ int ga_align_banded(const uint8_t *q_codes, const int64_t *q_off, const uint8_t 
   Events ev(stats != nullptr, c.s);
   if ((rc = setup(c))) return rc;
   if (npairs == 0) return finish(c, stats, ev.e0, ev.e1, 0);
-  SetView Q{q_codes, q_off, nullptr, nullptr}, T{t_codes, t_off, nullptr, nullptr};
-  if ((rc = prepare_set(c, q_codes, q_off, npairs, &Q.packed, &Q.bad, &c.small->invalid_q))) return rc;
-  if ((rc = prepare_set(c, t_codes, t_off, npairs, &T.packed, &T.bad, &c.small->invalid_t))) return rc;
-  uint32_t *keys = c.al.get<uint32_t>((size_t)npairs);
-  int32_t *sorted = c.al.get<int32_t>((size_t)npairs);
+  BandRun br(c, q_codes, q_off, t_codes, t_off, npairs);
+  if ((rc = br.prepare())) return rc;
+  if ((rc = br.plan(w0, default_w0, scores, w_used))) return rc;
+  if ((rc = br.launch(w0, default_w0, scores, w_used, nullptr, nullptr))) return rc;
+  rc = finish(c, stats, ev.e0, ev.e1, npairs);
+  if (!rc && stats) rc = br.band_stats(stats);
+  return rc;
+}
+
+int ga_band_min_w(const uint8_t *q_codes, const int64_t *q_off, const uint8_t *t_codes,
+                  const int64_t *t_off, int64_t npairs, const ga_scoring *scoring, int32_t *w_min,
+                  int32_t *scores, void *stream, ga_stats *stats) {
+  if (npairs < 0) return GA_ERR_ARG;
+  if (npairs > 0 && (!q_codes || !q_off || !t_codes || !t_off || !scores || !w_min)) return GA_ERR_ARG;
+  if (npairs >= (1ll << 31) - 64) return GA_ERR_ARG;
+  Call c((cudaStream_t)stream);
+  int rc = check_scoring(scoring, &c.sc);
+  if (rc) return rc;
+  if (c.sc.A > 4) return GA_ERR_ALPHABET;
+  c.mode = GA_GLOBAL;
+  c.timing = stats != nullptr;
+  Events ev(stats != nullptr, c.s);
+  if ((rc = setup(c))) return rc;
+  if (npairs == 0) return finish(c, stats, ev.e0, ev.e1, 0);
+  BandRun br(c, q_codes, q_off, t_codes, t_off, npairs);
+  if ((rc = br.prepare())) return rc;
+  int32_t *lo = c.al.get<int32_t>((size_t)npairs), *hi = c.al.get<int32_t>((size_t)npairs);
   if (c.al.failed) return GA_ERR_OOM;
-  if (cudaMemsetAsync(c.hist, 0, sizeof(int32_t) * kNumKeys, c.s) != cudaSuccess) return GA_ERR_CUDA;
-  BandPlanParams bp{};
-  bp.q_off = q_off;
-  bp.t_off = t_off;
-  bp.npairs = npairs;
-  bp.qbad = Q.bad;
-  bp.tbad = T.bad;
-  bp.w0 = w0;
-  bp.default_w0 = default_w0;
-  bp.alpha = c.sc.alpha;
-  bp.beta = c.sc.beta;
-  bp.scores = scores;
-  bp.w_used = w_used;
-  bp.keys = keys;
-  bp.status = &c.small->status;
-  bp.cells = &c.small->cells;
-  bp.max_rows = &c.small->max_rows;
+  // doubling from w = 0 brackets the minimal width
+  if ((rc = br.plan(nullptr, 0, scores, w_min))) return rc;
+  if ((rc = br.launch(nullptr, 0, scores, w_min, nullptr, nullptr))) return rc;
+  int32_t *maxgap = &c.small->counters[63];
   const unsigned nb = (unsigned)((npairs + 255) / 256);
-  band_plan_kernel<<<nb, 256, 0, c.s>>>(bp);
-  hist_kernel<<<nb, 256, 0, c.s>>>(keys, npairs, c.hist);
-  scan_partials_kernel<<<kScanTiles, kScanTile, 0, c.s>>>(c.hist, c.small->scan_partials);
-  scan_apply_kernel<<<kScanTiles, kScanTile, 0, c.s>>>(c.hist, c.small->scan_partials, c.cursor,
-                                                       c.small->ranges);
-  scatter_kernel<<<nb, 256, 0, c.s>>>(keys, npairs, c.cursor, sorted);
-  c.launches += 5;
-  if (cudaGetLastError() != cudaSuccess) return GA_ERR_CUDA;
+  bisect_init_kernel<<<nb, 256, 0, c.s>>>(q_off, t_off, npairs, w_min, lo, hi, maxgap);
+  ++c.launches;
   int32_t *h = (int32_t *)pinned_scratch();
-  if (cudaMemcpyAsync(h, &c.small->max_rows, sizeof(int32_t), cudaMemcpyDeviceToHost, c.s) != cudaSuccess ||
+  if (cudaGetLastError() != cudaSuccess ||
+      cudaMemcpyAsync(h, maxgap, sizeof(int32_t), cudaMemcpyDeviceToHost, c.s) != cudaSuccess ||
       cudaStreamSynchronize(c.s) != cudaSuccess)
     return GA_ERR_CUDA;
-  const int max_rows = h[0];
-  if (max_rows > 0) {
-    const int occ = std::max(blocks_per_sm_kc(), 1);
-    const int64_t want = (npairs + kKcWarps - 1) / kKcWarps;
-    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)c.nsm * occ));
-    const int64_t stride = (int64_t)max_rows + 128;
-    int2 *bnd = c.al.get<int2>((size_t)grid * kKcWarps * (size_t)stride);
-    if (c.al.failed) return GA_ERR_OOM;
-    KCParams kc{};
-    kc.packed_q = Q.packed;
-    kc.packed_t = T.packed;
-    kc.q_off = q_off;
-    kc.t_off = t_off;
-    kc.order = sorted;
-    kc.range = c.small->ranges;  // class 0, bin 0: every non-trivial pair
-    kc.task_counter = &c.small->counters[0];
-    std::memcpy(kc.tables, c.sc.tables, sizeof(kc.tables));
-    kc.alpha = c.sc.alpha;
-    kc.beta = c.sc.beta;
-    kc.sigma_max_pos = std::max(c.sc.smax, 0);
-    kc.w0 = w0;
-    kc.default_w0 = default_w0;
-    kc.scores = scores;
-    kc.w_used = w_used;
-    kc.retries = &c.small->band_retries;
-    kc.cells = &c.small->band_cells;
-    kc.bnd = bnd;
-    kc.bnd_stride = stride;
-    c.dp_begin();
-    const cudaError_t e = launch_kc(kc, grid, c.s);
-    c.dp_end();
-    if (e != cudaSuccess) return GA_ERR_CUDA;
-  }
+  int iters = 0;
+  while (iters < 31 && ((int64_t)1 << iters) < (int64_t)h[0] + 1) ++iters;
+  for (int it = 0; it < iters; ++it)
+    if ((rc = br.launch(nullptr, 0, scores, nullptr, lo, hi))) return rc;
+  bisect_final_kernel<<<nb, 256, 0, c.s>>>(npairs, lo, w_min);
+  ++c.launches;
+  if (cudaGetLastError() != cudaSuccess) return GA_ERR_CUDA;
   rc = finish(c, stats, ev.e0, ev.e1, npairs);
-  if (!rc && stats) {
-    unsigned long long *hb = (unsigned long long *)pinned_scratch();
-    if (cudaMemcpyAsync(hb, &c.small->band_retries, 2 * sizeof(unsigned long long),
-                        cudaMemcpyDeviceToHost, c.s) != cudaSuccess ||
-        cudaStreamSynchronize(c.s) != cudaSuccess)
-      return GA_ERR_CUDA;
-    stats->band_retries = (int64_t)hb[0];
-    stats->banded_cells = (int64_t)hb[1];
-  }
+  if (!rc && stats) rc = br.band_stats(stats);
   return rc;
+}
+
+int ga_band_features(const uint8_t *q_codes, const int64_t *q_off, const uint8_t *t_codes,
+                     const int64_t *t_off, int64_t npairs, float *features, void *stream,
+                     ga_stats *stats) {
+  if (npairs < 0 || (npairs > 0 && (!q_codes || !q_off || !t_codes || !t_off || !features)))
+    return GA_ERR_ARG;
+  return features_impl(q_codes, q_off, t_codes, t_off, npairs, features, nullptr, 0.f, nullptr,
+                       nullptr, stream, stats);
+}
+
+int ga_band_predict(const uint8_t *q_codes, const int64_t *q_off, const uint8_t *t_codes,
+                    const int64_t *t_off, int64_t npairs, const uint16_t *params_bf16, float margin,
+                    int32_t *w0, float *y, void *stream, ga_stats *stats) {
+  if (npairs < 0 ||
+      (npairs > 0 && (!q_codes || !q_off || !t_codes || !t_off || !params_bf16 || !w0)))
+    return GA_ERR_ARG;
+  if (!(margin > -64.f && margin < 64.f)) return GA_ERR_ARG;
+  return features_impl(q_codes, q_off, t_codes, t_off, npairs, nullptr, params_bf16, margin, w0, y,
+                       stream, stats);
 }
 
 const char *ga_strerror(int code) {

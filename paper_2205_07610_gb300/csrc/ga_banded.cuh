@@ -46,6 +46,12 @@ struct KCParams {
   unsigned long long *cells;
   int2 *bnd;
   int64_t bnd_stride;
+  // Bisection mode (both non-null): one attempt per pair at w = (lo+hi)/2 of
+  // the pair's interval [lo, hi] of candidate minimal widths, which the
+  // attempt then halves (certified: hi = w, else lo = w + 1); pairs with
+  // lo == hi are skipped and nothing else is written.
+  int32_t *bis_lo;
+  int32_t *bis_hi;
 };
 
 __device__ __forceinline__ int64_t band_ub(int64_t m, int64_t n, int64_t smax, int64_t alpha,
@@ -86,9 +92,21 @@ __global__ void __launch_bounds__(128) kc_kernel(const __grid_constant__ KCParam
     const int pid = p.order[p.range[0] + task];
     const int64_t qs = p.q_off[pid], ts = p.t_off[pid];
     const int m = (int)(p.q_off[pid + 1] - qs), n = (int)(p.t_off[pid + 1] - ts);
-    int w = p.w0 ? p.w0[pid] : p.default_w0;
+    const bool bisect = p.bis_lo != nullptr;
+    int w;
+    if (bisect) {
+      const int lw = p.bis_lo[pid], hw = p.bis_hi[pid];
+      if (lw >= hw) continue;
+      w = lw + (hw - lw) / 2;
+    } else {
+      w = p.w0 ? p.w0[pid] : p.default_w0;
+    }
     if (w < 0) w = 0;
     if (m == 0 || n == 0) {  // closed form, any band
+      if (bisect) {  // w = 0 already covers the matrix
+        if (t == 0) p.bis_lo[pid] = p.bis_hi[pid] = 0;
+        continue;
+      }
       if (t == 0) {
         const int len = m + n;
         p.scores[pid] = len ? -(alpha + beta * (len - 1)) : 0;
@@ -251,6 +269,13 @@ __global__ void __launch_bounds__(128) kc_kernel(const __grid_constant__ KCParam
       int64_t ub = INT64_MIN;
       if (lo - 1 >= -m) ub = ::max(ub, band_ub(m, n, p.sigma_max_pos, alpha, beta, lo - 1));
       if (hi + 1 <= n) ub = ::max(ub, band_ub(m, n, p.sigma_max_pos, alpha, beta, hi + 1));
+      if (bisect) {
+        if (t == 0) {
+          if (covers || (int64_t)S >= ub) p.bis_hi[pid] = w;
+          else p.bis_lo[pid] = w + 1;
+        }
+        break;
+      }
       if (covers || (int64_t)S >= ub) {
         if (t == 0) {
           p.scores[pid] = S;

@@ -1,0 +1,217 @@
+"""GPU parity of the band predictor (features, network, training, labels)
+against the CPU oracles, and the gain of the trained predictor.
+
+* features: bit-exact except the four log2 features (1e-6; log2f vs numpy);
+* network forward / loss / gradient: float32 kernels with bf16 weights vs the
+  float64 oracle on the same bf16 weights, within a float32 accumulation
+  bound; bf16 rounding bit-exact;
+* Adam: one step vs the float64 update from the same gradient;
+* labels (minimal certified w): bit-exact vs the oracle's bisection;
+* the trained predictor needs fewer banded cells on held-out pairs than the
+  best constant starting width chosen on the training pairs.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import band_features as obf
+from oracle import mlp as omlp
+import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_2205_07610_gb300 as ga  # noqa: E402
+from paper_2205_07610_gb300 import band  # noqa: E402
+
+NTHREADS = max(1, min(32, os.cpu_count() or 1))
+LOG_FEATS = [0, 1, 2, 5]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    ga.build()
+    ga.load()
+
+
+def _dev(b):
+    d = "cuda"
+    return (torch.from_numpy(np.ascontiguousarray(b.q_codes)).to(d),
+            torch.from_numpy(np.ascontiguousarray(b.q_off)).to(d),
+            torch.from_numpy(np.ascontiguousarray(b.t_codes)).to(d),
+            torch.from_numpy(np.ascontiguousarray(b.t_off)).to(d))
+
+
+def _feature_batch():
+    b = synth.long_dna_pairs(npairs=48, lmin=10, lmax=5000, seed=101)
+    rng = np.random.default_rng(4)
+    qs = [b.q_codes[b.q_off[p]:b.q_off[p + 1]] for p in range(b.npairs)]
+    ts = [b.t_codes[b.t_off[p]:b.t_off[p + 1]] for p in range(b.npairs)]
+    at = np.tile(np.array([0, 3], dtype=np.uint8), 400)
+    extra = [(np.zeros(0, np.uint8), rng.integers(0, 4, 50).astype(np.uint8)),
+             (rng.integers(0, 4, 11).astype(np.uint8), rng.integers(0, 4, 11).astype(np.uint8)),
+             (at[:700], at[:650]), (at[:2100], at[1:2101]),
+             (np.zeros(3000, np.uint8), np.zeros(2500, np.uint8))]
+    for q, t in extra:
+        qs.append(q)
+        ts.append(t)
+    qc, qo = synth.pack_csr(qs)
+    tc, to = synth.pack_csr(ts)
+    return synth.Batch(qc, qo, tc, to, synth.dna_matrix(2, -3), 5, 2, "features")
+
+
+def test_features_parity():
+    b = _feature_batch()
+    got = ga.band_features(*_dev(b)).cpu().numpy()
+    ref = obf.batch_features(b.q_codes, b.q_off, b.t_codes, b.t_off)
+    exact = [k for k in range(32) if k not in LOG_FEATS]
+    np.testing.assert_array_equal(got[:, exact], ref[:, exact])
+    np.testing.assert_allclose(got[:, LOG_FEATS], ref[:, LOG_FEATS], rtol=0, atol=1e-6)
+    assert (ref[:, 31] < 1).any() and (ref[:, 5] > 0.5).any()   # strided and hit-heavy cases ran
+
+
+def _params(seed):
+    rng = np.random.default_rng(seed)
+    p = synth.mlp_init(seed) + rng.normal(0, 0.05, size=synth.MLP_NPARAMS).astype(np.float32)
+    return p.astype(np.float32)
+
+
+def _bf16_dev(master_np):
+    m = torch.from_numpy(master_np).cuda()
+    wb = ga.mlp_cast(m)
+    bits = wb.cpu().numpy().view(np.uint16)
+    np.testing.assert_array_equal(bits, omlp.bf16_bits(master_np))
+    return wb, omlp.bf16_to_f32(bits).astype(np.float64)
+
+
+def _abs_scale(p64, X):
+    """Forward pass with |weights| and |x|: a bound on the magnitude of every sum."""
+    y, _ = omlp.forward(np.abs(p64), np.abs(X))
+    return np.abs(y) + 1.0
+
+
+def test_mlp_forward_parity():
+    p = _params(11)
+    wb, p64 = _bf16_dev(p)
+    X = np.random.default_rng(12).uniform(0, 1, size=(777, 32)).astype(np.float32)
+    y = ga.mlp_forward(wb, torch.from_numpy(X).cuda()).cpu().numpy().astype(np.float64)
+    ref, _ = omlp.forward(p64, X.astype(np.float64))
+    tol = 1e-5 * _abs_scale(p64, X.astype(np.float64))
+    assert np.all(np.abs(y - ref) <= tol), np.max(np.abs(y - ref) / tol)
+
+
+def test_mlp_grad_parity():
+    p = _params(13)
+    wb, p64 = _bf16_dev(p)
+    rng = np.random.default_rng(14)
+    X = rng.uniform(0, 1, size=(300, 32)).astype(np.float32)
+    t = rng.uniform(0, 12, size=300).astype(np.float32)
+    loss, g = ga.mlp_loss_grad(wb, torch.from_numpy(X).cuda(), torch.from_numpy(t).cuda())
+    L, gref = omlp.loss_grad(p64, X.astype(np.float64), t.astype(np.float64))
+    assert abs(float(loss.item()) - L) <= 1e-5 * max(1.0, L)
+    g = g.cpu().numpy().astype(np.float64)
+    err = np.abs(g - gref)
+    assert np.all(err <= 1e-4 * np.max(np.abs(gref)) + 1e-6), (np.argmax(err), err.max())
+
+
+def test_adam_step_parity():
+    p = _params(15)
+    rng = np.random.default_rng(16)
+    n = 256
+    X = rng.uniform(0, 1, size=(n, 32)).astype(np.float32)
+    t = rng.uniform(0, 12, size=n).astype(np.float32)
+    master = torch.from_numpy(p.copy()).cuda()
+    wb = ga.mlp_cast(master)
+    _, g = ga.mlp_loss_grad(wb, torch.from_numpy(X).cuda(), torch.from_numpy(t).cuda())
+    g = g.cpu().numpy().astype(np.float64)
+    am = torch.zeros_like(master)
+    av = torch.zeros_like(master)
+    idx = torch.arange(n, dtype=torch.int32, device="cuda").reshape(1, n)
+    lr = 1e-3
+    ga.mlp_train(master, wb, am, av, torch.from_numpy(X).cuda(), torch.from_numpy(t).cuda(), idx,
+                 lr=lr)
+    ref, mref, vref = omlp.adam_step(p.astype(np.float64), np.zeros_like(g), np.zeros_like(g), g, 1, lr)
+    got = master.cpu().numpy()
+    np.testing.assert_allclose(got, ref, rtol=0, atol=2e-7 + 1e-6 * lr)
+    np.testing.assert_allclose(am.cpu().numpy(), mref, rtol=1e-6, atol=1e-12)
+    np.testing.assert_array_equal(wb.cpu().numpy().view(np.uint16), omlp.bf16_bits(got))
+
+
+def test_mlp_train_rejects_bad_batch_index():
+    p = _params(17)
+    master = torch.from_numpy(p.copy()).cuda()
+    wb = ga.mlp_cast(master)
+    X = torch.rand(10, 32, device="cuda")
+    t = torch.rand(10, device="cuda")
+    idx = torch.tensor([[0, 5, 10]], dtype=torch.int32, device="cuda")
+    with pytest.raises(ga.GotohError):
+        ga.mlp_train(master, wb, torch.zeros_like(master), torch.zeros_like(master), X, t, idx)
+
+
+def _w0_ref(y, margin, m, n):
+    e = np.clip(np.float32(y) + np.float32(margin), np.float32(0), np.float32(30))
+    v = np.exp2(e.astype(np.float32))
+    w = (np.ceil(v) - 1).astype(np.int64)
+    return np.clip(w, 0, np.minimum(m, n)), v
+
+
+def test_predict_fused_matches_features_and_forward():
+    b = _feature_batch()
+    dev = _dev(b)
+    wb, _ = _bf16_dev(_params(19))
+    for margin in (0.0, 0.75, -0.5):
+        w0, y = ga.band_predict(*dev, wb, margin)
+        feats = ga.band_features(*dev)
+        y2 = ga.mlp_forward(wb, feats)
+        np.testing.assert_array_equal(y.cpu().numpy(), y2.cpu().numpy())
+        m = np.diff(b.q_off)
+        n = np.diff(b.t_off)
+        ref, v = _w0_ref(y.cpu().numpy(), margin, m, n)
+        clear = np.abs(v - np.round(v)) > 1e-3 * np.maximum(v, 1)
+        np.testing.assert_array_equal(w0.cpu().numpy()[clear], ref[clear])
+
+
+def test_min_w_labels_match_oracle():
+    b = synth.long_dna_pairs(npairs=50, lmin=20, lmax=700, seed=303)
+    rng = np.random.default_rng(5)
+    qs = [b.q_codes[b.q_off[p]:b.q_off[p + 1]] for p in range(b.npairs)]
+    ts = [b.t_codes[b.t_off[p]:b.t_off[p + 1]] for p in range(b.npairs)]
+    qs += [np.zeros(0, np.uint8), rng.integers(0, 4, 1).astype(np.uint8), rng.integers(0, 4, 300).astype(np.uint8)]
+    ts += [rng.integers(0, 4, 9).astype(np.uint8), np.zeros(0, np.uint8), rng.integers(0, 4, 40).astype(np.uint8)]
+    qc, qo = synth.pack_csr(qs)
+    tc, to = synth.pack_csr(ts)
+    for (ma, mi), al, be in (((2, -3), 5, 2), ((1, -1), 1, 1)):
+        mat = synth.dna_matrix(ma, mi)
+        bb = synth.Batch(qc, qo, tc, to, mat, al, be, "labels")
+        w, sc = ga.band_min_w(*_dev(bb), mat, al, be)
+        w = w.cpu().numpy()
+        sc = sc.cpu().numpy()
+        full, _ = oracle.batch(qc, qo, tc, to, mat, al, be, "global", nthreads=NTHREADS)
+        np.testing.assert_array_equal(sc, full)
+        for p in range(len(qs)):
+            ref = oracle.min_certified_w_blocks(qs[p], ts[p], mat, al, be, 16)
+            assert w[p] == ref, (p, len(qs[p]), len(ts[p]), int(w[p]), ref)
+
+
+def test_trained_predictor_beats_best_constant():
+    mat = synth.dna_matrix(2, -3)
+    tr = synth.long_dna_pairs(npairs=800, lmin=500, lmax=4000, seed=synth.SEED_BASE + 41)
+    te = synth.long_dna_pairs(npairs=300, lmin=500, lmax=4000, seed=synth.SEED_BASE + 42)
+    dtr, dte = _dev(tr), _dev(te)
+    steps, batch = 600, 128
+    pred, info = band.train(*dtr, mat, 5, 2, synth.mlp_init(7),
+                            synth.minibatches(tr.npairs, batch, steps, 8), lr=2e-3)
+    losses = info["losses"]
+    assert losses[-50:].mean() < 0.2 * losses[:10].mean(), (losses[:10].mean(), losses[-50:].mean())
+    c_w0, _ = band.best_constant_w0(*dtr, mat, 5, 2)
+    const_cells = band.banded_cells(*dte, mat, 5, 2, default_w0=c_w0)
+    sc, wu, st = pred.align(*dte, mat, 5, 2, stats=True)
+    full, _ = oracle.batch(te.q_codes, te.q_off, te.t_codes, te.t_off, mat, 5, 2, "global",
+                           nthreads=NTHREADS)
+    np.testing.assert_array_equal(sc.cpu().numpy(), full)
+    assert st["banded_cells"] < const_cells < st["cells"], (st["banded_cells"], const_cells, c_w0)
