@@ -8,6 +8,10 @@ metric is GCUPS: full-DP cells (sum of m*n, both modes) per second.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
+The line also carries "band": the learned-band vs full-DP time to exact global
+scores on 20k long DNA pairs (|Q| ~ U{1000..20000}, divergence 1-15 %), with
+the band predictor trained first on its own seeded pairs (--no-band skips it).
+
 Multi-GPU (torchrun, one process per GPU): every rank aligns its own seeded
 batch of the same shape (weak scaling, no data-path collective); the step time
 is the max over ranks and `value` counts the cells of all ranks.
@@ -50,6 +54,9 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="target CPU time of the bounded oracle sample")
+    ap.add_argument("--no-band", action="store_true", help="skip the learned-band measurement")
+    ap.add_argument("--band-pairs", type=int, default=20_000)
+    ap.add_argument("--band-train", type=int, default=4_000)
     return ap.parse_args()
 
 
@@ -172,6 +179,82 @@ def cpu_baseline(b, seconds: float):
     cells = 2 * sub.cells()
     return {"value": cells / dt / 1e9, "unit": "GCUPS", "cores": nthreads, "kind": "oracle",
             "sample": f"first {k} of {b.npairs} pairs, global+semiglobal, {dt:.1f} s"}
+
+
+def band_section(ga, dev, stream, npairs: int, ntrain: int, reps: int = 3):
+    """Learned-band vs full-DP time to exact global scores (20k long DNA pairs).
+
+    The predictor is trained first, on its own seeded pairs of the same
+    distribution (labels = minimal certified widths computed by the library),
+    then four ways to the same exact scores are timed on the test pairs:
+    full DP, band doubling from the default start (16), from the best
+    constant start chosen on the training pairs, and from the learned start
+    (prediction kernel included).
+    """
+    import torch
+    from paper_2205_07610_gb300 import band
+    mat = synth.dna_matrix(2, -3)
+    t0 = time.perf_counter()
+    te = synth.long_dna_pairs(npairs=npairs)
+    tr = synth.long_dna_pairs(npairs=ntrain, seed=synth.SEED_BASE + 400)
+    gen_s = time.perf_counter() - t0
+
+    def to_dev(b):
+        return tuple(torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+                     for a in (b.q_codes, b.q_off, b.t_codes, b.t_off))
+    d_te, d_tr = to_dev(te), to_dev(tr)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    w_min, _ = band.labels(*d_tr, mat, 5, 2, stream=stream)
+    torch.cuda.synchronize(dev)
+    labels_s = time.perf_counter() - t0
+    steps, batch = 1500, 256
+    t0 = time.perf_counter()
+    pred, info = band.train(*d_tr, mat, 5, 2, synth.mlp_init(synth.SEED_BASE + 401),
+                            synth.minibatches(tr.npairs, batch, steps, synth.SEED_BASE + 402),
+                            lr=2e-3, w_min=w_min, stream=stream)
+    torch.cuda.synchronize(dev)
+    train_s = time.perf_counter() - t0
+    c_w0, _ = band.best_constant_w0(*d_tr, mat, 5, 2, stream=stream)
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize(dev)
+        out = []
+        for _ in range(reps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            r = fn()
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            out.append(e0.elapsed_time(e1))
+        return float(np.median(out)), r
+
+    full_ms, (full, st_full) = timed(lambda: ga.align_batch(*d_te, mat, 5, 2, "global",
+                                                            stream=stream, stats=True))
+    runs = {}
+    for name, fn in (("default_w0_16", lambda: ga.align_banded(*d_te, mat, 5, 2, default_w0=16,
+                                                               stream=stream, stats=True)),
+                     (f"best_constant_w0_{c_w0}", lambda: ga.align_banded(
+                         *d_te, mat, 5, 2, default_w0=c_w0, stream=stream, stats=True)),
+                     ("learned", lambda: pred.align(*d_te, mat, 5, 2, stream=stream, stats=True))):
+        ms, (sc, wu, st) = timed(fn)
+        runs[name] = {"ms": ms, "exact": bool(torch.equal(sc, full)),
+                      "banded_cells": st["banded_cells"], "band_retries": st["band_retries"],
+                      "speedup_vs_full_dp": full_ms / ms}
+    losses = info["losses"]
+    return {
+        "metric": "time to exact global scores (ms)", "higher_is_better": False,
+        "workload": f"{npairs} DNA pairs L~U{{1000..20000}}, divergence U(1%,15%), "
+                    "indel fraction U(10%,40%); global, +2/-3, gap open 5, extend 2",
+        "full_dp_ms": full_ms, "full_dp_cells": st_full["cells"],
+        "full_dp_gcups": st_full["cells"] / full_ms / 1e6, "runs": runs,
+        "train": {"pairs": tr.npairs, "steps": steps, "batch": batch, "labels_s": labels_s,
+                  "train_s": train_s, "gen_s": gen_s, "loss_first": float(losses[:10].mean()),
+                  "loss_last": float(losses[-50:].mean()), "rmse_log2": info["rmse_log2"],
+                  "margin": info["margin"], "best_constant_w0": c_w0},
+    }
 
 
 def run_reference(args, rank: int):
@@ -340,6 +423,10 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(b, args.cpu_seconds)
 
+    band_res = None
+    if world == 1 and not args.no_band:
+        band_res = band_section(ga, dev, stream, args.band_pairs, args.band_train)
+
     if rank == 0:
         line = {
             "metric": "GCUPS", "value": value, "unit": "GCUPS", "n_gpus": world,
@@ -354,6 +441,7 @@ def main():
                 "l2": "inputs larger than L2 (2 x 200 MB raw codes re-read each step)",
             },
             "clocks": clocks, "roofline": roofline, "e2e": e2e, "cpu_baseline": cpu,
+            "band": band_res,
             "gpu_launches": launches, "dp_status": max(status) if status else 0,
             "pairs_int16_per_step": int16_pairs / args.steps,
         }
