@@ -30,7 +30,11 @@ GA_ERR_RANGE = 7
 EXPORTED = ("ga_align_batch", "ga_align_batch_host", "ga_align_cross", "ga_align_long",
             "ga_align_long_noalloc", "ga_align_banded", "ga_strerror", "ga_version",
             "ga_probe_issue_rate", "ga_band_features", "ga_band_min_w", "ga_band_predict",
-            "ga_mlp_forward", "ga_mlp_loss_grad", "ga_mlp_train", "ga_mlp_cast")
+            "ga_mlp_forward", "ga_mlp_loss_grad", "ga_mlp_train", "ga_mlp_cast",
+            "ga_server_create", "ga_server_add_scoring", "ga_server_submit_batch",
+            "ga_server_poll", "ga_server_drain", "ga_server_clock_ns", "ga_server_stats_get",
+            "ga_server_destroy")
+SERVE_MAX_LEN = 65536
 BAND_NFEAT = 32
 MLP_NPARAMS = 6337
 PROBES = {"vadd2": 0, "vmaxs2": 1, "viaddmax_s16x2": 2, "vimax3_s16x2": 3,
@@ -54,6 +58,26 @@ class Stats(ctypes.Structure):
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("arena_bytes", ctypes.c_int64), ("max_inflight", ctypes.c_int32),
+                ("max_tasks", ctypes.c_int32), ("device", ctypes.c_int32), ("idle_us", ctypes.c_int32)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("admitted", ctypes.c_int64),
+                ("completed", ctypes.c_int64), ("cells_completed", ctypes.c_int64),
+                ("arena_high_water", ctypes.c_int64), ("kernel_launches", ctypes.c_int64),
+                ("scheduler_ticks", ctypes.c_int64)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+RESULT_DTYPE = np.dtype([("id", np.int64), ("score", np.int32), ("status", np.int32),
+                         ("release_ns", np.int64), ("admit_ns", np.int64), ("done_ns", np.int64),
+                         ("cells", np.int64)])
 
 
 class GotohError(RuntimeError):
@@ -99,6 +123,19 @@ def load(build_if_missing: bool = False):
     lib.ga_mlp_loss_grad.argtypes = [P, P, P, i32, P, P, P]
     lib.ga_mlp_train.argtypes = [P, P, P, P, P, P, i64, P, i32, i32, i32, f32, f32, f32, f32, P, P]
     lib.ga_mlp_cast.argtypes = [P, P, P]
+    vp = ctypes.POINTER(ctypes.c_void_p)
+    lib.ga_server_create.argtypes = [ctypes.POINTER(ServerConfig), vp]
+    lib.ga_server_add_scoring.argtypes = [P, sp, ctypes.POINTER(i32)]
+    lib.ga_server_submit_batch.argtypes = [P, i64, P, P, P, P, P, P, P, ctypes.POINTER(i64)]
+    lib.ga_server_poll.argtypes = [P, P, i32, ctypes.POINTER(i32)]
+    lib.ga_server_drain.argtypes = [P, i64]
+    lib.ga_server_clock_ns.argtypes = [P]
+    lib.ga_server_clock_ns.restype = i64
+    lib.ga_server_stats_get.argtypes = [P, ctypes.POINTER(ServerStats)]
+    lib.ga_server_destroy.argtypes = [P]
+    for f in ("ga_server_create", "ga_server_add_scoring", "ga_server_submit_batch",
+              "ga_server_poll", "ga_server_drain", "ga_server_stats_get", "ga_server_destroy"):
+        getattr(lib, f).restype = i32
     for f in ("ga_align_batch", "ga_align_batch_host", "ga_align_cross", "ga_align_long",
               "ga_align_long_noalloc", "ga_align_banded", "ga_band_features", "ga_band_min_w",
               "ga_band_predict", "ga_mlp_forward", "ga_mlp_loss_grad", "ga_mlp_train",
@@ -411,3 +448,88 @@ def mlp_cast(master, params_bf16=None, stream=None):
     if rc:
         raise GotohError(rc, "ga_mlp_cast")
     return params_bf16
+
+
+class Server:
+    """Alignment server (include/gotoh_serve.h): continuous batching of requests.
+
+    Requests are host CSR arrays (copied at submission); results come back
+    through poll() as a numpy structured array (RESULT_DTYPE)."""
+
+    def __init__(self, arena_bytes: int = 0, max_inflight: int = 0, max_tasks: int = 0,
+                 device: int = 0, idle_us: int = 0):
+        cfg = ServerConfig(int(arena_bytes), int(max_inflight), int(max_tasks), int(device),
+                           int(idle_us))
+        h = ctypes.c_void_p()
+        rc = load().ga_server_create(ctypes.byref(cfg), ctypes.byref(h))
+        if rc:
+            raise GotohError(rc, "ga_server_create")
+        self._h = h
+        self._keep = []
+
+    def add_scoring(self, matrix, gap_open: int, gap_extend: int) -> int:
+        sc, keep = make_scoring(matrix, gap_open, gap_extend)
+        sid = ctypes.c_int32(-1)
+        rc = load().ga_server_add_scoring(self._h, ctypes.byref(sc), ctypes.byref(sid))
+        if rc:
+            raise GotohError(rc, "ga_server_add_scoring")
+        return int(sid.value)
+
+    def submit(self, q_codes, q_off, t_codes, t_off, modes, scoring_ids, release_ns=None) -> int:
+        """Submit requests (host arrays); returns the id of the first one."""
+        qc = np.ascontiguousarray(q_codes, dtype=np.uint8)
+        qo = np.ascontiguousarray(q_off, dtype=np.int64)
+        tc = np.ascontiguousarray(t_codes, dtype=np.uint8)
+        to = np.ascontiguousarray(t_off, dtype=np.int64)
+        n = len(qo) - 1
+        md = np.ascontiguousarray(np.broadcast_to(np.asarray(modes, dtype=np.int32), (n,)))
+        si = np.ascontiguousarray(np.broadcast_to(np.asarray(scoring_ids, dtype=np.int32), (n,)))
+        rel = None if release_ns is None else np.ascontiguousarray(release_ns, dtype=np.int64)
+        first = ctypes.c_int64(-1)
+        rc = load().ga_server_submit_batch(self._h, n, qc.ctypes.data, qo.ctypes.data, tc.ctypes.data,
+                                           to.ctypes.data, md.ctypes.data, si.ctypes.data,
+                                           None if rel is None else rel.ctypes.data,
+                                           ctypes.byref(first))
+        if rc:
+            raise GotohError(rc, "ga_server_submit_batch")
+        return int(first.value)
+
+    def poll(self, max_results: int = 1 << 16) -> np.ndarray:
+        out = np.zeros(max_results, dtype=RESULT_DTYPE)
+        cnt = ctypes.c_int32(0)
+        rc = load().ga_server_poll(self._h, out.ctypes.data, int(max_results), ctypes.byref(cnt))
+        if rc:
+            raise GotohError(rc, "ga_server_poll")
+        return out[:cnt.value]
+
+    def drain(self, timeout_ms: int = 600_000) -> None:
+        rc = load().ga_server_drain(self._h, int(timeout_ms))
+        if rc:
+            raise GotohError(rc, "ga_server_drain")
+
+    def clock_ns(self) -> int:
+        return int(load().ga_server_clock_ns(self._h))
+
+    def stats(self) -> dict:
+        st = ServerStats()
+        rc = load().ga_server_stats_get(self._h, ctypes.byref(st))
+        if rc:
+            raise GotohError(rc, "ga_server_stats_get")
+        return st.as_dict()
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            load().ga_server_destroy(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

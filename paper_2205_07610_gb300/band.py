@@ -20,12 +20,13 @@ library's CUDA kernels; this module only sequences the calls:
 from __future__ import annotations
 
 import dataclasses
+import time
 
 import numpy as np
 
 from . import _binding as B
 
-MARGINS = tuple(np.round(np.arange(-1.0, 2.01, 0.25), 2))
+MARGINS = tuple(np.round(np.arange(-0.5, 1.01, 0.25), 2))
 CONSTANT_W0 = (0, 8, 16, 32, 64, 128, 256, 512, 1024, 2048, 4096)
 
 
@@ -83,6 +84,13 @@ def train(q_codes, q_off, t_codes, t_off, matrix, gap_open, gap_extend, init_par
     """
     import torch
     dev = q_codes.device
+    times = {}
+
+    def mark(name, t0):
+        torch.cuda.synchronize(dev)
+        times[name] = time.perf_counter() - t0
+        return time.perf_counter()
+    t0 = time.perf_counter()
     if w_min is None:
         w_min, _ = labels(q_codes, q_off, t_codes, t_off, matrix, gap_open, gap_extend, stream=stream)
     w_host = w_min.cpu().numpy()
@@ -97,7 +105,9 @@ def train(q_codes, q_off, t_codes, t_off, matrix, gap_open, gap_extend, init_par
     wb = B.mlp_cast(master, stream=stream)
     am = torch.zeros_like(master)
     av = torch.zeros_like(master)
+    t0 = mark("labels_features", t0)
     losses = B.mlp_train(master, wb, am, av, x, t, torch.from_numpy(bi).to(dev), lr=lr, stream=stream)
+    t0 = mark("adam", t0)
     pred = BandPredictor(wb, 0.0)
     costs = []
     for mg in margins:
@@ -107,6 +117,7 @@ def train(q_codes, q_off, t_codes, t_off, matrix, gap_open, gap_extend, init_par
                                    w0=w0, stream=stream), float(mg)))
     cells, margin = min(costs)
     pred.margin = margin
+    t0 = mark("margin", t0)
     y = B.mlp_forward(wb, x, stream=stream)
     info = {
         "losses": losses.cpu().numpy(),
@@ -116,5 +127,6 @@ def train(q_codes, q_off, t_codes, t_off, matrix, gap_open, gap_extend, init_par
         "margin_costs": costs,
         "rmse_log2": float(torch.sqrt(torch.mean((y - t) ** 2)).item()),
         "master": master,
+        "seconds": times,
     }
     return pred, info

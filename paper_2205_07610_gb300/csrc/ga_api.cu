@@ -10,6 +10,7 @@
 #include "ga_band.cuh"
 #include "ga_banded.cuh"
 #include "ga_pool.h"
+#include "ga_serve_host.h"
 #include "ga_launch.h"
 #include "ga_prep.cuh"
 
@@ -809,7 +810,21 @@ int ga_align_cross(const uint8_t *q_codes, const int64_t *q_off, int64_t nq, con
 int ga_align_long(const uint8_t *q, int64_t m, const uint8_t *t, int64_t n, const ga_scoring *scoring,
                   int32_t mode, int32_t *score, void *stream, ga_stats *stats) {
   if (m < 0 || n < 0 || !score || (m > 0 && !q) || (n > 0 && !t)) return GA_ERR_ARG;
+  if (mode < 0 || mode > 2) return GA_ERR_ARG;
   cudaStream_t s = (cudaStream_t)stream;
+  {
+    Scoring sc;
+    const int rc = check_scoring(scoring, &sc);
+    if (rc) return rc;
+    const int64_t mn = m < n ? m : n;
+    if (m >= (1ll << 30) || n >= (1ll << 30) ||
+        2 * (int64_t)sc.alpha + (int64_t)sc.beta * (m + n) + 127 * mn >= (1ll << 30))
+      return GA_ERR_RANGE;
+    // every strip of 512 columns on its own warp, a few rows behind its
+    // left neighbour (up to 65536 residues); longer: one warp per pair
+    if (m <= 65536 && n <= 65536)
+      return sv_align_pair(q, m, t, n, sc.A, sc.mat, sc.alpha, sc.beta, mode, score, s, stats);
+  }
   int64_t *off = nullptr;
   if (pool_malloc((void **)&off, 4 * sizeof(int64_t), s) != cudaSuccess) return GA_ERR_OOM;
   fill_off_kernel<<<1, 1, 0, s>>>(off, 0, m);

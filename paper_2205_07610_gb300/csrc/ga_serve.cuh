@@ -1,0 +1,410 @@
+// ga_serve.cuh -- strip-task kernel: one warp computes one strip of 512
+// columns of one pair; the strips of a pair run on different warps (and
+// SMs) at the same time, each a few dozen rows behind its left neighbour.
+//
+// This is the paper's multi-stage partitioning of a long alignment (Sec. 3.1:
+// submatrices of the target computed left to right) spread over warps
+// instead of run by one thread group in sequence: the right edge of strip s
+// (H and the outgoing F of its last column, per row) is written to global
+// memory in batches of 32 rows and published through a per-strip progress
+// counter (release); strip s+1 waits (acquire, bounded) until the rows it
+// is about to read are published.  Rows are the shorter sequence, columns
+// the longer one.
+//
+// Tasks come from a device-resident ring: a warp claims the next task with
+// a compare-and-swap of `head` only while head < tail, so a claim is always
+// made by a running warp.  The strips of a pair are queued in order, so
+// the producer of every edge a warp waits on was claimed earlier by a warp
+// that is running: the waits end without any assumption about which blocks
+// are resident.  Every wait is bounded (globaltimer): an edge wait that
+// runs out marks the request GA_ERR_TIMEOUT and continues, an idle warp
+// exits after idle_ns, and a warp exits at once when the queue is empty and
+// `stop` is set.
+//
+// A request completes when its last strip finishes: that warp writes the
+// score to `out` (if set) and a completion record (id, score, status, seq)
+// to the completion ring, seq last.
+//
+// Substitution scores come from a per-warp int8 profile of the strip in
+// shared memory, P[c][x] = sigma(row residue c, column x), for any alphabet
+// of <= 31 symbols (Sec. 3.1, "scoring profile").  Cells are int32.
+#pragma once
+
+#include "ga_dp.cuh"
+
+namespace ga {
+
+constexpr int kSvK = 16;
+constexpr int kSvW = 32 * kSvK;  // columns per strip
+constexpr int kSvWarps = 4;      // warps per block
+constexpr int kSvMaxStrips = 128;
+constexpr int kSvMaxLen = kSvMaxStrips * kSvW;  // longer sequence <= 65536
+
+struct SvScoring {
+  int32_t A, alpha, beta, pad;
+  int8_t sigma[32 * 32];  // sigma(query code, target code), A x A row-major
+};
+
+struct SvRequest {
+  const uint8_t *q;     // device codes
+  const uint8_t *t;
+  int2 *edges;          // (nstrips - 1) edges of R + 1 int2 each
+  int32_t *out;         // nullable: the score is also stored here
+  int64_t id;
+  int32_t m, n;
+  int32_t mode, scoring;
+  int32_t nstrips;
+  int32_t score;        // local / semi: max over strips (starts 0); global: from the last strip
+  int32_t strips_done;
+  int32_t status;
+  int32_t pad[2];
+  int32_t progress[kSvMaxStrips];  // rows of each strip's edge published
+};
+
+struct SvCompletion {
+  int64_t id;
+  int32_t score, status;
+  int64_t seq;   // index + 1, written last
+  int64_t slot;  // request slot (host bookkeeping)
+};
+
+struct SvParams {
+  SvRequest *req;
+  const SvScoring *scorings;
+  const int2 *tasks;  // (slot, strip)
+  int64_t task_cap;
+  unsigned long long *head;
+  const unsigned long long *tail;
+  SvCompletion *comp;  // nullable
+  int64_t comp_cap;
+  unsigned long long *comp_count;
+  const int32_t *stop;
+  int64_t idle_ns;
+  int64_t wait_ns;
+  int32_t prof_bytes;  // per warp: (max A + 1) * kSvW
+};
+
+__device__ __forceinline__ uint64_t sv_now() {
+  uint64_t v;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(v));
+  return v;
+}
+__device__ __forceinline__ int sv_ld_acquire(const int32_t *p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ unsigned long long sv_ld_acquire64(const unsigned long long *p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void sv_st_release(int32_t *p, int v) {
+  asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ int sv_ld_sys(const int32_t *p) {
+  int v;
+  asm volatile("ld.relaxed.sys.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+struct SvView {
+  const uint8_t *rowraw, *colraw;
+  int2 *edges;
+  int R, C, sw, A, alpha, beta, nstrips;
+  const int8_t *sigma;
+};
+
+// One strip of one request; returns the strip's contribution to the score
+// (local: best H; semi: max of row R; global: H(R, C) on the lane that owns
+// column C, else INT_MIN).
+template <int MODE>
+__device__ int sv_strip(const SvParams &p, SvRequest *rq, const SvView &v, int s, int t, uint8_t *prof,
+                        uint8_t *colc, int2 *in_ring, int2 *out_ring, uint32_t *row_ring) {
+  using Cell = CellS32;
+  using T = int32_t;
+  constexpr int K = kSvK, W = kSvW;
+  constexpr int kNeg = kNeg32;
+  const int R = v.R, C = v.C, A = v.A, alpha = v.alpha, beta = v.beta;
+  const T NB = -beta;
+  const int col0 = s * W;
+  const int2 *edge_in = (s > 0) ? v.edges + (size_t)(s - 1) * (size_t)(R + 1) : nullptr;
+  int2 *edge_out = (s + 1 < v.nstrips) ? v.edges + (size_t)s * (size_t)(R + 1) : nullptr;
+
+  // ---- column codes and the strip's profile ---------------------------
+  for (int x = t; x < W; x += 32) {
+    const int col = col0 + x;
+    int c = A;  // pad
+    if (col < C) {
+      c = __ldcg(v.colraw + col);
+      if (c >= A) {
+        atomicCAS(&rq->status, 0, GA_ERR_RESIDUE);
+        c = A;
+      }
+    }
+    colc[x] = (uint8_t)c;
+  }
+  __syncwarp();
+  for (int e = t; e < (A + 1) * W; e += 32) {
+    const int c = e / W, x = e - c * W;
+    const int cc = colc[x];
+    int val = 0;
+    if (c < A && cc < A) val = v.sw ? v.sigma[cc * A + c] : v.sigma[c * A + cc];
+    prof[e] = (uint8_t)(int8_t)val;
+  }
+
+  T na[MODE == kModeSemi ? K : 1];
+  T H[K], E[K];
+#pragma unroll
+  for (int j = 0; j < K; ++j) {
+    const int col = col0 + t * K + j;
+    if constexpr (MODE == kModeSemi) na[j] = (col == C - 1) ? 0 : -alpha;
+    H[j] = (MODE == kModeGlobal) ? ::max(-alpha - beta * col, kNeg) : 0;  // H(0, col+1)
+    E[j] = ::max(H[j] - alpha, kNeg);
+  }
+  const int ocol = C - 1 - col0 - t * K;  // local index of column C, if in this tile
+  T best = 0;
+  int rowmax = 0, gscore = INT_MIN;
+
+  auto left_row = [&](int r) -> int2 {  // (H(r, col0), F(r, col0+1))
+    int2 lv;
+    if (s == 0) {
+      lv.x = (MODE == kModeGlobal) ? ((r == 0) ? 0 : ::max(-alpha - beta * (r - 1), kNeg)) : 0;
+      lv.y = ::max(lv.x - alpha, kNeg);
+    } else {
+      lv = in_ring[(r - 1) & 63];
+    }
+    return lv;
+  };
+  // rows 32b+1 .. 32b+32 of the left edge -> in_ring, after waiting for them
+  auto load_batch = [&](int b) {
+    if (s == 0) return;
+    const int need = ::min(R, 32 * b + 32);
+    if (32 * b + 1 > R) return;
+    const int32_t *pp = &rq->progress[s - 1];
+    if (t == 0 && sv_ld_acquire(pp) < need) {
+      const uint64_t t0 = sv_now();
+      unsigned ns = 32;
+      while (sv_ld_acquire(pp) < need) {
+        if (sv_now() - t0 > (uint64_t)p.wait_ns) {
+          atomicCAS(&rq->status, 0, GA_ERR_TIMEOUT);
+          break;
+        }
+        __nanosleep(ns);
+        if (ns < 2048) ns *= 2;
+      }
+    }
+    __syncwarp();
+    (void)sv_ld_acquire(pp);  // every lane orders its edge loads after the flag
+    const int r = 32 * b + 1 + t;
+    if (r <= R) in_ring[(r - 1) & 63] = __ldcg(edge_in + r);
+  };
+  auto fill_rows = [&](int b) {  // row codes, 4 batches of 32 in flight
+    const int r = 32 * b + 1 + t;
+    uint32_t c = (uint32_t)A;
+    if (r <= R) {
+      c = __ldcg(v.rowraw + r - 1);
+      if (c >= (uint32_t)A) {
+        atomicCAS(&rq->status, 0, GA_ERR_RESIDUE);
+        c = (uint32_t)A;
+      }
+    }
+    row_ring[r & 127] = c;
+  };
+  auto publish = [&](int rows) {  // edge rows 1..rows are in global memory
+    __threadfence();
+    __syncwarp();
+    if (t == 0) sv_st_release(&rq->progress[s], rows);
+  };
+
+  load_batch(0);
+  fill_rows(0);
+  fill_rows(1);
+  __syncwarp();
+
+  const int h00 = (MODE == kModeGlobal && col0 > 0) ? ::max(-alpha - beta * (col0 - 1), kNeg) : 0;
+  int hdt = 0;  // H(0, col0 + t*K)
+  if constexpr (MODE == kModeGlobal)
+    hdt = (col0 + t * K == 0) ? 0 : ::max(-alpha - beta * (col0 + t * K - 1), kNeg);
+  const int2 l1 = left_row(1);
+  T Hdiag = (t == 0) ? h00 : hdt;
+  T Hleft = (t == 0) ? l1.x : hdt;
+  T Fin = (t == 0) ? l1.y : kNeg;
+
+  const int nit = R + 31;
+  for (int it = 0; it < nit; ++it) {
+    if ((it & 31) == 0) {
+      __syncwarp();
+      load_batch(it / 32 + 1);
+      fill_rows(it / 32 + 2);
+      if (it >= 64 && edge_out) {  // flush lane-31 rows it-63 .. it-32
+        const int r = it - 63 + t;
+        edge_out[r] = out_ring[(r - 1) & 63];
+        publish(it - 32);
+      }
+      __syncwarp();
+    }
+    const int r = it - t + 1;
+    T Hout, Fout;
+    if ((unsigned)(r - 1) < (unsigned)R) {
+      const uint32_t rv = row_ring[r & 127];
+      const uint4 *pr = reinterpret_cast<const uint4 *>(prof + (size_t)rv * W + t * K);
+      const uint4 q4 = *pr;
+      const uint32_t w[4] = {q4.x, q4.y, q4.z, q4.w};
+      Fout = dp_row<Cell, MODE, K>(
+          H, E, Hdiag, Fin, NB, best,
+          [&](int j) -> T { return (T)prmt(w[j >> 2], 0u, sext_sel<Cell>(j & 3)); },
+          [&](int j) -> T {
+            if constexpr (MODE == kModeSemi) return na[j];
+            else return -alpha;
+          });
+      Hout = H[K - 1];
+      if (r == R) {
+        if constexpr (MODE == kModeGlobal) {
+          if (ocol >= 0 && ocol < K) {
+            T g = H[0];
+#pragma unroll
+            for (int j = 1; j < K; ++j)
+              if (j == ocol) g = H[j];
+            gscore = g;
+          }
+        } else if constexpr (MODE == kModeSemi) {
+#pragma unroll
+          for (int j = 0; j < K; ++j) rowmax = ::max(rowmax, H[j]);
+        }
+      }
+    } else {
+      Hout = H[K - 1];
+      Fout = kNeg;
+    }
+    if (t == 31 && r >= 1 && r <= R) out_ring[(r - 1) & 63] = make_int2(Hout, Fout);
+    Hdiag = Hleft;
+    Hleft = __shfl_up_sync(0xffffffffu, Hout, 1);
+    Fin = __shfl_up_sync(0xffffffffu, Fout, 1);
+    if (t == 0) {
+      const int2 lv = (it + 2 <= R) ? left_row(it + 2) : make_int2(0, kNeg);
+      Hleft = lv.x;
+      Fin = lv.y;
+    }
+  }
+  __syncwarp();
+  if (edge_out) {  // remaining lane-31 rows, then the whole edge is published
+    const int first = (nit >= 64) ? ((nit - 1) / 32) * 32 - 63 + 32 : 1;
+    for (int r = first + t; r <= R; r += 32) edge_out[r] = out_ring[(r - 1) & 63];
+    publish(R);
+  }
+  __syncwarp();
+  if constexpr (MODE == kModeLocal) return group_max<32>(best);
+  else if constexpr (MODE == kModeSemi) return group_max<32>(rowmax);
+  else return __reduce_max_sync(0xffffffffu, gscore);
+}
+
+__global__ void __launch_bounds__(32 * kSvWarps) ks_kernel(const __grid_constant__ SvParams p) {
+  extern __shared__ __align__(16) uint8_t sv_smem[];
+  __shared__ int2 in_ring_s[kSvWarps][64];
+  __shared__ int2 out_ring_s[kSvWarps][64];
+  __shared__ uint32_t row_ring_s[kSvWarps][128];
+  __shared__ __align__(16) uint8_t colc_s[kSvWarps][kSvW];
+  const int warp = threadIdx.x >> 5, t = threadIdx.x & 31;
+  uint8_t *prof = sv_smem + (size_t)warp * (size_t)p.prof_bytes;
+
+  for (;;) {
+    // ---- claim the next task (lane 0), bounded idle wait ----------------
+    int slot = -1, strip = 0, quit = 0;
+    if (t == 0) {
+      uint64_t idle0 = 0;
+      unsigned ns = 64;
+      for (;;) {
+        const unsigned long long tl = sv_ld_acquire64(p.tail);
+        const unsigned long long h = *(volatile unsigned long long *)p.head;
+        if (h < tl) {
+          if (atomicCAS(p.head, h, h + 1) == h) {
+            const int2 tk = __ldcg(p.tasks + (int64_t)(h % (unsigned long long)p.task_cap));
+            slot = tk.x;
+            strip = tk.y;
+            break;
+          }
+          continue;
+        }
+        if (sv_ld_sys(p.stop)) {
+          quit = 1;
+          break;
+        }
+        const uint64_t now = sv_now();
+        if (!idle0) idle0 = now;
+        else if (now - idle0 > (uint64_t)p.idle_ns) {
+          quit = 1;
+          break;
+        }
+        __nanosleep(ns);
+        if (ns < 4096) ns *= 2;
+      }
+    }
+    quit = __shfl_sync(0xffffffffu, quit, 0);
+    if (quit) break;
+    slot = __shfl_sync(0xffffffffu, slot, 0);
+    strip = __shfl_sync(0xffffffffu, strip, 0);
+
+    SvRequest *rq = p.req + slot;
+    const int m = __ldcg(&rq->m), n = __ldcg(&rq->n);
+    const int mode = __ldcg(&rq->mode), sc = __ldcg(&rq->scoring);
+    SvView v;
+    v.sw = m > n;
+    v.R = v.sw ? n : m;
+    v.C = v.sw ? m : n;
+    v.rowraw = v.sw ? (const uint8_t *)__ldcg((const unsigned long long *)&rq->t)
+                    : (const uint8_t *)__ldcg((const unsigned long long *)&rq->q);
+    v.colraw = v.sw ? (const uint8_t *)__ldcg((const unsigned long long *)&rq->q)
+                    : (const uint8_t *)__ldcg((const unsigned long long *)&rq->t);
+    v.nstrips = __ldcg(&rq->nstrips);
+    v.edges = (int2 *)__ldcg((const unsigned long long *)&rq->edges);
+    v.A = __ldcg(&p.scorings[sc].A);
+    v.alpha = __ldcg(&p.scorings[sc].alpha);
+    v.beta = __ldcg(&p.scorings[sc].beta);
+    v.sigma = p.scorings[sc].sigma;
+
+    int val;
+    if (v.R == 0 || v.C == 0) {  // closed forms, any mode
+      const int len = v.R + v.C;
+      val = (mode == kModeGlobal && len) ? -(v.alpha + v.beta * (len - 1)) : 0;
+    } else if (mode == kModeLocal) {
+      val = sv_strip<kModeLocal>(p, rq, v, strip, t, prof, colc_s[warp], in_ring_s[warp],
+                                 out_ring_s[warp], row_ring_s[warp]);
+    } else if (mode == kModeGlobal) {
+      val = sv_strip<kModeGlobal>(p, rq, v, strip, t, prof, colc_s[warp], in_ring_s[warp],
+                                  out_ring_s[warp], row_ring_s[warp]);
+    } else {
+      val = sv_strip<kModeSemi>(p, rq, v, strip, t, prof, colc_s[warp], in_ring_s[warp],
+                                out_ring_s[warp], row_ring_s[warp]);
+    }
+    if (t == 0) {
+      if (mode == kModeGlobal) {
+        if (strip + 1 == v.nstrips || v.R == 0 || v.C == 0) atomicExch(&rq->score, val);
+      } else {
+        atomicMax(&rq->score, val);
+      }
+      __threadfence();
+      const int done = atomicAdd(&rq->strips_done, 1) + 1;
+      if (done == v.nstrips) {
+        __threadfence();
+        const int score = atomicAdd(&rq->score, 0);
+        const int status = atomicAdd(&rq->status, 0);
+        int32_t *out = (int32_t *)__ldcg((const unsigned long long *)&rq->out);
+        if (out) *out = status ? INT_MIN : score;
+        if (p.comp) {
+          const unsigned long long idx = atomicAdd(p.comp_count, 1ull);
+          SvCompletion *c = p.comp + (int64_t)(idx % (unsigned long long)p.comp_cap);
+          c->id = __ldcg(&rq->id);
+          c->score = status ? INT_MIN : score;
+          c->status = status;
+          c->slot = slot;
+          __threadfence_system();
+          *(volatile int64_t *)&c->seq = (int64_t)idx + 1;
+        }
+      }
+    }
+    __syncwarp();
+  }
+}
+
+}  // namespace ga

@@ -139,7 +139,8 @@ def random_sequences(rng, lengths, alphabet_size=4, freqs=None):
     return codes, off
 
 
-def mutate(rng, codes, off, p_event, indel_frac, alphabet_size=4, freqs=None):
+def mutate(rng, codes, off, p_event, indel_frac, alphabet_size=4, freqs=None,
+           chunk_residues=1 << 23):
     """Mutated copies of the sequences codes[off[k]:off[k+1]].
 
     Per position an event happens with probability p_event[k]; an event is an
@@ -147,29 +148,47 @@ def mutate(rng, codes, off, p_event, indel_frac, alphabet_size=4, freqs=None):
     or deletion starting at it, length ~ Geometric(0.5) on {1,2,...},
     deletions clipped at the sequence end), otherwise a substitution by a
     different residue (uniform among the others, or drawn from ``freqs``
-    conditioned on differing).  Returns (codes, off) of the copies.
+    conditioned on differing).  Returns (codes, off) of the copies.  The
+    sequences are processed in groups of about chunk_residues residues.
     """
+    nseq = len(off) - 1
+    pe = np.broadcast_to(np.asarray(p_event, dtype=np.float64), (nseq,))
+    fi = np.broadcast_to(np.asarray(indel_frac, dtype=np.float64), (nseq,))
+    outs, lens = [], []
+    k = 0
+    while k < nseq:
+        k2 = int(np.searchsorted(off, off[k] + chunk_residues, side="right")) - 1
+        k2 = min(max(k2, k + 1), nseq)
+        sub_off = off[k:k2 + 1] - off[k]
+        c, o = _mutate_core(rng, codes[off[k]:off[k2]], sub_off, pe[k:k2], fi[k:k2], alphabet_size,
+                            freqs)
+        outs.append(c)
+        lens.append(np.diff(o))
+        k = k2
+    if not outs:
+        return np.zeros(0, dtype=np.uint8), np.zeros(nseq + 1, dtype=np.int64)
+    new_off = np.zeros(nseq + 1, dtype=np.int64)
+    np.cumsum(np.concatenate(lens), out=new_off[1:])
+    return np.concatenate(outs), new_off
+
+
+def _mutate_core(rng, codes, off, pe, fi, alphabet_size, freqs):
     nseq = len(off) - 1
     lens = np.diff(off)
     N = int(off[-1])
     seq_id = np.repeat(np.arange(nseq, dtype=np.int64), lens)
-    pe = np.asarray(p_event, dtype=np.float64)
-    fi = np.asarray(indel_frac, dtype=np.float64)
-    pe = np.broadcast_to(pe, (nseq,))[seq_id] if pe.ndim else np.full(N, float(pe))
-    fi = np.broadcast_to(fi, (nseq,))[seq_id] if fi.ndim else np.full(N, float(fi))
-    u = rng.random(N)
-    event = u < pe
-    v = rng.random(N)
-    indel = event & (v < fi)
-    sub = event & ~indel
-    ins_or_del = rng.random(N) < 0.5
-    ins = indel & ins_or_del
-    dele = indel & ~ins_or_del
-    glen = rng.geometric(0.5, size=N).astype(np.int64)
+    event = rng.random(N, dtype=np.float32) < pe.astype(np.float32)[seq_id]
+    eidx = np.nonzero(event)[0]
+    is_indel = rng.random(len(eidx)) < fi[seq_id[eidx]]
+    is_ins = rng.random(len(eidx)) < 0.5
+    sidx = eidx[~is_indel]
+    iidx = eidx[is_indel & is_ins]
+    didx = eidx[is_indel & ~is_ins]
+    ilen = rng.geometric(0.5, size=len(iidx)).astype(np.int64)
+    dlen = rng.geometric(0.5, size=len(didx)).astype(np.int64)
 
     out = codes.copy()
     # substitutions
-    sidx = np.nonzero(sub)[0]
     if len(sidx):
         if freqs is None:
             shift = rng.integers(1, alphabet_size, size=len(sidx))
@@ -184,31 +203,30 @@ def mutate(rng, codes, off, p_event, indel_frac, alphabet_size=4, freqs=None):
                 same = new == out[sidx]
             out[sidx] = new
     # deletions: positions [x, min(x+L, end)) removed
-    diff = np.zeros(N + 1, dtype=np.int64)
-    didx = np.nonzero(dele)[0]
+    diff = np.zeros(N + 1, dtype=np.int32)
     if len(didx):
-        ends = np.minimum(didx + glen[didx], off[seq_id[didx] + 1])
+        ends = np.minimum(didx + dlen, off[seq_id[didx] + 1])
         np.add.at(diff, didx, 1)
         np.add.at(diff, ends, -1)
-    deleted = np.cumsum(diff[:N]) > 0
-    keep = (~deleted).astype(np.int64)
-    ins_count = np.where(ins, glen, 0)
-    per_pos = keep + ins_count
+    per_pos = (np.cumsum(diff[:N]) == 0).astype(np.int64)  # kept residues
+    per_pos[iidx] += ilen                                    # insertions before the position
+    ins_count = np.zeros(N, dtype=np.int64)
+    ins_count[iidx] = ilen
     total = int(per_pos.sum())
     start = np.zeros(N + 1, dtype=np.int64)
     np.cumsum(per_pos, out=start[1:])
     src = np.repeat(np.arange(N, dtype=np.int64), per_pos)
     rank = np.arange(total, dtype=np.int64) - start[src]
-    is_ins = rank < ins_count[src]
+    is_new = rank < ins_count[src]
     new = np.empty(total, dtype=np.uint8)
-    n_ins = int(is_ins.sum())
+    n_ins = int(is_new.sum())
     if freqs is None:
-        new[is_ins] = rng.integers(0, alphabet_size, size=n_ins, dtype=np.uint8)
+        new[is_new] = rng.integers(0, alphabet_size, size=n_ins, dtype=np.uint8)
     else:
         cdf = np.cumsum(freqs)
         cdf[-1] = 1.0
-        new[is_ins] = np.searchsorted(cdf, rng.random(n_ins), side="right").astype(np.uint8)
-    new[~is_ins] = out[src[~is_ins]]
+        new[is_new] = np.searchsorted(cdf, rng.random(n_ins), side="right").astype(np.uint8)
+    new[~is_new] = out[src[~is_new]]
     out_len = start[off[1:]] - start[off[:-1]]
     new_off = np.zeros(nseq + 1, dtype=np.int64)
     np.cumsum(out_len, out=new_off[1:])
@@ -297,6 +315,25 @@ def long_dna_pairs(npairs=20_000, lmin=1000, lmax=20000, dmin=0.01, dmax=0.15, f
                  alpha, beta, f"dna-long-{npairs}-{lmin}-{lmax}", seed)
 
 
+def _interleave(n, parts):
+    """Merge CSR sets whose sequences belong to request indices idx into one
+    CSR in request order."""
+    lens = np.zeros(n, dtype=np.int64)
+    for idx, _, off in parts:
+        lens[idx] = np.diff(off)
+    out_off = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
+    out = np.empty(int(out_off[-1]), dtype=np.uint8)
+    for idx, codes, off in parts:
+        ln = np.diff(off)
+        tot = int(ln.sum())
+        if not tot:
+            continue
+        # destination of every residue: request start + position in request
+        dst = np.repeat(out_off[idx] - off[:-1], ln) + np.arange(off[0], off[0] + tot)
+        out[dst] = codes[off[0]:off[0] + tot]
+    return out, out_off
+
+
 def serving_stream(nreq=200_000, rate=1.0e4, median=1000, sigma=1.2, lmin=100, lmax=50_000,
                    frac_dna=0.6, seed=SEED_BASE + 5) -> Stream:
     """Configuration 5: Poisson request stream of mixed DNA/protein pairs."""
@@ -307,7 +344,7 @@ def serving_stream(nreq=200_000, rate=1.0e4, median=1000, sigma=1.2, lmin=100, l
     protein = rng.random(nreq) >= frac_dna
     mode = np.where(rng.random(nreq) < 0.5, 0, 1).astype(np.int32)  # 0 local, 1 global
     bg = np.concatenate([PROTEIN_BACKGROUND, np.zeros(4)])
-    q_parts, t_parts = [None] * nreq, [None] * nreq
+    parts = []  # (request indices, q CSR, t CSR) per alphabet
     for is_prot in (False, True):
         idx = np.nonzero(protein == is_prot)[0]
         if not len(idx):
@@ -318,10 +355,8 @@ def serving_stream(nreq=200_000, rate=1.0e4, median=1000, sigma=1.2, lmin=100, l
         else:
             qc, qo = random_sequences(rng, lens[idx])
             tc, to = mutate(rng, qc, qo, 0.06, 1.0 / 6.0)
-        for k, r in enumerate(idx):
-            q_parts[r] = qc[qo[k]:qo[k + 1]]
-            t_parts[r] = tc[to[k]:to[k + 1]]
-    qc, qo = pack_csr(q_parts)
-    tc, to = pack_csr(t_parts)
+        parts.append((idx, qc, qo, tc, to))
+    qc, qo = _interleave(nreq, [(p[0], p[1], p[2]) for p in parts])
+    tc, to = _interleave(nreq, [(p[0], p[3], p[4]) for p in parts])
     return Stream(arrival, qc, qo, tc, to, protein, mode, (dna_matrix(2, -3), 5, 2),
                   (blosum62(), 11, 1), seed)
