@@ -8,7 +8,9 @@ metric is GCUPS: full-DP cells (sum of m*n, both modes) per second.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
-The line also carries "band": the learned-band vs full-DP time to exact global
+The line also carries "serve": p50/p99 latency and GCUPS of a Poisson stream
+of 200k mixed requests through the alignment server (--no-serve skips it),
+and "band": the learned-band vs full-DP time to exact global
 scores on 20k long DNA pairs (|Q| ~ U{1000..20000}, divergence 1-15 %), with
 the band predictor trained first on its own seeded pairs (--no-band skips it).
 
@@ -57,6 +59,8 @@ def parse_args():
     ap.add_argument("--no-band", action="store_true", help="skip the learned-band measurement")
     ap.add_argument("--band-pairs", type=int, default=20_000)
     ap.add_argument("--band-train", type=int, default=4_000)
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
+    ap.add_argument("--serve-requests", type=int, default=200_000)
     return ap.parse_args()
 
 
@@ -253,7 +257,80 @@ def band_section(ga, dev, stream, npairs: int, ntrain: int, reps: int = 3):
         "train": {"pairs": tr.npairs, "steps": steps, "batch": batch, "labels_s": labels_s,
                   "train_s": train_s, "gen_s": gen_s, "loss_first": float(losses[:10].mean()),
                   "loss_last": float(losses[-50:].mean()), "rmse_log2": info["rmse_log2"],
-                  "margin": info["margin"], "best_constant_w0": c_w0},
+                  "margin": info["margin"], "best_constant_w0": c_w0,
+                  "phase_s": info["seconds"]},
+    }
+
+
+def serve_section(ga, dev, nreq: int, load: float = 0.7, burst: int = 50_000):
+    """Serving: a Poisson stream of mixed requests through the alignment server.
+
+    Capacity is measured first with a burst (the first `burst` requests
+    released at once); the stream's arrival times are then rescaled to
+    `load` x that capacity and replayed (release times on the server clock).
+    Latency = completion seen by the scheduler - release.  Every score is
+    checked against ga_align_batch of the same pairs.
+    """
+    import torch
+    t0 = time.perf_counter()
+    s = synth.serving_stream(nreq=nreq)
+    gen_s = time.perf_counter() - t0
+    cells = np.diff(s.q_off) * np.diff(s.t_off)
+    with ga.Server(arena_bytes=32 << 30, max_inflight=65536, max_tasks=1 << 22,
+                   device=dev.index or 0) as srv:
+        d = srv.add_scoring(*s.dna_scoring)
+        p = srv.add_scoring(*s.protein_scoring)
+        sid = np.where(s.protein, p, d).astype(np.int32)
+        nb = min(burst, s.nreq)
+        t0 = time.perf_counter()
+        srv.submit(s.q_codes, s.q_off[:nb + 1], s.t_codes, s.t_off[:nb + 1], s.mode[:nb], sid[:nb])
+        srv.drain(600_000)
+        burst_s = time.perf_counter() - t0
+        srv.poll(nb + 16)
+        cap_req_s = nb / burst_s
+        cap_gcups = float(cells[:nb].sum()) / burst_s / 1e9
+        rate = load * cap_req_s
+        arr = (s.arrival - s.arrival[0]) * (1.0e4 / rate)  # generator rate is 1e4/s
+        start = srv.clock_ns() + 5_000_000
+        rel = (start + arr * 1e9).astype(np.int64)
+        srv.submit(s.q_codes, s.q_off, s.t_codes, s.t_off, s.mode, sid, rel)
+        srv.drain(600_000)
+        res = srv.poll(s.nreq + 16)
+        st = srv.stats()
+    res = res[np.argsort(res["id"])]
+    lat_ms = (res["done_ns"] - res["release_ns"]) / 1e6
+    wait_ms = (res["admit_ns"] - res["release_ns"]) / 1e6   # host: memory / slot admission
+    dev_ms = (res["done_ns"] - res["admit_ns"]) / 1e6       # device queue + strips
+    span_s = (res["done_ns"].max() - res["release_ns"].min()) / 1e9
+    # exactness: the same pairs through ga_align_batch, grouped by scoring and mode
+    exact = True
+    scores = res["score"].astype(np.int64)
+    for prot in (False, True):
+        for md in (0, 1):
+            idx = np.nonzero((s.protein == prot) & (s.mode == md))[0]
+            if not len(idx):
+                continue
+            mat, al, be = s.protein_scoring if prot else s.dna_scoring
+            qc, qo = synth.pack_csr([s.q_codes[s.q_off[i]:s.q_off[i + 1]] for i in idx])
+            tc, to = synth.pack_csr([s.t_codes[s.t_off[i]:s.t_off[i + 1]] for i in idx])
+            ref = ga.align_batch(*(torch.from_numpy(a).to(dev) for a in (qc, qo, tc, to)), mat, al, be,
+                                 "global" if md else "local")
+            exact &= bool(np.array_equal(ref.cpu().numpy().astype(np.int64), scores[idx]))
+    return {
+        "metric": "serve latency p50 / p99 (ms) at the offered load", "higher_is_better": False,
+        "workload": f"{s.nreq} requests, Poisson arrivals at {load:.0%} of measured capacity, "
+                    "lengths LogNormal(median 1000, sigma 1.2) in [100, 50000], 60% DNA (+2/-3, 5/2) "
+                    "/ 40% protein (BLOSUM62, 11/1), 50/50 local/global",
+        "p50_ms": float(np.percentile(lat_ms, 50)), "p90_ms": float(np.percentile(lat_ms, 90)),
+        "p99_ms": float(np.percentile(lat_ms, 99)), "max_ms": float(lat_ms.max()),
+        "admit_wait_p50_ms": float(np.percentile(wait_ms, 50)),
+        "admit_wait_p99_ms": float(np.percentile(wait_ms, 99)),
+        "device_p50_ms": float(np.percentile(dev_ms, 50)), "device_p99_ms": float(np.percentile(dev_ms, 99)),
+        "gcups": float(cells.sum()) / span_s / 1e9, "offered_req_s": rate,
+        "capacity_req_s": cap_req_s, "capacity_gcups": cap_gcups, "span_s": span_s,
+        "exact": exact, "status_errors": int((res["status"] != 0).sum()),
+        "kernel_launches": st["kernel_launches"], "arena_high_water": st["arena_high_water"],
+        "gen_s": gen_s,
     }
 
 
@@ -426,6 +503,9 @@ def main():
     band_res = None
     if world == 1 and not args.no_band:
         band_res = band_section(ga, dev, stream, args.band_pairs, args.band_train)
+    serve_res = None
+    if world == 1 and not args.no_serve:
+        serve_res = serve_section(ga, dev, args.serve_requests)
 
     if rank == 0:
         line = {
@@ -441,7 +521,7 @@ def main():
                 "l2": "inputs larger than L2 (2 x 200 MB raw codes re-read each step)",
             },
             "clocks": clocks, "roofline": roofline, "e2e": e2e, "cpu_baseline": cpu,
-            "band": band_res,
+            "band": band_res, "serve": serve_res,
             "gpu_launches": launches, "dp_status": max(status) if status else 0,
             "pairs_int16_per_step": int16_pairs / args.steps,
         }

@@ -163,9 +163,9 @@ def test_server_rejects_bad_requests():
             srv.submit(q[:10], [0, 10], q[:10], [0, 10], [0], [d + 5])
         with pytest.raises(ga.GotohError):
             srv.submit(q[:10], [0, 10], q[:10], [0, 10], [3], [d])
-        big = np.zeros(30000, dtype=np.uint8)  # strip edges of 30000 x 30000 exceed the arena
+        big = np.zeros(40000, dtype=np.uint8)  # 78 strip edges of 40001 rows: 25 MB > 16 MB arena
         with pytest.raises(ga.GotohError):
-            srv.submit(big, [0, 30000], big, [0, 30000], [1], [d])
+            srv.submit(big, [0, 40000], big, [0, 40000], [1], [d])
         # a residue outside the alphabet is reported per request
         bad = np.full(20, 7, dtype=np.uint8)
         srv.submit(bad, [0, 20], q[:10], [0, 10], [1], [d])
