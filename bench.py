@@ -39,6 +39,10 @@ import synth  # noqa: E402
 # int16 operations per cell in the paper's count for global / semi-global
 # affine alignment (Sec. 4.2: 4 max + 3 add/sub); local adds 2.
 OPS_PER_CELL = 7
+# DRAM bytes (read + write) of one launch of the dominant DP kernel,
+# ka_kernel<CellS16x2, semi, 16, 18>, on this batch: one ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum) of the current kernel code.
+KA_TRAFFIC_BYTES = 79.596032e6 + 2.576640e6
 PEAK_SM_MHZ = 2070.0     # maximum SM clock of a GB300
 N_SM = 152
 LANES_PER_SM = 128       # 4 SM sub-partitions x 32 lanes, one integer op each per clock
@@ -460,8 +464,10 @@ def main():
     roofline = {
         "bound": "alu", "achieved": achieved_ops / 1e12, "peak": peak_ops / 1e12,
         "unit": "Tops/s (int16, 7 ops per cell)", "frac": achieved_ops / peak_ops,
-        "traffic": None,
-        "kernel": "ka_kernel<CellS16x2> (inter-sequence, packed int16x2)",
+        "traffic": KA_TRAFFIC_BYTES,
+        "traffic_unit": "bytes per launch of ka_kernel<CellS16x2, semi, 16, 18> (ncu)",
+        "kernel": "ka_kernel<CellS16x2> (inter-sequence, packed int16x2); achieved and peak "
+                  "over all of its launches in the timed region",
         "dp_gcups": step_cells * args.steps / (dp_ms / 1e3) / 1e9 if dp_ms > 0 else None,
         "dp_launches_per_step": dp_launches / args.steps,
         "peak_gcups_at_7_ops": peak_ops / OPS_PER_CELL / 1e9,
