@@ -295,7 +295,10 @@ def serve_section(ga, dev, nreq: int, load: float = 0.7, burst: int = 50_000):
         cap_gcups = float(cells[:nb].sum()) / burst_s / 1e9
         rate = load * cap_req_s
         arr = (s.arrival - s.arrival[0]) * (1.0e4 / rate)  # generator rate is 1e4/s
-        start = srv.clock_ns() + 5_000_000
+        st_burst = srv.stats()
+        # the stream starts 2 s after submission begins: submitting copies the
+        # whole stream (~0.8 GB), which must not eat into the first arrivals
+        start = srv.clock_ns() + 2_000_000_000
         rel = (start + arr * 1e9).astype(np.int64)
         srv.submit(s.q_codes, s.q_off, s.t_codes, s.t_off, s.mode, sid, rel)
         srv.drain(600_000)
@@ -334,6 +337,8 @@ def serve_section(ga, dev, nreq: int, load: float = 0.7, burst: int = 50_000):
         "capacity_req_s": cap_req_s, "capacity_gcups": cap_gcups, "span_s": span_s,
         "exact": exact, "status_errors": int((res["status"] != 0).sum()),
         "kernel_launches": st["kernel_launches"], "arena_high_water": st["arena_high_water"],
+        "burst_scheduler_s": {k: st_burst[k] / 1e9 for k in ("admit_host_ns", "copy_ns", "complete_ns")},
+        "burst_ticks": st_burst["scheduler_ticks"],
         "gen_s": gen_s,
     }
 

@@ -62,6 +62,9 @@ typedef struct {
     int64_t arena_high_water;    /* bytes */
     int64_t kernel_launches;     /* launches of the persistent kernel */
     int64_t scheduler_ticks;
+    int64_t admit_host_ns;       /* scheduler time: admission decisions and staging */
+    int64_t copy_ns;             /* scheduler time: copies in and publication */
+    int64_t complete_ns;         /* scheduler time: completion records */
 } ga_server_stats;
 
 /* Create a server on cfg->device; *out receives the handle.  GA_ERR_OOM

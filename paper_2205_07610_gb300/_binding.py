@@ -69,7 +69,8 @@ class ServerStats(ctypes.Structure):
     _fields_ = [("submitted", ctypes.c_int64), ("admitted", ctypes.c_int64),
                 ("completed", ctypes.c_int64), ("cells_completed", ctypes.c_int64),
                 ("arena_high_water", ctypes.c_int64), ("kernel_launches", ctypes.c_int64),
-                ("scheduler_ticks", ctypes.c_int64)]
+                ("scheduler_ticks", ctypes.c_int64), ("admit_host_ns", ctypes.c_int64),
+                ("copy_ns", ctypes.c_int64), ("complete_ns", ctypes.c_int64)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -32,11 +32,16 @@ cudaError_t sv_prepare_launch(size_t smem, int *blocks_per_sm) {
 __global__ void sv_oneshot_init_kernel(SvRequest *rq, SvScoring *sc_out, const SvScoring sc,
                                        const uint8_t *q, const uint8_t *t, int2 *edges, int32_t *out,
                                        int m, int n, int mode, int nstrips, int2 *tasks,
-                                       unsigned long long *head_tail, int32_t *stop) {
+                                       unsigned long long *ctr, unsigned long long *cont_seq,
+                                       int32_t *stop) {
   const int i = threadIdx.x;
-  for (int k = i; k < kSvMaxStrips; k += blockDim.x) rq->progress[k] = 0;
-  for (int k = i; k < nstrips; k += blockDim.x) tasks[k] = make_int2(0, k);
+  for (int k = i; k < kSvMaxStrips; k += blockDim.x) {
+    rq->progress[k] = 0;
+    cont_seq[k] = 0;
+  }
+  if (i < 8) ctr[i] = 0;
   if (i == 0) {
+    tasks[0] = make_int2(0, 0);  // strip 0; the strips after it come as continuations
     *sc_out = sc;
     rq->q = q;
     rq->t = t;
@@ -51,9 +56,12 @@ __global__ void sv_oneshot_init_kernel(SvRequest *rq, SvScoring *sc_out, const S
     rq->score = (mode == kModeGlobal) ? INT_MIN : 0;
     rq->strips_done = 0;
     rq->status = 0;
-    head_tail[0] = 0;
-    head_tail[1] = (unsigned long long)nstrips;
     *stop = 1;
+  }
+  __syncthreads();
+  if (i == 0) {
+    ctr[1] = 1;  // tail: one task
+    ctr[3] = 1;  // one request admitted
   }
 }
 
@@ -62,6 +70,7 @@ inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 }  // namespace
 
 int sv_strips_for(int64_t m, int64_t n) {
+  if (m == 0 || n == 0) return 1;  // closed form, one task
   const int64_t c = m > n ? m : n;
   return (int)std::max<int64_t>(1, (c + kSvW - 1) / kSvW);
 }
@@ -77,10 +86,11 @@ int sv_align_pair(const uint8_t *q, int64_t m, const uint8_t *t, int64_t n, int 
   const int nstrips = sv_strips_for(m, n);
   const int64_t R = m < n ? m : n;
   const size_t o_sc = 0, o_rq = align256(o_sc + sizeof(SvScoring));
-  const size_t o_ht = align256(o_rq + sizeof(SvRequest)), o_stop = o_ht + 2 * sizeof(unsigned long long);
-  const size_t o_st = align256(o_stop + sizeof(int32_t));
-  const size_t o_tasks = align256(o_st + sizeof(int32_t));
-  const size_t o_edges = align256(o_tasks + sizeof(int2) * (size_t)nstrips);
+  const size_t o_ht = align256(o_rq + sizeof(SvRequest)), o_stop = o_ht + 8 * sizeof(unsigned long long);
+  const size_t o_cseq = align256(o_stop + sizeof(int32_t));
+  const size_t o_cont = align256(o_cseq + sizeof(unsigned long long) * kSvMaxStrips);
+  const size_t o_tasks = align256(o_cont + sizeof(int2) * kSvMaxStrips);
+  const size_t o_edges = align256(o_tasks + sizeof(int2));
   const size_t bytes = o_edges + sizeof(int2) * (size_t)(nstrips - 1) * (size_t)(R + 1) + 256;
   char *base = nullptr;
   if (pool_malloc((void **)&base, bytes, s) != cudaSuccess) return GA_ERR_OOM;
@@ -90,8 +100,10 @@ int sv_align_pair(const uint8_t *q, int64_t m, const uint8_t *t, int64_t n, int 
   int32_t *stop = (int32_t *)(base + o_stop);
   int2 *tasks = (int2 *)(base + o_tasks);
   int2 *edges = (int2 *)(base + o_edges);
+  unsigned long long *cseq = (unsigned long long *)(base + o_cseq);
+  int2 *cont = (int2 *)(base + o_cont);
 
-  const size_t smem = (size_t)kSvWarps * (size_t)(sc.A + 1) * kSvW;
+  const size_t smem = (size_t)kSvWarps * (size_t)sc.A * kSvW;
   int occ = 0, dev = 0, nsm = 0;
   if (sv_prepare_launch(smem, &occ) != cudaSuccess || cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
@@ -105,21 +117,28 @@ int sv_align_pair(const uint8_t *q, int64_t m, const uint8_t *t, int64_t n, int 
     cudaEventRecord(e0, s);
   }
   sv_oneshot_init_kernel<<<1, 128, 0, s>>>(rq, dsc, sc, q, t, edges, score, (int)m, (int)n, mode, nstrips,
-                                           tasks, ht, stop);
+                                           tasks, ht, cseq, stop);
   SvParams p{};
   p.req = rq;
   p.scorings = dsc;
   p.tasks = tasks;
-  p.task_cap = nstrips;
+  p.task_cap = 1;
   p.head = ht;
   p.tail = ht + 1;
   p.comp = nullptr;
   p.comp_cap = 1;
   p.comp_count = nullptr;
   p.stop = stop;
+  p.cont = cont;
+  p.cont_seq = cseq;
+  p.cont_cap = kSvMaxStrips;
+  p.cont_head = ht + 5;
+  p.cont_tail = ht + 6;
+  p.admitted = ht + 3;
+  p.completed = ht + 4;
   p.idle_ns = 0;
   p.wait_ns = 10ll * 1000 * 1000 * 1000;
-  p.prof_bytes = (sc.A + 1) * kSvW;
+  p.prof_bytes = sc.A * kSvW;
   const int grid = std::max(1, std::min((nstrips + kSvWarps - 1) / kSvWarps, nsm * std::max(occ, 1)));
   ks_kernel<<<grid, 32 * kSvWarps, smem, s>>>(p);
   int rc = cudaGetLastError() == cudaSuccess ? GA_OK : GA_ERR_CUDA;
@@ -245,7 +264,9 @@ struct ga_server {
   ga::SvRequest *req = nullptr;
   ga::SvScoring *scorings = nullptr;
   int2 *tasks = nullptr;
-  unsigned long long *ctr = nullptr;  // head, tail, comp_count
+  unsigned long long *ctr = nullptr;  // head, tail, comp_count, admitted, completed, cont head, cont tail
+  int2 *cont = nullptr;               // continuation ring (req_cap entries)
+  unsigned long long *cont_seq = nullptr;
   // host (pinned, mapped where the kernel reads or writes it)
   ga::SvCompletion *comp_h = nullptr;
   int32_t *stop_h = nullptr;
@@ -291,6 +312,7 @@ namespace {
 bool sched_tick(ga_server *S) {
   bool busy = false;
   const int64_t now = S->now_ns();
+  int64_t t_a = 0, t_b = 0, t_c = 0;  // phase times of this tick
   // ---- admission decisions (arrival order), under the lock -------------
   struct Adm {
     Pending pd;
@@ -310,7 +332,7 @@ bool sched_tick(ga_server *S) {
       const int nstrips = sv_strips_for(m, n);
       const int slot = (int)((S->req_seq + (int64_t)admit.size()) % S->req_cap);
       if (S->slots[slot].used) break;  // slot still busy: keep arrival order
-      if (S->tasks_inflight + ntasks + nstrips > S->task_cap) break;
+      if (S->tasks_inflight + ntasks + 1 > S->task_cap) break;
       const int64_t seq_bytes = seq_bytes_for(m, n);
       if (stage_bytes + seq_bytes > S->stage_seq_cap) break;
       const int64_t edge_bytes = edge_bytes_for(m, n);
@@ -334,7 +356,7 @@ bool sched_tick(ga_server *S) {
       f.edge_off = eo;
       f.edge_bytes = edge_bytes;
       f.nstrips = nstrips;
-      ntasks += nstrips;
+      ntasks += 1;  // strip 0; the kernel queues the others
       stage_bytes += seq_bytes;
       admit.push_back(Adm{pd, slot, m, n});
       ++S->pending_head;
@@ -384,11 +406,12 @@ bool sched_tick(ga_server *S) {
       r.scoring = a.pd.scoring;
       r.nstrips = f.nstrips;
       r.score = a.pd.mode == kModeGlobal ? INT_MIN : 0;
-      for (int j = 0; j < f.nstrips; ++j) S->stage_tasks[k + j] = make_int2(a.slot, j);
-      k += f.nstrips;
+      S->stage_tasks[k] = make_int2(a.slot, 0);
+      k += 1;
       off += f.seq_bytes;
     }
     flush_run();
+    t_a = S->now_ns();
     const int64_t first_slot = admit[0].slot;
     const int64_t n1 = std::min<int64_t>((int64_t)admit.size(), S->req_cap - first_slot);
     cudaMemcpyAsync(S->req + first_slot, S->stage_req, sizeof(SvRequest) * (size_t)n1,
@@ -404,12 +427,18 @@ bool sched_tick(ga_server *S) {
       cudaMemcpyAsync(S->tasks, S->stage_tasks + k1, sizeof(int2) * (size_t)(ntasks - k1),
                       cudaMemcpyHostToDevice, S->feed);
     const unsigned long long new_tail = S->tail + (unsigned long long)ntasks;
-    *S->stage_tail = new_tail;
+    S->stage_tail[0] = new_tail;
+    S->stage_tail[1] = (unsigned long long)(S->req_seq + (int64_t)admit.size());  // admitted
     cudaMemcpyAsync(S->ctr + 1, S->stage_tail, sizeof(unsigned long long), cudaMemcpyHostToDevice,
+                    S->feed);
+    cudaMemcpyAsync(S->ctr + 3, S->stage_tail + 1, sizeof(unsigned long long), cudaMemcpyHostToDevice,
                     S->feed);
     const bool ok = cudaStreamSynchronize(S->feed) == cudaSuccess;
     const int64_t t_admit = S->now_ns();
+    t_b = t_admit;
     std::lock_guard<std::mutex> lk(S->mu);
+    S->st.admit_host_ns += t_a - now;
+    S->st.copy_ns += t_b - t_a;
     if (!ok) S->sched_error = GA_ERR_CUDA;
     S->tail = new_tail;
     for (const Adm &a : admit) S->slots[a.slot].admit_ns = t_admit;
@@ -439,7 +468,14 @@ bool sched_tick(ga_server *S) {
     p.stop = stop_d;
     p.idle_ns = S->idle_ns;
     p.wait_ns = 10ll * 1000 * 1000 * 1000;
-    p.prof_bytes = (S->max_A + 1) * kSvW;
+    p.prof_bytes = S->max_A * kSvW;
+    p.cont = S->cont;
+    p.cont_seq = S->cont_seq;
+    p.cont_cap = S->req_cap;
+    p.cont_head = S->ctr + 5;
+    p.cont_tail = S->ctr + 6;
+    p.admitted = S->ctr + 3;
+    p.completed = S->ctr + 4;
     ks_kernel<<<S->grid, 32 * kSvWarps, S->smem, S->kstream>>>(p);
     if (cudaGetLastError() != cudaSuccess) S->sched_error = GA_ERR_CUDA;
     S->kernel_running = true;
@@ -447,6 +483,8 @@ bool sched_tick(ga_server *S) {
     busy = true;
   }
   // ---- completions -----------------------------------------------------
+  t_c = S->now_ns();
+  int64_t ncomp = 0;
   for (;;) {
     SvCompletion *c = S->comp_h + (S->comp_next % S->req_cap);
     const int64_t seq = *(volatile int64_t *)&c->seq;
@@ -468,7 +506,7 @@ bool sched_tick(ga_server *S) {
         res.cells = f.cells;
         S->alloc->release(f.seq_off, f.seq_bytes);
         if (f.edge_off >= 0) S->alloc->release(f.edge_off, f.edge_bytes);
-        S->tasks_inflight -= f.nstrips;
+        S->tasks_inflight -= 1;
         f.used = false;
         --S->inflight;
       } else {
@@ -480,7 +518,13 @@ bool sched_tick(ga_server *S) {
       S->st.arena_high_water = S->alloc->high_water();
     }
     ++S->comp_next;
+    ++ncomp;
     busy = true;
+  }
+  if (ncomp) {
+    const int64_t t_d = S->now_ns();
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->st.complete_ns += t_d - t_c;
   }
   ++S->st.scheduler_ticks;
   return busy;
@@ -521,7 +565,9 @@ int ga_server_create(const ga_server_config *cfg, ga_server **out) {
             cudaMalloc((void **)&S->req, sizeof(SvRequest) * (size_t)S->req_cap) == cudaSuccess &&
             cudaMalloc((void **)&S->scorings, sizeof(SvScoring) * GA_SERVE_MAX_SCORINGS) == cudaSuccess &&
             cudaMalloc((void **)&S->tasks, sizeof(int2) * (size_t)S->task_cap) == cudaSuccess &&
-            cudaMalloc((void **)&S->ctr, 4 * sizeof(unsigned long long)) == cudaSuccess &&
+            cudaMalloc((void **)&S->ctr, 8 * sizeof(unsigned long long)) == cudaSuccess &&
+            cudaMalloc((void **)&S->cont, sizeof(int2) * (size_t)S->req_cap) == cudaSuccess &&
+            cudaMalloc((void **)&S->cont_seq, sizeof(unsigned long long) * (size_t)S->req_cap) == cudaSuccess &&
             cudaHostAlloc((void **)&S->comp_h, sizeof(SvCompletion) * (size_t)S->req_cap,
                           cudaHostAllocMapped) == cudaSuccess &&
             cudaHostAlloc((void **)&S->stop_h, 64, cudaHostAllocMapped) == cudaSuccess;
@@ -538,13 +584,14 @@ int ga_server_create(const ga_server_config *cfg, ga_server **out) {
   }
   std::memset(S->comp_h, 0, sizeof(SvCompletion) * (size_t)S->req_cap);
   *S->stop_h = 0;
-  if (cudaMemset(S->ctr, 0, 4 * sizeof(unsigned long long)) != cudaSuccess) {
+  if (cudaMemset(S->ctr, 0, 8 * sizeof(unsigned long long)) != cudaSuccess ||
+      cudaMemset(S->cont_seq, 0, sizeof(unsigned long long) * (size_t)S->req_cap) != cudaSuccess) {
     ga_server_destroy(S.release());
     return GA_ERR_CUDA;
   }
   S->slots.resize((size_t)S->req_cap);
   S->alloc.reset(new ArenaAlloc(S->arena_bytes));
-  S->smem = (size_t)kSvWarps * (size_t)(S->max_A + 1) * kSvW;
+  S->smem = (size_t)kSvWarps * (size_t)S->max_A * kSvW;
   int occ = 0, nsm = 0;
   if (sv_prepare_launch(S->smem, &occ) != cudaSuccess ||
       cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, S->device) != cudaSuccess) {
@@ -578,7 +625,7 @@ int ga_server_add_scoring(ga_server *S, const ga_scoring *sc, int32_t *scoring_i
   S->sc_host.push_back(h);
   if (h.A > S->max_A) {
     S->max_A = h.A;
-    S->smem = (size_t)kSvWarps * (size_t)(S->max_A + 1) * kSvW;
+    S->smem = (size_t)kSvWarps * (size_t)S->max_A * kSvW;
     int occ = 0, nsm = 0;
     if (sv_prepare_launch(S->smem, &occ) != cudaSuccess ||
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, S->device) != cudaSuccess)
@@ -685,6 +732,8 @@ int ga_server_destroy(ga_server *S) {
   cudaFree(S->scorings);
   cudaFree(S->tasks);
   cudaFree(S->ctr);
+  cudaFree(S->cont);
+  cudaFree(S->cont_seq);
   cudaFreeHost(S->comp_h);
   cudaFreeHost(S->stop_h);
   cudaFreeHost(S->stage_seq);

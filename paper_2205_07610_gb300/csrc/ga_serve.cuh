@@ -11,15 +11,19 @@
 // is about to read are published.  Rows are the shorter sequence, columns
 // the longer one.
 //
-// Tasks come from a device-resident ring: a warp claims the next task with
-// a compare-and-swap of `head` only while head < tail, so a claim is always
-// made by a running warp.  The strips of a pair are queued in order, so
-// the producer of every edge a warp waits on was claimed earlier by a warp
-// that is running: the waits end without any assumption about which blocks
-// are resident.  Every wait is bounded (globaltimer): an edge wait that
-// runs out marks the request GA_ERR_TIMEOUT and continues, an idle warp
-// exits after idle_ns, and a warp exits at once when the queue is empty and
-// `stop` is set.
+// Tasks come from two device-resident rings: strip 0 of each request from
+// the producer's ring (host or init kernel), strip s+1 from a continuation
+// ring that the warp running strip s fills once it has published the first
+// kSvContRows edge rows, so the next strip rarely waits.  A warp claims a
+// task with a compare-and-swap of the ring head only when an entry is
+// there, continuations first, so a claim is always made by a running warp,
+// and the producer of every edge a warp waits on (strip s of the same
+// request) was claimed earlier by a warp that is running: the waits end
+// without any assumption about which blocks are resident.  Every wait is
+// bounded (globaltimer): an edge wait that runs out marks the request
+// GA_ERR_TIMEOUT and continues; a warp without work exits once no request
+// is in flight and `stop` is set or it has idled for idle_ns, and in any
+// case after wait_ns without a claimable task.
 //
 // A request completes when its last strip finishes: that warp writes the
 // score to `out` (if set) and a completion record (id, score, status, seq)
@@ -39,6 +43,7 @@ constexpr int kSvW = 32 * kSvK;  // columns per strip
 constexpr int kSvWarps = 4;      // warps per block
 constexpr int kSvMaxStrips = 128;
 constexpr int kSvMaxLen = kSvMaxStrips * kSvW;  // longer sequence <= 65536
+constexpr int kSvContRows = 96;  // edge rows published before the next strip is queued
 
 struct SvScoring {
   int32_t A, alpha, beta, pad;
@@ -79,9 +84,21 @@ struct SvParams {
   int64_t comp_cap;
   unsigned long long *comp_count;
   const int32_t *stop;
+  // continuation queue: strip s+1 of a request, pushed by the warp running
+  // strip s once that strip has published kSvContRows edge rows (at most one
+  // unclaimed continuation per request, so cont_cap >= requests in flight)
+  int2 *cont;
+  unsigned long long *cont_seq;  // entry i holds a task once cont_seq[i % cap] == i + 1
+  int64_t cont_cap;
+  unsigned long long *cont_head;
+  unsigned long long *cont_tail;
+  // requests admitted (published by the producer of the task queue) and
+  // completed (counted here): warps stay while some request is in flight
+  const unsigned long long *admitted;
+  unsigned long long *completed;
   int64_t idle_ns;
   int64_t wait_ns;
-  int32_t prof_bytes;  // per warp: (max A + 1) * kSvW
+  int32_t prof_bytes;  // per warp: max A * kSvW (rows of real residues only)
 };
 
 __device__ __forceinline__ uint64_t sv_now() {
@@ -102,6 +119,9 @@ __device__ __forceinline__ unsigned long long sv_ld_acquire64(const unsigned lon
 __device__ __forceinline__ void sv_st_release(int32_t *p, int v) {
   asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
+__device__ __forceinline__ void sv_st_release64(unsigned long long *p, unsigned long long v) {
+  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
 __device__ __forceinline__ int sv_ld_sys(const int32_t *p) {
   int v;
   asm volatile("ld.relaxed.sys.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
@@ -119,8 +139,9 @@ struct SvView {
 // (local: best H; semi: max of row R; global: H(R, C) on the lane that owns
 // column C, else INT_MIN).
 template <int MODE>
-__device__ int sv_strip(const SvParams &p, SvRequest *rq, const SvView &v, int s, int t, uint8_t *prof,
-                        uint8_t *colc, int2 *in_ring, int2 *out_ring, uint32_t *row_ring) {
+__device__ int sv_strip(const SvParams &p, SvRequest *rq, int slot, const SvView &v, int s, int t,
+                        uint8_t *prof, uint8_t *colc, int2 *in_ring, int2 *out_ring,
+                        uint32_t *row_ring) {
   using Cell = CellS32;
   using T = int32_t;
   constexpr int K = kSvK, W = kSvW;
@@ -145,7 +166,9 @@ __device__ int sv_strip(const SvParams &p, SvRequest *rq, const SvView &v, int s
     colc[x] = (uint8_t)c;
   }
   __syncwarp();
-  for (int e = t; e < (A + 1) * W; e += 32) {
+  // rows c < A only: pad rows (beyond R) are never computed, pad columns
+  // (beyond C) read 0 from their own entries
+  for (int e = t; e < A * W; e += 32) {
     const int c = e / W, x = e - c * W;
     const int cc = colc[x];
     int val = 0;
@@ -204,17 +227,28 @@ __device__ int sv_strip(const SvParams &p, SvRequest *rq, const SvView &v, int s
     uint32_t c = (uint32_t)A;
     if (r <= R) {
       c = __ldcg(v.rowraw + r - 1);
-      if (c >= (uint32_t)A) {
+      if (c >= (uint32_t)A) {  // reported; any in-range row keeps the profile read in bounds
         atomicCAS(&rq->status, 0, GA_ERR_RESIDUE);
-        c = (uint32_t)A;
+        c = 0;
       }
     }
     row_ring[r & 127] = c;
   };
+  bool queued = false;  // strip s+1 queued
   auto publish = [&](int rows) {  // edge rows 1..rows are in global memory
     __threadfence();
     __syncwarp();
-    if (t == 0) sv_st_release(&rq->progress[s], rows);
+    if (t == 0) {
+      sv_st_release(&rq->progress[s], rows);
+      if (!queued && rows >= ::min(R, kSvContRows)) {
+        const unsigned long long idx = atomicAdd(p.cont_tail, 1ull);
+        const int64_t e = (int64_t)(idx % (unsigned long long)p.cont_cap);
+        p.cont[e] = make_int2(slot, s + 1);
+        __threadfence();
+        sv_st_release64(p.cont_seq + e, idx + 1);
+      }
+    }
+    queued = queued || rows >= ::min(R, kSvContRows);
   };
 
   load_batch(0);
@@ -315,6 +349,20 @@ __global__ void __launch_bounds__(32 * kSvWarps) ks_kernel(const __grid_constant
       uint64_t idle0 = 0;
       unsigned ns = 64;
       for (;;) {
+        // continuations first: they belong to requests already running
+        const unsigned long long ch = *(volatile unsigned long long *)p.cont_head;
+        if (ch < sv_ld_acquire64(p.cont_tail)) {
+          const int64_t e = (int64_t)(ch % (unsigned long long)p.cont_cap);
+          if (sv_ld_acquire64(p.cont_seq + e) == ch + 1) {
+            if (atomicCAS(p.cont_head, ch, ch + 1) == ch) {
+              const int2 tk = __ldcg(p.cont + e);
+              slot = tk.x;
+              strip = tk.y;
+              break;
+            }
+            continue;
+          }
+        }
         const unsigned long long tl = sv_ld_acquire64(p.tail);
         const unsigned long long h = *(volatile unsigned long long *)p.head;
         if (h < tl) {
@@ -326,13 +374,19 @@ __global__ void __launch_bounds__(32 * kSvWarps) ks_kernel(const __grid_constant
           }
           continue;
         }
-        if (sv_ld_sys(p.stop)) {
+        // no task: leave once nothing is in flight and the producer has
+        // stopped (or has been quiet for idle_ns)
+        const bool drained = sv_ld_acquire64(p.admitted) == *(volatile unsigned long long *)p.completed;
+        if (drained && sv_ld_sys(p.stop)) {
           quit = 1;
           break;
         }
         const uint64_t now = sv_now();
         if (!idle0) idle0 = now;
-        else if (now - idle0 > (uint64_t)p.idle_ns) {
+        else if (drained && now - idle0 > (uint64_t)p.idle_ns) {
+          quit = 1;
+          break;
+        } else if (now - idle0 > (uint64_t)p.wait_ns) {  // nothing claimable for wait_ns
           quit = 1;
           break;
         }
@@ -368,13 +422,13 @@ __global__ void __launch_bounds__(32 * kSvWarps) ks_kernel(const __grid_constant
       const int len = v.R + v.C;
       val = (mode == kModeGlobal && len) ? -(v.alpha + v.beta * (len - 1)) : 0;
     } else if (mode == kModeLocal) {
-      val = sv_strip<kModeLocal>(p, rq, v, strip, t, prof, colc_s[warp], in_ring_s[warp],
+      val = sv_strip<kModeLocal>(p, rq, slot, v, strip, t, prof, colc_s[warp], in_ring_s[warp],
                                  out_ring_s[warp], row_ring_s[warp]);
     } else if (mode == kModeGlobal) {
-      val = sv_strip<kModeGlobal>(p, rq, v, strip, t, prof, colc_s[warp], in_ring_s[warp],
+      val = sv_strip<kModeGlobal>(p, rq, slot, v, strip, t, prof, colc_s[warp], in_ring_s[warp],
                                   out_ring_s[warp], row_ring_s[warp]);
     } else {
-      val = sv_strip<kModeSemi>(p, rq, v, strip, t, prof, colc_s[warp], in_ring_s[warp],
+      val = sv_strip<kModeSemi>(p, rq, slot, v, strip, t, prof, colc_s[warp], in_ring_s[warp],
                                 out_ring_s[warp], row_ring_s[warp]);
     }
     if (t == 0) {
@@ -387,6 +441,7 @@ __global__ void __launch_bounds__(32 * kSvWarps) ks_kernel(const __grid_constant
       const int done = atomicAdd(&rq->strips_done, 1) + 1;
       if (done == v.nstrips) {
         __threadfence();
+        atomicAdd(p.completed, 1ull);
         const int score = atomicAdd(&rq->score, 0);
         const int status = atomicAdd(&rq->status, 0);
         int32_t *out = (int32_t *)__ldcg((const unsigned long long *)&rq->out);
