@@ -127,9 +127,14 @@ int ga_align_batch(const uint8_t *q_codes, const int64_t *q_off, const uint8_t *
 
 /*
  * ga_align_batch_host -- ga_align_batch with every array in HOST memory
- * (pinned memory gives the fastest copies).  The call copies the inputs to
- * the device on `stream`, aligns, copies scores back and synchronises
- * before returning; the host buffers may be reused afterwards.
+ * (pinned memory gives the fastest copies).  The pairs are cut into up to 8
+ * chunks of geometrically growing size (one chunk per 2^18 pairs, the
+ * first the smallest); all inputs are copied in, chunk by chunk,
+ * on a stream of the call's own while the chunks are aligned on `stream`,
+ * each as soon as its inputs have arrived, and its scores copied back
+ * behind it.  The call synchronises before returning; the host buffers may
+ * be reused afterwards.  stats (nullable) sums the chunks' statistics;
+ * kernel_ms is the device time of the whole call.
  */
 int ga_align_batch_host(const uint8_t *q_codes, const int64_t *q_off, const uint8_t *t_codes,
                         const int64_t *t_off, int64_t npairs, const ga_scoring *scoring,

@@ -235,30 +235,46 @@ int setup(Call &c) {
 }
 
 // Validate + pack one sequence set.  Reads back the total residue count.
+// Residue range [off[0], off[nseq]) of a set, when the caller knows it on
+// the host (otherwise it is read back from the device offsets).
+struct KnownRange {
+  bool known = false;
+  int64_t start = 0, total = 0;
+};
+
 int prepare_set(Call &c, const uint8_t *codes, const int64_t *off, int64_t nseq, uint32_t **packed,
-                uint8_t **bad, int32_t *invalid) {
+                uint8_t **bad, int32_t *invalid, KnownRange kr = KnownRange()) {
   *bad = c.al.get<uint8_t>((size_t)nseq + 1);
   *packed = nullptr;
   if (c.al.failed) return GA_ERR_OOM;
   if (nseq == 0) return GA_OK;
-  int64_t *h = (int64_t *)pinned_scratch();
-  if (cudaMemcpyAsync(h, off + nseq, sizeof(int64_t), cudaMemcpyDeviceToHost, c.s) != cudaSuccess ||
-      cudaStreamSynchronize(c.s) != cudaSuccess)
-    return GA_ERR_CUDA;
-  const int64_t total = std::max<int64_t>(h[0], 0);
+  // the set's residues are codes[off[0] .. off[nseq]) (off[0] > 0 when the
+  // set is a chunk of a larger buffer); packed words keep absolute positions
+  int64_t h0 = kr.start, h1 = kr.total;
+  if (!kr.known) {
+    int64_t *h = (int64_t *)pinned_scratch();
+    if (cudaMemcpyAsync(h, off, sizeof(int64_t), cudaMemcpyDeviceToHost, c.s) != cudaSuccess ||
+        cudaMemcpyAsync(h + 1, off + nseq, sizeof(int64_t), cudaMemcpyDeviceToHost, c.s) != cudaSuccess ||
+        cudaStreamSynchronize(c.s) != cudaSuccess)
+      return GA_ERR_CUDA;
+    h0 = h[0];
+    h1 = h[1];
+  }
+  const int64_t total = std::max<int64_t>(h1, 0);
+  const int64_t start = std::min(std::max<int64_t>(h0, 0), total);
   if (c.dna) {
     *packed = c.al.get<uint32_t>((size_t)(total / 16 + 2));
     if (c.al.failed) return GA_ERR_OOM;
   }
-  const int64_t nwords = (total + 15) / 16;
+  const int64_t nwords = (total + 15) / 16 - start / 16;
   const int64_t pblocks = std::min<int64_t>((nwords + 255) / 256, (int64_t)c.nsm * 16);
   if (nwords > 0) {
-    flat_pack_kernel<<<(unsigned)std::max<int64_t>(pblocks, 1), 256, 0, c.s>>>(codes, total, c.sc.A,
-                                                                               *packed, invalid);
+    flat_pack_kernel<<<(unsigned)std::max<int64_t>(pblocks, 1), 256, 0, c.s>>>(codes, start, total,
+                                                                               c.sc.A, *packed, invalid);
     ++c.launches;
   }
-  validate_kernel<<<(unsigned)((nseq + 255) / 256), 256, 0, c.s>>>(codes, off, nseq, total, c.sc.A,
-                                                                   invalid, *bad);
+  validate_kernel<<<(unsigned)((nseq + 255) / 256), 256, 0, c.s>>>(codes, off, nseq, start, total,
+                                                                   c.sc.A, invalid, *bad);
   ++c.launches;
   if (cudaGetLastError() != cudaSuccess) return GA_ERR_CUDA;
   return GA_OK;
@@ -502,7 +518,8 @@ struct Events {
 
 int batch_impl(const uint8_t *q_codes, const int64_t *q_off, const uint8_t *t_codes,
                const int64_t *t_off, int64_t npairs, const ga_scoring *scoring, int32_t mode,
-               int32_t *scores, void *stream, ga_stats *stats, int force_long) {
+               int32_t *scores, void *stream, ga_stats *stats, int force_long,
+               KnownRange qr = KnownRange(), KnownRange tr = KnownRange()) {
   if (npairs < 0 || mode < 0 || mode > 2) return GA_ERR_ARG;
   if (npairs > 0 && (!q_codes || !q_off || !t_codes || !t_off || !scores)) return GA_ERR_ARG;
   if (npairs >= (1ll << 31) - 64) return GA_ERR_ARG;
@@ -514,8 +531,8 @@ int batch_impl(const uint8_t *q_codes, const int64_t *q_off, const uint8_t *t_co
   Events ev(stats != nullptr, c.s);
   if ((rc = setup(c))) return rc;
   SetView Q{q_codes, q_off, nullptr, nullptr}, T{t_codes, t_off, nullptr, nullptr};
-  if ((rc = prepare_set(c, q_codes, q_off, npairs, &Q.packed, &Q.bad, &c.small->invalid_q))) return rc;
-  if ((rc = prepare_set(c, t_codes, t_off, npairs, &T.packed, &T.bad, &c.small->invalid_t))) return rc;
+  if ((rc = prepare_set(c, q_codes, q_off, npairs, &Q.packed, &Q.bad, &c.small->invalid_q, qr))) return rc;
+  if ((rc = prepare_set(c, t_codes, t_off, npairs, &T.packed, &T.bad, &c.small->invalid_t, tr))) return rc;
   uint32_t *keys = c.al.get<uint32_t>((size_t)npairs);
   int4 *info = c.al.get<int4>((size_t)npairs);
   int32_t *sorted = c.al.get<int32_t>((size_t)npairs);
@@ -741,36 +758,119 @@ int ga_align_batch_host(const uint8_t *q_codes, const int64_t *q_off, const uint
                         int32_t mode, int32_t *scores, void *stream, ga_stats *stats) {
   if (npairs < 0) return GA_ERR_ARG;
   if (npairs > 0 && (!q_codes || !q_off || !t_codes || !t_off || !scores)) return GA_ERR_ARG;
+  if (npairs == 0) return batch_impl(nullptr, nullptr, nullptr, nullptr, 0, scoring, mode, nullptr, stream,
+                                     stats, 0);
   cudaStream_t s = (cudaStream_t)stream;
-  const int64_t qn = npairs ? q_off[npairs] : 0, tn = npairs ? t_off[npairs] : 0;
-  if (qn < 0 || tn < 0) return GA_ERR_ARG;
+  const int64_t qn = q_off[npairs], tn = t_off[npairs];
+  if (qn < 0 || tn < 0 || q_off[0] < 0 || t_off[0] < 0 || q_off[0] > qn || t_off[0] > tn) return GA_ERR_ARG;
+  // Chunks of pairs: the copies of every chunk go in order on a copy stream,
+  // the alignment of chunk k on `stream` waits only for chunk k's copy, and
+  // its scores go back as soon as it is done, so copies and alignment overlap.
+  const int64_t kChunkPairs = 1 << 18;
+  const int nchunk = (int)std::min<int64_t>(8, std::max<int64_t>(1, (npairs + kChunkPairs - 1) / kChunkPairs));
+  // geometric chunk sizes (1, 2, 4, ... parts): the first alignment starts
+  // after a small copy, and every later copy (host->device bandwidth well
+  // above the alignment's input rate) is done before its chunk is reached
+  std::vector<int64_t> cut((size_t)nchunk + 1);
+  const int64_t parts = ((int64_t)1 << nchunk) - 1;
+  for (int k = 0; k <= nchunk; ++k) cut[k] = (int64_t)((double)npairs * (double)(((int64_t)1 << k) - 1) / (double)parts);
+  cut[nchunk] = npairs;
   uint8_t *dq = nullptr, *dt = nullptr;
   int64_t *dqo = nullptr, *dto = nullptr;
   int32_t *ds = nullptr;
+  cudaStream_t cs = nullptr;
+  std::vector<cudaEvent_t> ev_in((size_t)nchunk, nullptr), ev_done((size_t)nchunk, nullptr);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
   auto cleanup = [&]() {
     cudaFreeAsync(dq, s); cudaFreeAsync(dt, s); cudaFreeAsync(dqo, s);
     cudaFreeAsync(dto, s); cudaFreeAsync(ds, s);
   };
-  if (pool_malloc((void **)&dq, (size_t)qn + 16, s) != cudaSuccess ||
-      pool_malloc((void **)&dt, (size_t)tn + 16, s) != cudaSuccess ||
-      pool_malloc((void **)&dqo, sizeof(int64_t) * (size_t)(npairs + 1), s) != cudaSuccess ||
-      pool_malloc((void **)&dto, sizeof(int64_t) * (size_t)(npairs + 1), s) != cudaSuccess ||
-      pool_malloc((void **)&ds, sizeof(int32_t) * (size_t)(npairs + 1), s) != cudaSuccess) {
-    cleanup();
-    return GA_ERR_OOM;
+  bool ok = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) == cudaSuccess;
+  for (int k = 0; ok && k < nchunk; ++k)
+    ok = cudaEventCreateWithFlags(&ev_in[k], cudaEventDisableTiming) == cudaSuccess &&
+         cudaEventCreateWithFlags(&ev_done[k], cudaEventDisableTiming) == cudaSuccess;
+  int rc = ok ? GA_OK : GA_ERR_CUDA;
+  if (!rc && (pool_malloc((void **)&dq, (size_t)qn + 16, s) != cudaSuccess ||
+              pool_malloc((void **)&dt, (size_t)tn + 16, s) != cudaSuccess ||
+              pool_malloc((void **)&dqo, sizeof(int64_t) * (size_t)(npairs + 1), s) != cudaSuccess ||
+              pool_malloc((void **)&dto, sizeof(int64_t) * (size_t)(npairs + 1), s) != cudaSuccess ||
+              pool_malloc((void **)&ds, sizeof(int32_t) * (size_t)(npairs + 1), s) != cudaSuccess))
+    rc = GA_ERR_OOM;
+  cudaEvent_t ready = nullptr;  // the allocations above are ordered on `s`
+  if (!rc && (cudaEventCreateWithFlags(&ready, cudaEventDisableTiming) != cudaSuccess ||
+              cudaEventRecord(ready, s) != cudaSuccess || cudaStreamWaitEvent(cs, ready, 0) != cudaSuccess))
+    rc = GA_ERR_CUDA;
+  if (!rc && stats) {
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventRecord(e0, s);
   }
-  int rc = GA_OK;
-  if (cudaMemcpyAsync(dq, q_codes, (size_t)qn, cudaMemcpyHostToDevice, s) != cudaSuccess ||
-      cudaMemcpyAsync(dt, t_codes, (size_t)tn, cudaMemcpyHostToDevice, s) != cudaSuccess ||
-      cudaMemcpyAsync(dqo, q_off, sizeof(int64_t) * (size_t)(npairs + 1), cudaMemcpyHostToDevice, s) != cudaSuccess ||
-      cudaMemcpyAsync(dto, t_off, sizeof(int64_t) * (size_t)(npairs + 1), cudaMemcpyHostToDevice, s) != cudaSuccess)
-    rc = GA_ERR_CUDA;
-  if (!rc) rc = batch_impl(dq, dqo, dt, dto, npairs, scoring, mode, ds, stream, stats, 0);
-  if (!rc && npairs > 0 &&
-      cudaMemcpyAsync(scores, ds, sizeof(int32_t) * (size_t)npairs, cudaMemcpyDeviceToHost, s) != cudaSuccess)
-    rc = GA_ERR_CUDA;
+  // all copies in, chunk by chunk
+  for (int k = 0; !rc && k < nchunk; ++k) {
+    const int64_t a = cut[k], b = cut[k + 1];
+    const int64_t qa = q_off[a], qb = q_off[b], ta = t_off[a], tb = t_off[b];
+    if (qb < qa || tb < ta) {
+      rc = GA_ERR_ARG;
+      break;
+    }
+    if (cudaMemcpyAsync(dqo + a, q_off + a, sizeof(int64_t) * (size_t)(b - a + 1), cudaMemcpyHostToDevice, cs) != cudaSuccess ||
+        cudaMemcpyAsync(dto + a, t_off + a, sizeof(int64_t) * (size_t)(b - a + 1), cudaMemcpyHostToDevice, cs) != cudaSuccess ||
+        (qb > qa && cudaMemcpyAsync(dq + qa, q_codes + qa, (size_t)(qb - qa), cudaMemcpyHostToDevice, cs) != cudaSuccess) ||
+        (tb > ta && cudaMemcpyAsync(dt + ta, t_codes + ta, (size_t)(tb - ta), cudaMemcpyHostToDevice, cs) != cudaSuccess) ||
+        cudaEventRecord(ev_in[k], cs) != cudaSuccess)
+      rc = GA_ERR_CUDA;
+  }
+  // align chunk by chunk; scores of a chunk go back behind its alignment
+  ga_stats tot{};
+  for (int k = 0; !rc && k < nchunk; ++k) {
+    const int64_t a = cut[k], b = cut[k + 1];
+    if (cudaStreamWaitEvent(s, ev_in[k], 0) != cudaSuccess) {
+      rc = GA_ERR_CUDA;
+      break;
+    }
+    ga_stats st{};
+    KnownRange qr, tr;
+    qr.known = tr.known = true;
+    qr.start = q_off[a];
+    qr.total = q_off[b];
+    tr.start = t_off[a];
+    tr.total = t_off[b];
+    rc = batch_impl(dq, dqo + a, dt, dto + a, b - a, scoring, mode, ds + a, stream, stats ? &st : nullptr, 0,
+                    qr, tr);
+    if (rc) break;
+    if (stats) {
+      tot.cells += st.cells; tot.pairs += st.pairs; tot.pairs_int16 += st.pairs_int16;
+      tot.pairs_int32 += st.pairs_int32; tot.pairs_int32_rerun += st.pairs_int32_rerun;
+      tot.dp_ms += st.dp_ms; tot.dp_launches += st.dp_launches; tot.launches += st.launches;
+      if (!tot.status) tot.status = st.status;
+    }
+    if (cudaEventRecord(ev_done[k], s) != cudaSuccess || cudaStreamWaitEvent(cs, ev_done[k], 0) != cudaSuccess ||
+        cudaMemcpyAsync(scores + a, ds + a, sizeof(int32_t) * (size_t)(b - a), cudaMemcpyDeviceToHost, cs) != cudaSuccess)
+      rc = GA_ERR_CUDA;
+  }
+  // the frees are ordered after the last score copy
+  cudaEvent_t copied = nullptr;
+  if (cudaEventCreateWithFlags(&copied, cudaEventDisableTiming) == cudaSuccess) {
+    cudaEventRecord(copied, cs);
+    cudaStreamWaitEvent(s, copied, 0);
+  }
+  if (e1) cudaEventRecord(e1, s);
   cleanup();
   if (cudaStreamSynchronize(s) != cudaSuccess && !rc) rc = GA_ERR_CUDA;
+  if (cs && cudaStreamSynchronize(cs) != cudaSuccess && !rc) rc = GA_ERR_CUDA;
+  if (!rc && stats) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    tot.kernel_ms = ms;
+    *stats = tot;
+  }
+  for (cudaEvent_t e : ev_in) if (e) cudaEventDestroy(e);
+  for (cudaEvent_t e : ev_done) if (e) cudaEventDestroy(e);
+  if (ready) cudaEventDestroy(ready);
+  if (copied) cudaEventDestroy(copied);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (cs) cudaStreamDestroy(cs);
   return rc;
 }
 

@@ -62,13 +62,17 @@ __device__ __forceinline__ uint32_t pack4(uint32_t x) {
 // Flat 2-bit packing of the whole code buffer (residue x -> word x/16),
 // one thread per word with a 16-byte load; any code >= A anywhere raises
 // *invalid (per-sequence validation then runs its slow path).
-__global__ void flat_pack_kernel(const uint8_t *codes, int64_t total, int A, uint32_t *packed,
-                                 int32_t *invalid) {
+__global__ void flat_pack_kernel(const uint8_t *codes, int64_t start, int64_t total, int A,
+                                 uint32_t *packed, int32_t *invalid) {
+  // words start/16 .. (total+15)/16 - 1: the residues [start, total) and the
+  // bytes before `start` in its word (which exist: they are codes of the
+  // same buffer)
   const int64_t nwords = (total + 15) / 16;
+  const int64_t w_first = start / 16;
   const bool aligned16 = (reinterpret_cast<uintptr_t>(codes) & 15u) == 0;
   const uint32_t A4 = (uint32_t)A * 0x01010101u;
   bool bad = false;
-  for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < nwords;
+  for (int64_t w = w_first + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < nwords;
        w += (int64_t)gridDim.x * blockDim.x) {
     const int64_t s0 = w * 16;
     uint32_t x[4];
@@ -97,15 +101,16 @@ __global__ void flat_pack_kernel(const uint8_t *codes, int64_t total, int A, uin
 }
 
 // Thread per sequence: 0 ok, 1 residue code >= A, 2 offsets decreasing or
-// outside [0, total].  Residues are scanned only when the packing pass saw
+// outside [start, total] (start = off[0], total = off[nseq]).  Residues are scanned only when the packing pass saw
 // an invalid code somewhere.
 __global__ void validate_kernel(const uint8_t *codes, const int64_t *off, int64_t nseq,
-                                int64_t total, int A, const int32_t *invalid, uint8_t *bad) {
+                                int64_t start, int64_t total, int A, const int32_t *invalid,
+                                uint8_t *bad) {
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= nseq) return;
   const int64_t s = off[k], e = off[k + 1];
   uint8_t b = 0;
-  if (s < 0 || e < s || e > total) {
+  if (s < start || e < s || e > total) {
     b = 2;
   } else if (*invalid) {
     for (int64_t x = s; x < e; ++x)

@@ -230,6 +230,32 @@ def test_host_entry_point_matches_device():
         assert_same(host, gpu_batch(b, mode), f"host {mode}")
 
 
+def test_host_entry_point_in_chunks():
+    # more pairs than one copy chunk (2^18): chunks start at arbitrary residue
+    # offsets (not multiples of 16), each is packed from its own first residue
+    rng = np.random.default_rng(5)
+    n = 700_000
+    qc, qo = synth.random_sequences(rng, rng.integers(1, 40, size=n))
+    tc, to = synth.random_sequences(rng, rng.integers(1, 40, size=n))
+    b = synth.Batch(qc, qo, tc, to, synth.dna_matrix(2, -3), 5, 2, "chunks")
+    for mode in MODES:
+        host, st = ga.align_batch_host(qc, qo, tc, to, b.matrix, 5, 2, mode, stats=True)
+        assert_same(host, gpu_batch(b, mode), f"host chunks {mode}")
+        assert st["pairs"] == n and st["status"] == 0
+    sub = rng.choice(n, size=300, replace=False)
+    want, _ = oracle.batch(*_subset(b, sub), b.matrix, 5, 2, "global", nthreads=NTHREADS)
+    host = ga.align_batch_host(qc, qo, tc, to, b.matrix, 5, 2, "global")
+    assert_same(host[sub], want, "host chunks vs oracle")
+
+
+def _subset(b, idx):
+    qs = [b.q_codes[b.q_off[i]:b.q_off[i + 1]] for i in idx]
+    ts = [b.t_codes[b.t_off[i]:b.t_off[i + 1]] for i in idx]
+    qc, qo = synth.pack_csr(qs)
+    tc, to = synth.pack_csr(ts)
+    return qc, qo, tc, to
+
+
 @pytest.mark.parametrize("mode", MODES)
 def test_cross_small(mode):
     cr = synth.protein_database(nq=6, qmin=20, qmax=300, nt=80, median=120, seed=31)
