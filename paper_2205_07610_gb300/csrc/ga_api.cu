@@ -10,6 +10,7 @@
 #include "ga_band.cuh"
 #include "ga_banded.cuh"
 #include "ga_pool.h"
+#include "ga_prot.cuh"
 #include "ga_serve_host.h"
 #include "ga_launch.h"
 #include "ga_prep.cuh"
@@ -740,6 +741,168 @@ int features_impl(const uint8_t *q_codes, const int64_t *q_off, const uint8_t *t
   return finish(c, stats, ev.e0, ev.e1, npairs);
 }
 
+// Database search of protein (alphabets of > 4 symbols), local mode, on the
+// packed query-profile kernel: targets sorted longest first, queries binned
+// by length (columns per lane K = 8, 16, 24 or 32; longer queries run in
+// stages of 512 columns), flagged pairs recomputed exactly in int32.
+template <int K>
+int launch_kp(Call &c, KPParams &kp, int64_t max_grid) {
+  const size_t smem = (size_t)kKpWarps * (size_t)(c.sc.A + 1) * (size_t)(kKpG * K);
+  if (cudaFuncSetAttribute(kp_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    return GA_ERR_CUDA;
+  int occ = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kp_kernel<K>, 32 * kKpWarps, smem) != cudaSuccess)
+    return GA_ERR_CUDA;
+  kp.prof_bytes = (c.sc.A + 1) * kKpG * K;
+  const int64_t ntasks = (int64_t)kp.nqb * ((kp.ntv + 3) / 4);
+  const int64_t want = (ntasks + kKpWarps - 1) / kKpWarps;
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>({want, (int64_t)c.nsm * std::max(occ, 1), max_grid}));
+  c.dp_begin();
+  kp_kernel<K><<<grid, 32 * kKpWarps, smem, c.s>>>(kp);
+  c.dp_end();
+  return cudaGetLastError() == cudaSuccess ? GA_OK : GA_ERR_CUDA;
+}
+
+int cross_protein_local(Call &c, const uint8_t *q_codes, const int64_t *q_off, int64_t nq,
+                        const uint8_t *t_codes, const int64_t *t_off, int64_t nt, int32_t *scores,
+                        ga_stats *stats, cudaEvent_t e0, cudaEvent_t e1) {
+  int rc;
+  SetView Q{q_codes, q_off, nullptr, nullptr}, T{t_codes, t_off, nullptr, nullptr};
+  if ((rc = prepare_set(c, q_codes, q_off, nq, &Q.packed, &Q.bad, &c.small->invalid_q))) return rc;
+  if ((rc = prepare_set(c, t_codes, t_off, nt, &T.packed, &T.bad, &c.small->invalid_t))) return rc;
+  if (nt >= (1ll << 31) - 64 || nq * nt >= (1ll << 31) - 64) return GA_ERR_ARG;
+  uint32_t *keys = c.al.get<uint32_t>((size_t)nt);
+  int32_t *sorted = c.al.get<int32_t>((size_t)nt);
+  const int32_t rerun_cap = (int32_t)std::min<int64_t>(std::max<int64_t>(nq * nt, 1), 1 << 22);
+  int32_t *rerun = c.al.get<int32_t>((size_t)rerun_cap);
+  if (c.al.failed) return GA_ERR_OOM;
+  // targets: longest first, invalid ones left out
+  if (cudaMemsetAsync(c.hist, 0, sizeof(int32_t) * kNumKeys, c.s) != cudaSuccess) return GA_ERR_CUDA;
+  const unsigned nbt = (unsigned)((nt + 255) / 256);
+  kp_target_keys_kernel<<<nbt, 256, 0, c.s>>>(t_off, nt, T.bad, keys, &c.small->max_rows);
+  hist_kernel<<<nbt, 256, 0, c.s>>>(keys, nt, c.hist);
+  scan_partials_kernel<<<kScanTiles, kScanTile, 0, c.s>>>(c.hist, c.small->scan_partials);
+  scan_apply_kernel<<<kScanTiles, kScanTile, 0, c.s>>>(c.hist, c.small->scan_partials, c.cursor, c.small->ranges);
+  scatter_kernel<<<nbt, 256, 0, c.s>>>(keys, nt, c.cursor, sorted);
+  c.launches += 5;
+  if (cudaGetLastError() != cudaSuccess) return GA_ERR_CUDA;
+  // host view: query offsets and validity, target count and longest target
+  std::vector<int64_t> hqo((size_t)nq + 1);
+  std::vector<uint8_t> hqb((size_t)nq);
+  Small *hs = (Small *)pinned_scratch();
+  static_assert(sizeof(Small) <= 4096, "pinned scratch holds the call's scalars");
+  if (cudaMemcpyAsync(hqo.data(), q_off, sizeof(int64_t) * (size_t)(nq + 1), cudaMemcpyDeviceToHost, c.s) != cudaSuccess ||
+      cudaMemcpyAsync(hqb.data(), Q.bad, (size_t)nq, cudaMemcpyDeviceToHost, c.s) != cudaSuccess ||
+      cudaMemcpyAsync(hs, c.small, sizeof(Small), cudaMemcpyDeviceToHost, c.s) != cudaSuccess ||
+      cudaStreamSynchronize(c.s) != cudaSuccess)
+    return GA_ERR_CUDA;
+  const int32_t ntv = hs->ranges[1] - hs->ranges[0];
+  const int32_t max_len = hs->max_rows;
+  bool any_bad = ntv < nt;
+  for (int64_t k = 0; k < nq; ++k) any_bad |= hqb[k] != 0;
+  if (any_bad) {
+    kp_invalid_kernel<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>((nq * nt + 255) / 256, (int64_t)c.nsm * 32)),
+                        256, 0, c.s>>>(Q.bad, nq, T.bad, nt, scores, &c.small->status);
+    ++c.launches;
+  }
+  // query bins
+  std::vector<int32_t> bins[4];
+  int64_t cells = 0, tcells = 0;
+  for (int64_t k = 0; k < nq; ++k) {
+    if (hqb[k]) continue;
+    const int64_t m = hqo[k + 1] - hqo[k];
+    bins[m <= 128 ? 0 : m <= 256 ? 1 : m <= 384 ? 2 : 3].push_back((int32_t)k);
+    cells += m;
+  }
+  {
+    std::vector<int64_t> hto((size_t)nt + 1);
+    std::vector<uint8_t> htb((size_t)nt);
+    if (cudaMemcpy(hto.data(), t_off, sizeof(int64_t) * (size_t)(nt + 1), cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(htb.data(), T.bad, (size_t)nt, cudaMemcpyDeviceToHost) != cudaSuccess)
+      return GA_ERR_CUDA;
+    for (int64_t l = 0; l < nt; ++l)
+      if (!htb[l]) tcells += hto[l + 1] - hto[l];
+  }
+  cells *= tcells;
+  int32_t *dq = c.al.get<int32_t>((size_t)std::max<int64_t>(nq, 1));
+  if (c.al.failed) return GA_ERR_OOM;
+  std::vector<int32_t> flat;
+  for (int b = 0; b < 4; ++b) flat.insert(flat.end(), bins[b].begin(), bins[b].end());
+  if (!flat.empty() &&
+      cudaMemcpyAsync(dq, flat.data(), sizeof(int32_t) * flat.size(), cudaMemcpyHostToDevice, c.s) != cudaSuccess)
+    return GA_ERR_CUDA;
+  // per-group stage edges: every group slot of the largest grid
+  const int64_t max_grid = (int64_t)c.nsm * 4;
+  const int64_t stride = (int64_t)std::max(max_len, 0) + 64;
+  int2 *bnd = c.al.get<int2>((size_t)max_grid * kKpWarps * 2 * (size_t)stride);
+  if (c.al.failed) return GA_ERR_OOM;
+  KPParams kp{};
+  kp.q_codes = q_codes;
+  kp.q_off = q_off;
+  kp.t_codes = t_codes;
+  kp.t_off = t_off;
+  kp.t_sorted = sorted;
+  kp.ntv = ntv;
+  kp.nt = nt;
+  kp.A = c.sc.A;
+  kp.alpha = c.sc.alpha;
+  kp.beta = c.sc.beta;
+  kp.sigma_max_pos = std::max(c.sc.smax, 0);
+  std::memcpy(kp.sigma, c.sc.mat, sizeof(kp.sigma));
+  kp.scores = scores;
+  kp.rerun_list = rerun;
+  kp.rerun_count = &c.small->rerun_range[1];
+  kp.rerun_cap = rerun_cap;
+  kp.bnd = bnd;
+  kp.bnd_stride = stride;
+  size_t off = 0;
+  for (int b = 0; b < 4; ++b) {
+    if (bins[b].empty() || ntv == 0) {
+      off += bins[b].size();
+      continue;
+    }
+    kp.queries = dq + off;
+    kp.nqb = (int32_t)bins[b].size();
+    kp.task_counter = &c.small->counters[b];
+    off += bins[b].size();
+    rc = b == 0 ? launch_kp<8>(c, kp, max_grid) : b == 1 ? launch_kp<16>(c, kp, max_grid)
+       : b == 2 ? launch_kp<24>(c, kp, max_grid) : launch_kp<32>(c, kp, max_grid);
+    if (rc) return rc;
+  }
+  // exact int32 rerun of flagged pairs (rare: a local score near 32767)
+  int32_t *hn = (int32_t *)pinned_scratch();
+  if (cudaMemcpyAsync(hn, &c.small->rerun_range[1], sizeof(int32_t), cudaMemcpyDeviceToHost, c.s) != cudaSuccess ||
+      cudaStreamSynchronize(c.s) != cudaSuccess)
+    return GA_ERR_CUDA;
+  const int32_t nre = hn[0];
+  if (nre > rerun_cap) return GA_ERR_RANGE;
+  if (nre > 0) {
+    int64_t *info = c.al.get<int64_t>((size_t)nre * 4);
+    std::vector<int32_t> ids((size_t)nre);
+    std::vector<int64_t> hinfo((size_t)nre * 4);
+    if (c.al.failed) return GA_ERR_OOM;
+    kp_rerun_info_kernel<<<(unsigned)((nre + 255) / 256), 256, 0, c.s>>>(rerun, nre, nt, q_off, t_off, info);
+    if (cudaMemcpyAsync(ids.data(), rerun, sizeof(int32_t) * (size_t)nre, cudaMemcpyDeviceToHost, c.s) != cudaSuccess ||
+        cudaMemcpyAsync(hinfo.data(), info, sizeof(int64_t) * (size_t)nre * 4, cudaMemcpyDeviceToHost, c.s) != cudaSuccess ||
+        cudaStreamSynchronize(c.s) != cudaSuccess)
+      return GA_ERR_CUDA;
+    for (int32_t i = 0; i < nre; ++i) {
+      const int64_t *f = &hinfo[(size_t)i * 4];
+      rc = sv_align_pair(q_codes + f[0], f[1], t_codes + f[2], f[3], c.sc.A, c.sc.mat, c.sc.alpha, c.sc.beta,
+                         GA_LOCAL, scores + ids[i], c.s, nullptr);
+      if (rc) return rc;
+    }
+    c.pairs32 += nre;
+  }
+  c.pairs16 += (int64_t)flat.size() * ntv - nre;
+  rc = finish(c, stats, e0, e1, nq * nt);
+  if (!rc && stats) {
+    stats->cells = cells;
+    stats->pairs_int32_rerun = nre;
+  }
+  return rc;
+}
+
 }  // namespace
 }  // namespace ga
 
@@ -887,6 +1050,8 @@ int ga_align_cross(const uint8_t *q_codes, const int64_t *q_off, int64_t nq, con
   Events ev(stats != nullptr, c.s);
   if ((rc = setup(c))) return rc;
   if (nq == 0 || nt == 0) return finish(c, stats, ev.e0, ev.e1, 0);
+  if (c.sc.A > 4 && mode == GA_LOCAL)
+    return cross_protein_local(c, q_codes, q_off, nq, t_codes, t_off, nt, scores, stats, ev.e0, ev.e1);
   SetView Q{q_codes, q_off, nullptr, nullptr}, T{t_codes, t_off, nullptr, nullptr};
   if ((rc = prepare_set(c, q_codes, q_off, nq, &Q.packed, &Q.bad, &c.small->invalid_q))) return rc;
   if ((rc = prepare_set(c, t_codes, t_off, nt, &T.packed, &T.bad, &c.small->invalid_t))) return rc;

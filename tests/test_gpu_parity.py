@@ -256,6 +256,56 @@ def _subset(b, idx):
     return qc, qo, tc, to
 
 
+def test_protein_cross_local_bins_and_stages():
+    # queries in every column bin of the packed protein kernel (<= 128, 256,
+    # 384, 512 columns) and longer ones that run in stages of 512 columns;
+    # targets from empty to long, one with an invalid residue
+    rng = np.random.default_rng(12)
+    bg = np.concatenate([synth.PROTEIN_BACKGROUND, np.zeros(4)])
+    qlens = [0, 1, 50, 128, 129, 256, 300, 384, 385, 512, 513, 700, 1100]
+    tlens = list(rng.integers(1, 900, size=150)) + [0, 1, 2, 2000]
+    qs = [rng.choice(24, size=n, p=bg).astype(np.uint8) for n in qlens]
+    ts = [rng.choice(24, size=int(n), p=bg).astype(np.uint8) for n in tlens]
+    ts[5] = qs[11][100:600].copy()  # a strong local hit
+    qc, qo = synth.pack_csr(qs)
+    tc, to = synth.pack_csr(ts)
+    mat = synth.blosum62()
+    d = "cuda"
+    dev = [torch.from_numpy(a).to(d) for a in (qc, qo, tc, to)]
+    got, st = ga.align_cross(*dev, mat, 11, 1, "local", stats=True)
+    want, _ = oracle.cross(qc, qo, tc, to, mat, 11, 1, "local", nthreads=NTHREADS)
+    assert_same(got.cpu().numpy().ravel(), want.ravel(), "protein cross local")
+    assert st["status"] == 0
+    # an invalid residue in one target: that column is INT32_MIN, the rest exact
+    tc2 = tc.copy()
+    tc2[to[7]] = 30
+    got2, st2 = ga.align_cross(dev[0], dev[1], torch.from_numpy(tc2).to(d), dev[3], mat, 11, 1, "local",
+                               stats=True)
+    g2 = got2.cpu().numpy()
+    assert st2["status"] == 5 and np.all(g2[:, 7] == np.iinfo(np.int32).min)
+    keep = [l for l in range(len(ts)) if l != 7]
+    assert_same(g2[:, keep].ravel(), want[:, keep].ravel(), "protein cross, invalid target")
+
+
+def test_protein_cross_int16_rerun():
+    # identical 7000-residue sequences: the local score exceeds the int16 range,
+    # the pair is flagged and recomputed exactly in int32
+    rng = np.random.default_rng(13)
+    bg = np.concatenate([synth.PROTEIN_BACKGROUND, np.zeros(4)])
+    q = rng.choice(24, size=7000, p=bg).astype(np.uint8)
+    qs = [q, q[:300]]
+    ts = [q.copy(), rng.choice(24, size=500, p=bg).astype(np.uint8)]
+    qc, qo = synth.pack_csr(qs)
+    tc, to = synth.pack_csr(ts)
+    mat = synth.blosum62()
+    dev = [torch.from_numpy(a).cuda() for a in (qc, qo, tc, to)]
+    got, st = ga.align_cross(*dev, mat, 11, 1, "local", stats=True)
+    want, _ = oracle.cross(qc, qo, tc, to, mat, 11, 1, "local", nthreads=NTHREADS)
+    assert want[0, 0] > 32767
+    assert_same(got.cpu().numpy().ravel(), want.ravel(), "protein rerun")
+    assert st["pairs_int32_rerun"] >= 1
+
+
 @pytest.mark.parametrize("mode", MODES)
 def test_cross_small(mode):
     cr = synth.protein_database(nq=6, qmin=20, qmax=300, nt=80, median=120, seed=31)
