@@ -10,9 +10,11 @@ metric is GCUPS: full-DP cells (sum of m*n, both modes) per second.
 
 The line also carries "serve": p50/p99 latency and GCUPS of a Poisson stream
 of 200k mixed requests through the alignment server (--no-serve skips it),
-and "band": the learned-band vs full-DP time to exact global
+"band": the learned-band vs full-DP time to exact global
 scores on 20k long DNA pairs (|Q| ~ U{1000..20000}, divergence 1-15 %), with
-the band predictor trained first on its own seeded pairs (--no-band skips it).
+the band predictor trained first on its own seeded pairs (--no-band skips it),
+and "protein": GCUPS of 512 protein queries against a 200k-target database in
+local mode with BLOSUM62 (--no-protein skips it).
 
 Multi-GPU (torchrun, one process per GPU): every rank aligns its own seeded
 batch of the same shape (weak scaling, no data-path collective); the step time
@@ -64,6 +66,9 @@ def parse_args():
     ap.add_argument("--band-pairs", type=int, default=20_000)
     ap.add_argument("--band-train", type=int, default=4_000)
     ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
+    ap.add_argument("--no-protein", action="store_true", help="skip the protein database search")
+    ap.add_argument("--protein-queries", type=int, default=512)
+    ap.add_argument("--protein-targets", type=int, default=200_000)
     ap.add_argument("--serve-requests", type=int, default=200_000)
     return ap.parse_args()
 
@@ -343,6 +348,72 @@ def serve_section(ga, dev, nreq: int, load: float = 0.7, burst: int = 50_000):
     }
 
 
+def protein_section(ga, dev, stream, nq: int, nt: int, reps: int = 2, check_targets: int = 512):
+    """Protein database search: every query against every target, local mode.
+
+    512 queries |Q| ~ U{100..1000} against 200k targets |T| ~ LogNormal(ln 300,
+    0.6) in [10, 5000], BLOSUM62 background residues, gap open 11, extend 1,
+    through ga_align_cross (packed int16x2 query-profile kernel, flagged pairs
+    rerun in int32).  GCUPS = sum over pairs of m*n / time.  The int16 scores
+    of every query against a seeded sample of targets (the 64 longest
+    included) are checked against the int32 warp-per-pair path of
+    ga_align_batch on the same pairs.
+    """
+    import torch
+    t0 = time.perf_counter()
+    cr = synth.protein_database(nq=nq, nt=nt)
+    gen_s = time.perf_counter() - t0
+    d = [torch.from_numpy(np.ascontiguousarray(a)).to(dev) for a in (cr.q_codes, cr.q_off, cr.t_codes, cr.t_off)]
+    scores = torch.empty((cr.nq, cr.nt), dtype=torch.int32, device=dev)
+    # warm-up on a few queries (kernel attributes, workspace pool)
+    ga.align_cross(d[0], d[1][:9], d[2], d[3], cr.matrix, cr.alpha, cr.beta, "local", stream=stream)
+    torch.cuda.synchronize(dev)
+    times, st = [], None
+    for _ in range(reps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        _, st = ga.align_cross(*d, cr.matrix, cr.alpha, cr.beta, "local", scores=scores, stream=stream,
+                               stats=True)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        times.append(e0.elapsed_time(e1))
+    ms = float(np.median(times))
+    cells = cr.cells()
+    # sampled int32 check: all queries x `check_targets` targets
+    rng = np.random.default_rng(synth.SEED_BASE + 303)
+    tl = np.diff(cr.t_off)
+    longest = np.argsort(tl)[-64:]
+    pick = np.unique(np.concatenate([longest, rng.choice(cr.nt, size=check_targets - 64, replace=False)]))
+    qi = np.repeat(np.arange(cr.nq), len(pick))
+    ti = np.tile(pick, cr.nq)
+    qo = np.concatenate([[0], np.cumsum(np.diff(cr.q_off)[qi])]).astype(np.int64)
+    to = np.concatenate([[0], np.cumsum(tl[ti])]).astype(np.int64)
+    qstart = torch.from_numpy(cr.q_off[qi]).to(dev)
+    tstart = torch.from_numpy(cr.t_off[ti]).to(dev)
+    dqo, dto = torch.from_numpy(qo).to(dev), torch.from_numpy(to).to(dev)
+    # gather the pairs' residues on the device (index arithmetic only)
+    qidx = torch.repeat_interleave(qstart - dqo[:-1], dqo.diff()) + torch.arange(int(qo[-1]), device=dev)
+    tidx = torch.repeat_interleave(tstart - dto[:-1], dto.diff()) + torch.arange(int(to[-1]), device=dev)
+    ref = ga.align_batch(d[0][qidx], dqo, d[2][tidx], dto, cr.matrix, cr.alpha, cr.beta, "local", stream=stream)
+    got = scores[torch.from_numpy(qi).to(dev), torch.from_numpy(ti).to(dev)]
+    exact = bool(torch.equal(ref, got))
+    return {
+        "metric": "GCUPS", "higher_is_better": True,
+        "workload": f"{cr.nq} protein queries L~U{{100..1000}} x {cr.nt} targets L~LogNormal(ln 300, 0.6) "
+                    "in [10, 5000]; local, BLOSUM62, gap open 11, extend 1",
+        "ms": ms, "ms_runs": times, "cells": cells, "gcups": cells / ms / 1e6,
+        "dp_ms": st["dp_ms"], "dp_gcups": cells / st["dp_ms"] / 1e6 if st["dp_ms"] > 0 else None,
+        "pairs_int32_rerun": st["pairs_int32_rerun"], "status": st["status"],
+        "exact_vs_int32_sample": exact, "checked_pairs": int(len(qi)), "gen_s": gen_s,
+        "roofline": {"bound": "alu", "ops_per_cell": 9,
+                     "achieved": cells * 9 / (st["dp_ms"] / 1e3) / 1e12 if st["dp_ms"] > 0 else None,
+                     "peak": N_SM * LANES_PER_SM * SIMD * PEAK_SM_MHZ * 1e6 / 1e12,
+                     "unit": "Tops/s (int16, 9 ops per local cell)",
+                     "kernel": "kp_kernel (packed int16x2 query-profile kernel)"},
+    }
+
+
 def run_reference(args, rank: int):
     if rank != 0:
         return
@@ -514,6 +585,9 @@ def main():
     band_res = None
     if world == 1 and not args.no_band:
         band_res = band_section(ga, dev, stream, args.band_pairs, args.band_train)
+    prot_res = None
+    if world == 1 and not args.no_protein:
+        prot_res = protein_section(ga, dev, stream, args.protein_queries, args.protein_targets)
     serve_res = None
     if world == 1 and not args.no_serve:
         serve_res = serve_section(ga, dev, args.serve_requests)
@@ -532,7 +606,7 @@ def main():
                 "l2": "inputs larger than L2 (2 x 200 MB raw codes re-read each step)",
             },
             "clocks": clocks, "roofline": roofline, "e2e": e2e, "cpu_baseline": cpu,
-            "band": band_res, "serve": serve_res,
+            "band": band_res, "protein": prot_res, "serve": serve_res,
             "gpu_launches": launches, "dp_status": max(status) if status else 0,
             "pairs_int16_per_step": int16_pairs / args.steps,
         }
