@@ -13,8 +13,10 @@ of 200k mixed requests through the alignment server (--no-serve skips it),
 "band": the learned-band vs full-DP time to exact global
 scores on 20k long DNA pairs (|Q| ~ U{1000..20000}, divergence 1-15 %), with
 the band predictor trained first on its own seeded pairs (--no-band skips it),
-and "protein": GCUPS of 512 protein queries against a 200k-target database in
-local mode with BLOSUM62 (--no-protein skips it).
+"protein": GCUPS of 512 protein queries against a 200k-target database in
+local mode with BLOSUM62 (--no-protein skips it), and "plan": preallocated
+batch plans and their CUDA-graph replays against eager calls, on 1,000
+150 x 150 pairs and on the 1M-pair step with autotuned bins (--no-plan).
 
 Multi-GPU (torchrun, one process per GPU): every rank aligns its own seeded
 batch of the same shape (weak scaling, no data-path collective); the step time
@@ -67,6 +69,7 @@ def parse_args():
     ap.add_argument("--band-train", type=int, default=4_000)
     ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
     ap.add_argument("--no-protein", action="store_true", help="skip the protein database search")
+    ap.add_argument("--no-plan", action="store_true", help="skip the batch-plan / graph measurement")
     ap.add_argument("--protein-queries", type=int, default=512)
     ap.add_argument("--protein-targets", type=int, default=200_000)
     ap.add_argument("--serve-requests", type=int, default=200_000)
@@ -414,6 +417,84 @@ def protein_section(ga, dev, stream, nq: int, nt: int, reps: int = 2, check_targ
     }
 
 
+def plan_section(ga, dev, stream, big, d_big, reps: int = 200):
+    """Batch plans: eager calls vs preallocated runs vs CUDA-graph replays.
+
+    small: 1,000 pairs of 150 x 150 uniform DNA, local mode (+2/-3, 5/2), the
+    launch-bound case; `reps` back-to-back calls per path, CUDA events around
+    the loop.  large: the 1M-pair mutated-DNA step (global + semi-global)
+    replayed from graphs of autotuned plans (tuned on a 100k-pair sample of
+    another seed), against the eager ga_align_batch step.
+    """
+    import torch
+    out = {}
+    c1 = synth.uniform_dna_pairs()
+    d1 = [torch.from_numpy(np.ascontiguousarray(a)).to(dev) for a in (c1.q_codes, c1.q_off, c1.t_codes, c1.t_off)]
+    s1 = torch.empty(c1.npairs, dtype=torch.int32, device=dev)
+
+    def loop_ms(fn, n):
+        fn()
+        torch.cuda.synchronize(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(n):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        return e0.elapsed_time(e1) / n
+
+    eager = loop_ms(lambda: ga.align_batch(*d1, c1.matrix, c1.alpha, c1.beta, "local", scores=s1, stream=stream),
+                    reps)
+    ref = s1.clone()
+    with ga.Plan(c1.matrix, c1.alpha, c1.beta, "local", c1.npairs, max(c1.q_off[-1], c1.t_off[-1]), 160) as pl:
+        run_untuned = loop_ms(lambda: pl.run(*d1, scores=s1, stream=stream), reps)
+        tuning1, _ = pl.autotune(*d1, reps=20, stream=stream)
+        run = loop_ms(lambda: pl.run(*d1, scores=s1, stream=stream), reps)
+        pl.capture(*d1, s1)
+        graph = loop_ms(lambda: pl.launch(stream), reps)
+        exact = bool(torch.equal(s1, ref))
+    cells = c1.cells()
+    out["small"] = {"workload": "1000 DNA pairs 150 x 150, local", "cells": cells, "tuning": tuning1,
+                    "eager_us": eager * 1e3, "plan_run_untuned_us": run_untuned * 1e3,
+                    "plan_run_us": run * 1e3, "graph_us": graph * 1e3,
+                    "eager_gcups": cells / eager / 1e6, "plan_run_gcups": cells / run / 1e6,
+                    "graph_gcups": cells / graph / 1e6, "exact": exact}
+
+    sample = synth.mutated_dna_pairs(npairs=100_000, seed=synth.SEED_BASE + 2 + 777)
+    ds = [torch.from_numpy(np.ascontiguousarray(a)).to(dev) for a in
+          (sample.q_codes, sample.q_off, sample.t_codes, sample.t_off)]
+    cap = int(max(big.q_off[-1], big.t_off[-1]))
+    outs = {m: torch.empty(big.npairs, dtype=torch.int32, device=dev) for m in ("global", "semiglobal")}
+    plans, tunings = {}, {}
+    for m in ("global", "semiglobal"):
+        plans[m] = ga.Plan(big.matrix, big.alpha, big.beta, m, big.npairs, cap, 512)
+        tunings[m], _ = plans[m].autotune(*ds, reps=5, stream=stream)
+        plans[m].capture(*d_big, outs[m])
+
+    def graph_step():
+        plans["global"].launch(stream)
+        plans["semiglobal"].launch(stream)
+
+    step_ms = loop_ms(graph_step, 10)
+    tmp = torch.empty(big.npairs, dtype=torch.int32, device=dev)
+    eager_big = loop_ms(lambda: [ga.align_batch(*d_big, big.matrix, big.alpha, big.beta, m, scores=tmp,
+                                                stream=stream) for m in ("global", "semiglobal")], 5)
+    ref_g = ga.align_batch(*d_big, big.matrix, big.alpha, big.beta, "global", stream=stream)
+    ref_s = ga.align_batch(*d_big, big.matrix, big.alpha, big.beta, "semiglobal", stream=stream)
+    graph_step()
+    torch.cuda.synchronize(dev)
+    exact_big = bool(torch.equal(ref_g, outs["global"]) and torch.equal(ref_s, outs["semiglobal"]))
+    for p in plans.values():
+        p.close()
+    cells_big = 2 * big.cells()
+    out["large"] = {"workload": f"{big.npairs} mutated DNA pairs, global + semi-global (one bench step)",
+                    "tuning": tunings, "graph_step_ms": step_ms, "eager_step_ms": eager_big,
+                    "graph_gcups": cells_big / step_ms / 1e6, "eager_gcups": cells_big / eager_big / 1e6,
+                    "exact": exact_big}
+    return out
+
+
 def run_reference(args, rank: int):
     if rank != 0:
         return
@@ -585,6 +666,9 @@ def main():
     band_res = None
     if world == 1 and not args.no_band:
         band_res = band_section(ga, dev, stream, args.band_pairs, args.band_train)
+    plan_res = None
+    if world == 1 and not args.no_plan:
+        plan_res = plan_section(ga, dev, stream, b, (q, qo, t, to))
     prot_res = None
     if world == 1 and not args.no_protein:
         prot_res = protein_section(ga, dev, stream, args.protein_queries, args.protein_targets)
@@ -606,7 +690,7 @@ def main():
                 "l2": "inputs larger than L2 (2 x 200 MB raw codes re-read each step)",
             },
             "clocks": clocks, "roofline": roofline, "e2e": e2e, "cpu_baseline": cpu,
-            "band": band_res, "protein": prot_res, "serve": serve_res,
+            "band": band_res, "protein": prot_res, "plan": plan_res, "serve": serve_res,
             "gpu_launches": launches, "dp_status": max(status) if status else 0,
             "pairs_int16_per_step": int16_pairs / args.steps,
         }

@@ -12,7 +12,8 @@ from ._binding import (LOCAL, GLOBAL, SEMIGLOBAL, EXPORTED, GotohError, Scoring,
                        align_long_noalloc, NOALLOC_MAX_LEN, PROBES, probe_issue_rate,
                        lib_path, load, make_scoring, strerror, version, BAND_NFEAT, MLP_NPARAMS,
                        band_features, band_min_w, band_predict, mlp_forward, mlp_loss_grad,
-                       mlp_train, mlp_cast, Server, RESULT_DTYPE, SERVE_MAX_LEN)
+                       mlp_train, mlp_cast, Server, RESULT_DTYPE, SERVE_MAX_LEN, Plan, Tuning,
+                       TILE_K)
 from .build import build
 
 __all__ = [
@@ -21,5 +22,5 @@ __all__ = [
     "NOALLOC_MAX_LEN", "PROBES", "probe_issue_rate", "lib_path", "load",
     "make_scoring", "strerror", "version", "build", "BAND_NFEAT", "MLP_NPARAMS", "band_features",
     "band_min_w", "band_predict", "mlp_forward", "mlp_loss_grad", "mlp_train", "mlp_cast",
-    "Server", "RESULT_DTYPE", "SERVE_MAX_LEN",
+    "Server", "RESULT_DTYPE", "SERVE_MAX_LEN", "Plan", "Tuning", "TILE_K",
 ]

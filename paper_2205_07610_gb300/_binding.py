@@ -33,7 +33,10 @@ EXPORTED = ("ga_align_batch", "ga_align_batch_host", "ga_align_cross", "ga_align
             "ga_mlp_forward", "ga_mlp_loss_grad", "ga_mlp_train", "ga_mlp_cast",
             "ga_server_create", "ga_server_add_scoring", "ga_server_submit_batch",
             "ga_server_poll", "ga_server_drain", "ga_server_clock_ns", "ga_server_stats_get",
-            "ga_server_destroy")
+            "ga_server_destroy", "ga_plan_create", "ga_plan_run", "ga_plan_capture",
+            "ga_plan_launch", "ga_plan_stats", "ga_plan_autotune", "ga_plan_get_tuning",
+            "ga_plan_set_tuning", "ga_plan_destroy")
+TILE_K = (8, 10, 12, 14, 16, 18, 20, 24, 32)  # columns per lane of tile 0..8 (16 lanes per pair)
 SERVE_MAX_LEN = 65536
 BAND_NFEAT = 32
 MLP_NPARAMS = 6337
@@ -74,6 +77,17 @@ class ServerStats(ctypes.Structure):
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class Tuning(ctypes.Structure):
+    """ga_tuning: active tiles of the int16x2 / int32 bins and bin concurrency."""
+    _fields_ = [("tiles16", ctypes.c_uint32), ("tiles32", ctypes.c_uint32),
+                ("concurrent", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+    def as_dict(self) -> dict:
+        return {"tiles16": [TILE_K[k] for k in range(len(TILE_K)) if self.tiles16 >> k & 1],
+                "tiles32": [TILE_K[k] for k in range(len(TILE_K)) if self.tiles32 >> k & 1],
+                "concurrent": int(self.concurrent)}
 
 
 RESULT_DTYPE = np.dtype([("id", np.int64), ("score", np.int32), ("status", np.int32),
@@ -137,10 +151,22 @@ def load(build_if_missing: bool = False):
     for f in ("ga_server_create", "ga_server_add_scoring", "ga_server_submit_batch",
               "ga_server_poll", "ga_server_drain", "ga_server_stats_get", "ga_server_destroy"):
         getattr(lib, f).restype = i32
+    tp = ctypes.POINTER(Tuning)
+    lib.ga_plan_create.argtypes = [sp, i32, i64, i64, i32, vp]
+    lib.ga_plan_run.argtypes = [P, P, P, P, P, i64, P, P]
+    lib.ga_plan_capture.argtypes = [P, P, P, P, P, i64, P]
+    lib.ga_plan_launch.argtypes = [P, P]
+    lib.ga_plan_stats.argtypes = [P, P, stp]
+    lib.ga_plan_autotune.argtypes = [P, P, P, P, P, i64, P, i32, P, tp, ctypes.POINTER(f32)]
+    lib.ga_plan_get_tuning.argtypes = [P, tp]
+    lib.ga_plan_set_tuning.argtypes = [P, tp]
+    lib.ga_plan_destroy.argtypes = [P]
     for f in ("ga_align_batch", "ga_align_batch_host", "ga_align_cross", "ga_align_long",
               "ga_align_long_noalloc", "ga_align_banded", "ga_band_features", "ga_band_min_w",
               "ga_band_predict", "ga_mlp_forward", "ga_mlp_loss_grad", "ga_mlp_train",
-              "ga_mlp_cast"):
+              "ga_mlp_cast", "ga_plan_create", "ga_plan_run", "ga_plan_capture", "ga_plan_launch",
+              "ga_plan_stats", "ga_plan_autotune", "ga_plan_get_tuning", "ga_plan_set_tuning",
+              "ga_plan_destroy"):
         getattr(lib, f).restype = i32
     lib.ga_probe_issue_rate.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                         ctypes.POINTER(ctypes.c_float),
@@ -521,6 +547,107 @@ class Server:
     def close(self) -> None:
         if getattr(self, "_h", None):
             load().ga_server_destroy(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Plan:
+    """Batch plan (include/gotoh_plan.h): ga_align_batch with its workspace
+    allocated once, capture-safe runs, CUDA-graph replay and an autotuner.
+
+    Inputs are device CSR tensors as for align_batch; q_off[npairs] and
+    t_off[npairs] must not exceed max_residues, sequences not max_len."""
+
+    def __init__(self, matrix, gap_open: int, gap_extend: int, mode, max_pairs: int,
+                 max_residues: int, max_len: int):
+        sc, keep = make_scoring(matrix, gap_open, gap_extend)
+        h = ctypes.c_void_p()
+        rc = load().ga_plan_create(ctypes.byref(sc), _mode(mode), int(max_pairs), int(max_residues),
+                                   int(max_len), ctypes.byref(h))
+        if rc:
+            raise GotohError(rc, "ga_plan_create")
+        self._h = h
+        self._captured = None
+
+    def run(self, q_codes, q_off, t_codes, t_off, scores=None, stream=None):
+        import torch
+        _check_dev(q_codes, q_off, t_codes, t_off)
+        npairs = q_off.numel() - 1
+        if scores is None:
+            scores = torch.empty(max(npairs, 0), dtype=torch.int32, device=q_codes.device)
+        rc = load().ga_plan_run(self._h, _ptr(q_codes), _ptr(q_off), _ptr(t_codes), _ptr(t_off), npairs,
+                                _ptr(scores), _stream_ptr(stream))
+        if rc:
+            raise GotohError(rc, "ga_plan_run")
+        return scores
+
+    def capture(self, q_codes, q_off, t_codes, t_off, scores):
+        """Record one run on these buffers into the plan's CUDA graph."""
+        _check_dev(q_codes, q_off, t_codes, t_off, scores)
+        npairs = q_off.numel() - 1
+        rc = load().ga_plan_capture(self._h, _ptr(q_codes), _ptr(q_off), _ptr(t_codes), _ptr(t_off),
+                                    npairs, _ptr(scores))
+        if rc:
+            raise GotohError(rc, "ga_plan_capture")
+        self._captured = (q_codes, q_off, t_codes, t_off, scores)  # keep the buffers alive
+
+    def launch(self, stream=None):
+        rc = load().ga_plan_launch(self._h, _stream_ptr(stream))
+        if rc:
+            raise GotohError(rc, "ga_plan_launch")
+
+    def stats(self, stream=None) -> dict:
+        st = Stats()
+        rc = load().ga_plan_stats(self._h, _stream_ptr(stream), ctypes.byref(st))
+        if rc:
+            raise GotohError(rc, "ga_plan_stats")
+        return st.as_dict()
+
+    def autotune(self, q_codes, q_off, t_codes, t_off, reps: int = 5, stream=None):
+        """(tuning dict, median ms) of the fastest tuning on this sample batch."""
+        import torch
+        _check_dev(q_codes, q_off, t_codes, t_off)
+        npairs = q_off.numel() - 1
+        scores = torch.empty(max(npairs, 1), dtype=torch.int32, device=q_codes.device)
+        tu = Tuning()
+        ms = ctypes.c_float(0.0)
+        rc = load().ga_plan_autotune(self._h, _ptr(q_codes), _ptr(q_off), _ptr(t_codes), _ptr(t_off),
+                                     npairs, _ptr(scores), int(reps), _stream_ptr(stream),
+                                     ctypes.byref(tu), ctypes.byref(ms))
+        if rc:
+            raise GotohError(rc, "ga_plan_autotune")
+        self._captured = None
+        return tu.as_dict(), float(ms.value)
+
+    @property
+    def tuning(self) -> Tuning:
+        tu = Tuning()
+        rc = load().ga_plan_get_tuning(self._h, ctypes.byref(tu))
+        if rc:
+            raise GotohError(rc, "ga_plan_get_tuning")
+        return tu
+
+    @tuning.setter
+    def tuning(self, tu: Tuning):
+        rc = load().ga_plan_set_tuning(self._h, ctypes.byref(tu))
+        if rc:
+            raise GotohError(rc, "ga_plan_set_tuning")
+        self._captured = None
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            load().ga_plan_destroy(self._h)
             self._h = None
 
     def __enter__(self):

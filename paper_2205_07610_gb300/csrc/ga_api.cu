@@ -1,12 +1,14 @@
 // ga_api.cu -- the C ABI (include/gotoh_align.h): argument checks, workspace,
 // planning (encode, classify, length sort) and kernel dispatch.
 #include <algorithm>
+#include <memory>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
 #include <vector>
 
 #include "../../include/gotoh_band.h"
+#include "../../include/gotoh_plan.h"
 #include "ga_band.cuh"
 #include "ga_banded.cuh"
 #include "ga_pool.h"
@@ -172,6 +174,12 @@ __global__ void fill_off_kernel(int64_t *off, int64_t a, int64_t b) {
 }
 
 __global__ void count_reruns_kernel(const int32_t *rerun_range, int32_t *total) {
+  *total += rerun_range[1];
+}
+
+// Plan runs: the rerun list [0, count) as a kernel range, counted in total.
+__global__ void rerun_setup_kernel(int32_t *rerun_range, int32_t *total) {
+  rerun_range[0] = 0;
   *total += rerun_range[1];
 }
 
@@ -903,6 +911,452 @@ int cross_protein_local(Call &c, const uint8_t *q_codes, const int64_t *q_off, i
   return rc;
 }
 
+
+// ---- batch plans (include/gotoh_plan.h) ---------------------------------
+// The workspace of a batch is allocated once; a run enqueues the same
+// kernels as ga_align_batch, but with every size that batch_impl reads back
+// from the device (the residue range of each set, the bin populations, the
+// longest long-class pair) replaced by the plan's capacity, so nothing in a
+// run waits for the host and the whole run can be captured in a graph.
+
+constexpr int kPlanSide = 4;  // side streams for concurrent bins
+static_assert(GA_TILE_COUNT == kKaNumBins, "one tuning bit per inter-sequence tile");
+
+struct PlanImpl {
+  int dev = 0, nsm = 0, mode = 0;
+  Scoring sc;
+  int64_t max_pairs = 0, max_res = 0;
+  int32_t max_len = 0;
+  ga_tuning tune{};
+  int occ16[kKaNumBins] = {}, occ32[kKaNumBins] = {};
+  int occ_kb = 0, long_grid = 0;
+  size_t long_smem = 0;
+  Small *small = nullptr;
+  int32_t *hist = nullptr, *cursor = nullptr;
+  uint32_t *packed_q = nullptr, *packed_t = nullptr;
+  uint8_t *qbad = nullptr, *tbad = nullptr;
+  uint32_t *keys = nullptr;
+  int4 *info = nullptr;
+  int32_t *sorted = nullptr, *rerun = nullptr;
+  int2 *bnd = nullptr;
+  int64_t bnd_stride = 0;
+  std::vector<void *> allocs;
+  cudaStream_t side[kPlanSide] = {};
+  cudaEvent_t fork = nullptr, join[kPlanSide] = {};
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t exec = nullptr;
+
+  template <class T>
+  T *alloc(size_t n) {
+    void *p = nullptr;
+    if (cudaMalloc(&p, n * sizeof(T) + 256) != cudaSuccess) return nullptr;
+    allocs.push_back(p);
+    return (T *)p;
+  }
+  void drop_graph() {
+    if (exec) cudaGraphExecDestroy(exec);
+    exec = nullptr;
+  }
+  ~PlanImpl() {
+    drop_graph();
+    for (void *p : allocs) cudaFree(p);
+    for (int i = 0; i < kPlanSide; ++i) {
+      if (side[i]) cudaStreamDestroy(side[i]);
+      if (join[i]) cudaEventDestroy(join[i]);
+    }
+    if (fork) cudaEventDestroy(fork);
+    if (cap_stream) cudaStreamDestroy(cap_stream);
+  }
+};
+
+int plan_occupancy(int cls, int mode, int bin) {
+  if (cls == 0)
+    return mode == GA_LOCAL ? blocks_per_sm_ka16_local(bin) : mode == GA_GLOBAL ? blocks_per_sm_ka16_global(bin)
+                                                                                : blocks_per_sm_ka16_semi(bin);
+  return mode == GA_LOCAL ? blocks_per_sm_ka32_local(bin) : mode == GA_GLOBAL ? blocks_per_sm_ka32_global(bin)
+                                                                              : blocks_per_sm_ka32_semi(bin);
+}
+
+cudaError_t plan_launch_ka(int cls, int mode, int tile, const KAParams &ka, int grid, cudaStream_t s) {
+  if (cls == 0)
+    return mode == GA_LOCAL ? launch_ka16_local(tile, ka, grid, s) : mode == GA_GLOBAL ? launch_ka16_global(tile, ka, grid, s)
+                                                                                       : launch_ka16_semi(tile, ka, grid, s);
+  return mode == GA_LOCAL ? launch_ka32_local(tile, ka, grid, s) : mode == GA_GLOBAL ? launch_ka32_global(tile, ka, grid, s)
+                                                                                     : launch_ka32_semi(tile, ka, grid, s);
+}
+
+int plan_create(const ga_scoring *scoring, int32_t mode, int64_t max_pairs, int64_t max_res, int32_t max_len,
+                PlanImpl **out) {
+  if (!out || mode < 0 || mode > 2 || max_pairs < 1 || max_pairs >= (1ll << 31) - 64 || max_res < 0 ||
+      max_len < 1 || max_len > (1 << 24))
+    return GA_ERR_ARG;
+  std::unique_ptr<PlanImpl> P(new PlanImpl());
+  int rc = check_scoring(scoring, &P->sc);
+  if (rc) return rc;
+  P->mode = mode;
+  P->max_pairs = max_pairs;
+  P->max_res = max_res;
+  P->max_len = max_len;
+  P->tune.tiles16 = P->tune.tiles32 = (1u << kKaNumBins) - 1;
+  P->tune.concurrent = 0;
+  if (cudaGetDevice(&P->dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&P->nsm, cudaDevAttrMultiProcessorCount, P->dev) != cudaSuccess)
+    return GA_ERR_CUDA;
+  const bool dna = P->sc.A <= 4;
+  for (int b = 0; b < kKaNumBins; ++b) {
+    P->occ16[b] = std::max(plan_occupancy(0, mode, b), 1);
+    P->occ32[b] = std::max(plan_occupancy(1, mode, b), 1);
+  }
+  P->long_smem = dna ? 0 : (size_t)kKbWarps * (size_t)(P->sc.A + 1) * (32 * kKbK);
+  P->occ_kb = dna ? (mode == GA_LOCAL ? blocks_per_sm_kb_local_sel(0) : mode == GA_GLOBAL ? blocks_per_sm_kb_global_sel(0)
+                                                                                         : blocks_per_sm_kb_semi_sel(0))
+                  : (mode == GA_LOCAL ? blocks_per_sm_kb_local_prof(P->long_smem)
+                                      : mode == GA_GLOBAL ? blocks_per_sm_kb_global_prof(P->long_smem)
+                                                          : blocks_per_sm_kb_semi_prof(P->long_smem));
+  P->occ_kb = std::max(P->occ_kb, 1);
+  P->long_grid = (int)std::min<int64_t>((int64_t)P->nsm * P->occ_kb, (max_pairs + kKbWarps - 1) / kKbWarps);
+  P->bnd_stride = (int64_t)max_len + 128;
+  P->small = P->alloc<Small>(1);
+  P->hist = P->alloc<int32_t>(kNumKeys);
+  P->cursor = P->alloc<int32_t>(kNumKeys);
+  if (dna) {
+    P->packed_q = P->alloc<uint32_t>((size_t)(max_res / 16 + 2));
+    P->packed_t = P->alloc<uint32_t>((size_t)(max_res / 16 + 2));
+  }
+  P->qbad = P->alloc<uint8_t>((size_t)max_pairs + 1);
+  P->tbad = P->alloc<uint8_t>((size_t)max_pairs + 1);
+  P->keys = P->alloc<uint32_t>((size_t)max_pairs);
+  P->info = P->alloc<int4>((size_t)max_pairs);
+  P->sorted = P->alloc<int32_t>((size_t)max_pairs);
+  P->rerun = P->alloc<int32_t>((size_t)max_pairs);
+  P->bnd = P->alloc<int2>((size_t)P->long_grid * kKbWarps * (size_t)P->bnd_stride);
+  if (!P->small || !P->hist || !P->cursor || !P->qbad || !P->tbad || !P->keys || !P->info || !P->sorted ||
+      !P->rerun || !P->bnd || (dna && (!P->packed_q || !P->packed_t)))
+    return GA_ERR_OOM;
+  for (int i = 0; i < kPlanSide; ++i)
+    if (cudaStreamCreateWithFlags(&P->side[i], cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&P->join[i], cudaEventDisableTiming) != cudaSuccess)
+      return GA_ERR_CUDA;
+  if (cudaEventCreateWithFlags(&P->fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&P->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+    return GA_ERR_CUDA;
+  *out = P.release();
+  return GA_OK;
+}
+
+// One run, enqueued on s with no host synchronisation and no allocation.
+int plan_enqueue(PlanImpl &P, const uint8_t *q_codes, const int64_t *q_off, const uint8_t *t_codes,
+                 const int64_t *t_off, int64_t npairs, int32_t *scores, cudaStream_t s) {
+  if (npairs < 0 || npairs > P.max_pairs) return GA_ERR_ARG;
+  if (npairs > 0 && (!q_codes || !q_off || !t_codes || !t_off || !scores)) return GA_ERR_ARG;
+  int cur = 0;
+  if (cudaGetDevice(&cur) != cudaSuccess || cur != P.dev) return GA_ERR_ARG;
+  if (cudaMemsetAsync(P.small, 0, sizeof(Small), s) != cudaSuccess ||
+      cudaMemsetAsync(P.hist, 0, sizeof(int32_t) * kNumKeys, s) != cudaSuccess)
+    return GA_ERR_CUDA;
+  if (npairs == 0) return GA_OK;
+  const int A = P.sc.A;
+  const bool dna = A <= 4;
+  const unsigned vb = (unsigned)((npairs + 255) / 256);
+  const unsigned pb = (unsigned)std::max<int64_t>(1, std::min<int64_t>((P.max_res / 16 + 256) / 256, (int64_t)P.nsm * 16));
+  plan_pack_kernel<<<pb, 256, 0, s>>>(q_codes, q_off, npairs, P.max_res, A, P.packed_q, &P.small->invalid_q);
+  plan_pack_kernel<<<pb, 256, 0, s>>>(t_codes, t_off, npairs, P.max_res, A, P.packed_t, &P.small->invalid_t);
+  plan_validate_kernel<<<vb, 256, 0, s>>>(q_codes, q_off, npairs, P.max_res, P.max_len, A, &P.small->invalid_q, P.qbad);
+  plan_validate_kernel<<<vb, 256, 0, s>>>(t_codes, t_off, npairs, P.max_res, P.max_len, A, &P.small->invalid_t, P.tbad);
+
+  // bins: the active tiles, narrowest first
+  int tile16[kKaNumBins], tile32[kKaNumBins], n16 = 0, n32 = 0;
+  for (int b = 0; b < kKaNumBins; ++b) {
+    if (P.tune.tiles16 >> b & 1u) tile16[n16++] = b;
+    if (P.tune.tiles32 >> b & 1u) tile32[n32++] = b;
+  }
+  PlanParams pp{};
+  pp.q_off = q_off;
+  pp.t_off = t_off;
+  pp.npairs = npairs;
+  pp.qbad = P.qbad;
+  pp.tbad = P.tbad;
+  pp.A = A;
+  pp.mode = P.mode;
+  pp.alpha = P.sc.alpha;
+  pp.beta = P.sc.beta;
+  pp.sigma_max = P.sc.smax;
+  pp.sigma_min = P.sc.smin;
+  pp.dna = dna;
+  pp.bins.n16 = n16;
+  pp.bins.n32 = n32;
+  for (int i = 0; i < n16; ++i) pp.bins.w16[i] = kKaG * kKaK[tile16[i]];
+  for (int i = 0; i < n32; ++i) pp.bins.w32[i] = kKaG * kKaK[tile32[i]];
+  pp.scores = scores;
+  pp.keys = P.keys;
+  pp.info = P.info;
+  pp.status = &P.small->status;
+  pp.cells = &P.small->cells;
+  pp.rmax_long = &P.small->rmax_long;
+  plan_kernel<<<vb, 256, 0, s>>>(pp);
+  hist_kernel<<<vb, 256, 0, s>>>(P.keys, npairs, P.hist);
+  scan_partials_kernel<<<kScanTiles, kScanTile, 0, s>>>(P.hist, P.small->scan_partials);
+  scan_apply_kernel<<<kScanTiles, kScanTile, 0, s>>>(P.hist, P.small->scan_partials, P.cursor, P.small->ranges);
+  scatter_kernel<<<vb, 256, 0, s>>>(P.keys, npairs, P.cursor, P.sorted);
+  if (cudaGetLastError() != cudaSuccess) return GA_ERR_CUDA;
+
+  KAParams ka{};
+  ka.packed_q = P.packed_q;
+  ka.packed_t = P.packed_t;
+  ka.q_off = q_off;
+  ka.t_off = t_off;
+  ka.info = P.info;
+  ka.sorted = P.sorted;
+  std::memcpy(ka.tables, P.sc.tables, sizeof(ka.tables));
+  ka.alpha = P.sc.alpha;
+  ka.beta = P.sc.beta;
+  ka.sigma_max_pos = std::max(P.sc.smax, 0);
+  ka.scores = scores;
+  ka.rerun_list = P.rerun;
+  ka.rerun_count = &P.small->rerun_range[1];
+
+  // every bin (widest first) plus the long class, one persistent launch
+  // each; concurrent: round-robin over the side streams, joined on s
+  const bool conc = P.tune.concurrent != 0;
+  int nlaunch = 0, counter = 0;
+  auto stream_for = [&](int i) { return conc ? P.side[i % kPlanSide] : s; };
+  if (conc) {
+    if (cudaEventRecord(P.fork, s) != cudaSuccess) return GA_ERR_CUDA;
+    for (int i = 0; i < kPlanSide; ++i)
+      if (cudaStreamWaitEvent(P.side[i], P.fork, 0) != cudaSuccess) return GA_ERR_CUDA;
+  }
+  if (dna) {
+    for (int cls = 0; cls < 2; ++cls) {
+      const int nb = cls == 0 ? n16 : n32;
+      for (int i = nb - 1; i >= 0; --i) {
+        const int tile = cls == 0 ? tile16[i] : tile32[i];
+        ka.range = &P.small->ranges[2 * (cls * kBins + i)];
+        ka.task_counter = &P.small->counters[counter++];
+        const int occ = cls == 0 ? P.occ16[tile] : P.occ32[tile];
+        const int ppt = (cls == 0 ? 2 : 1) * (32 / kKaG);
+        const int64_t want = (npairs + ppt * (kKaThreads / 32) - 1) / (ppt * (kKaThreads / 32));
+        const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)P.nsm * occ));
+        if (plan_launch_ka(cls, P.mode, tile, ka, grid, stream_for(nlaunch++)) != cudaSuccess) return GA_ERR_CUDA;
+      }
+    }
+  }
+  {
+    KBParams kb{};
+    kb.packed_q = P.packed_q;
+    kb.packed_t = P.packed_t;
+    kb.q_codes = q_codes;
+    kb.t_codes = t_codes;
+    kb.q_off = q_off;
+    kb.t_off = t_off;
+    kb.info = P.info;
+    kb.sorted = P.sorted;
+    kb.range = &P.small->ranges[2 * (kClassLong * kBins)];
+    kb.task_counter = &P.small->counters[counter++];
+    std::memcpy(kb.tables, P.sc.tables, sizeof(kb.tables));
+    std::memcpy(kb.sigma, P.sc.mat, sizeof(kb.sigma));
+    kb.A = A;
+    kb.alpha = P.sc.alpha;
+    kb.beta = P.sc.beta;
+    kb.scores = scores;
+    kb.bnd = P.bnd;
+    kb.bnd_stride = P.bnd_stride;
+    const int grid = std::max(P.long_grid, 1);
+    const cudaStream_t ls = stream_for(nlaunch++);
+    cudaError_t e;
+    if (!dna)
+      e = P.mode == GA_LOCAL ? launch_kb_local_prof(kb, grid, P.long_smem, ls)
+        : P.mode == GA_GLOBAL ? launch_kb_global_prof(kb, grid, P.long_smem, ls)
+                              : launch_kb_semi_prof(kb, grid, P.long_smem, ls);
+    else
+      e = P.mode == GA_LOCAL ? launch_kb_local_sel(kb, grid, 0, ls)
+        : P.mode == GA_GLOBAL ? launch_kb_global_sel(kb, grid, 0, ls)
+                              : launch_kb_semi_sel(kb, grid, 0, ls);
+    if (e != cudaSuccess) return GA_ERR_CUDA;
+  }
+  if (conc) {
+    for (int i = 0; i < kPlanSide; ++i)
+      if (cudaEventRecord(P.join[i], P.side[i]) != cudaSuccess || cudaStreamWaitEvent(s, P.join[i], 0) != cudaSuccess)
+        return GA_ERR_CUDA;
+  }
+  // exact int32 rerun of local int16 pairs that reached the int16 limit
+  if (P.mode == GA_LOCAL && dna && n16 > 0) {
+    rerun_setup_kernel<<<1, 1, 0, s>>>(P.small->rerun_range, &P.small->rerun_total);
+    ka.sorted = P.rerun;
+    ka.range = P.small->rerun_range;
+    ka.rerun_list = nullptr;
+    ka.rerun_count = nullptr;
+    ka.task_counter = &P.small->counters[counter++];
+    const int tile = kKaNumBins - 1;
+    if (plan_launch_ka(1, GA_LOCAL, tile, ka, P.nsm * P.occ32[tile], s) != cudaSuccess) return GA_ERR_CUDA;
+  }
+  return cudaGetLastError() == cudaSuccess ? GA_OK : GA_ERR_CUDA;
+}
+
+int plan_capture(PlanImpl &P, const uint8_t *q_codes, const int64_t *q_off, const uint8_t *t_codes,
+                 const int64_t *t_off, int64_t npairs, int32_t *scores) {
+  P.drop_graph();
+  cudaStream_t s = P.cap_stream;
+  if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return GA_ERR_CUDA;
+  const int rc = plan_enqueue(P, q_codes, q_off, t_codes, t_off, npairs, scores, s);
+  cudaGraph_t g = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(s, &g);
+  if (rc) {
+    if (g) cudaGraphDestroy(g);
+    return rc;
+  }
+  if (e != cudaSuccess || !g) return GA_ERR_CUDA;
+  const cudaError_t ei = cudaGraphInstantiate(&P.exec, g, 0);
+  cudaGraphDestroy(g);
+  if (ei != cudaSuccess) {
+    P.exec = nullptr;
+    return GA_ERR_CUDA;
+  }
+  return GA_OK;
+}
+
+int plan_stats(PlanImpl &P, cudaStream_t s, ga_stats *st) {
+  Readback *rb = (Readback *)pinned_scratch();
+  if (cudaMemcpyAsync(rb, P.small, sizeof(Readback), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return GA_ERR_CUDA;
+  std::memset(st, 0, sizeof(*st));
+  st->cells = (int64_t)rb->cells;
+  st->pairs_int32_rerun = rb->rerun_total;
+  st->status = rb->status;
+  int32_t p16 = 0, p32 = 0, pl = 0;
+  for (int b = 0; b < kBins; ++b) {
+    p16 += rb->ranges[2 * b + 1] - rb->ranges[2 * b];
+    p32 += rb->ranges[2 * (kBins + b) + 1] - rb->ranges[2 * (kBins + b)];
+  }
+  pl = rb->ranges[2 * (kClassLong * kBins) + 1] - rb->ranges[2 * (kClassLong * kBins)];
+  st->pairs_int16 = p16;
+  st->pairs_int32 = p32 + pl;
+  return GA_OK;
+}
+
+// Median device time of `reps` runs (after one untimed run).
+int plan_time(PlanImpl &P, const uint8_t *qc, const int64_t *qo, const uint8_t *tc, const int64_t *to,
+              int64_t npairs, int32_t *scores, int reps, cudaStream_t s, float *ms) {
+  int rc = plan_enqueue(P, qc, qo, tc, to, npairs, scores, s);
+  if (rc) return rc;
+  std::vector<float> t;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) rc = GA_ERR_CUDA;
+  for (int r = 0; !rc && r < reps; ++r) {
+    cudaEventRecord(e0, s);
+    rc = plan_enqueue(P, qc, qo, tc, to, npairs, scores, s);
+    cudaEventRecord(e1, s);
+    float x = 0.f;
+    if (!rc && (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&x, e0, e1) != cudaSuccess))
+      rc = GA_ERR_CUDA;
+    t.push_back(x);
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (rc) return rc;
+  std::sort(t.begin(), t.end());
+  *ms = t[t.size() / 2];
+  return GA_OK;
+}
+
+int plan_autotune(PlanImpl &P, const uint8_t *qc, const int64_t *qo, const uint8_t *tc, const int64_t *to,
+                  int64_t npairs, int32_t *scores, int reps, cudaStream_t s, ga_tuning *out, float *ms_out) {
+  if (reps < 1 || reps > 1000) return GA_ERR_ARG;
+  P.drop_graph();
+  ga_tuning best = P.tune;
+  float tbest = 0.f;
+  int rc = plan_time(P, qc, qo, tc, to, npairs, scores, reps, s, &tbest);
+  if (rc) return rc;
+  auto consider = [&](ga_tuning cand) -> int {
+    P.tune = cand;
+    float t = 0.f;
+    const int r = plan_time(P, qc, qo, tc, to, npairs, scores, reps, s, &t);
+    if (r) return r;
+    if (t < tbest * 0.99f) {
+      tbest = t;
+      best = cand;
+    }
+    P.tune = best;
+    return GA_OK;
+  };
+  // active tiles of the kept tuning that hold pairs of the sample
+  auto live_mask = [&](int cls, uint32_t *live) -> int {
+    P.tune = best;
+    int r = plan_enqueue(P, qc, qo, tc, to, npairs, scores, s);
+    if (r) return r;
+    Readback *rb = (Readback *)pinned_scratch();
+    if (cudaMemcpyAsync(rb, P.small, sizeof(Readback), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+      return GA_ERR_CUDA;
+    const uint32_t mask = cls == 0 ? best.tiles16 : best.tiles32;
+    *live = 0;
+    for (int b = 0, i = 0; b < kKaNumBins; ++b) {
+      if (!(mask >> b & 1u)) continue;
+      const int k = cls * kBins + i++;
+      if (rb->ranges[2 * k + 1] > rb->ranges[2 * k]) *live |= 1u << b;
+    }
+    return GA_OK;
+  };
+  // 1. tiles that no pair of the sample uses: each costs one launch (pairs
+  //    of other batches in their range go to the next wider active tile)
+  {
+    uint32_t l16 = 0, l32 = 0;
+    if ((rc = live_mask(0, &l16)) || (rc = live_mask(1, &l32))) return rc;
+    if (l16 != best.tiles16 || l32 != best.tiles32) {
+      ga_tuning cand = best;
+      // keep the widest tile of each class so that the pairs of its range
+      // stay on the inter-sequence kernels
+      cand.tiles16 = l16 | (best.tiles16 & (1u << (kKaNumBins - 1)));
+      cand.tiles32 = l32 | (best.tiles32 & (1u << (kKaNumBins - 1)));
+      if (l32 == 0) cand.tiles32 = 0;
+      if ((rc = consider(cand))) return rc;
+    }
+  }
+  // 2. bins one after another or concurrent
+  {
+    ga_tuning cand = best;
+    cand.concurrent = !best.concurrent;
+    if ((rc = consider(cand))) return rc;
+  }
+  // 3. greedy removal of non-empty tiles (class by class)
+  for (int cls = 0; cls < 2; ++cls) {
+    for (;;) {
+      uint32_t lm = 0;
+      if ((rc = live_mask(cls, &lm))) return rc;
+      std::vector<int> live;
+      for (int b = 0; b < kKaNumBins; ++b)
+        if (lm >> b & 1u) live.push_back(b);
+      if (live.size() < 2) break;
+      ga_tuning round_best = best;
+      float t_round = tbest;
+      for (int b : live) {
+        ga_tuning cand = best;
+        (cls == 0 ? cand.tiles16 : cand.tiles32) &= ~(1u << b);
+        P.tune = cand;
+        float t = 0.f;
+        if ((rc = plan_time(P, qc, qo, tc, to, npairs, scores, reps, s, &t))) return rc;
+        if (t < t_round) {
+          t_round = t;
+          round_best = cand;
+        }
+      }
+      P.tune = best;
+      if (t_round < tbest * 0.99f) {
+        tbest = t_round;
+        best = round_best;
+        P.tune = best;
+      } else {
+        break;
+      }
+    }
+  }
+  P.tune = best;
+  if (out) *out = best;
+  if (ms_out) *ms_out = tbest;
+  // leave the sample's scores from the kept tuning
+  return plan_enqueue(P, qc, qo, tc, to, npairs, scores, s);
+}
+
 }  // namespace
 }  // namespace ga
 
@@ -1204,11 +1658,80 @@ const char *ga_strerror(int code) {
     case GA_ERR_CUDA: return "CUDA error";
     case GA_ERR_RESIDUE: return "residue code outside the alphabet";
     case GA_ERR_TIMEOUT: return "bounded device wait timed out";
-    case GA_ERR_RANGE: return "scores of a pair could exceed the int32 range";
+    case GA_ERR_RANGE: return "pair outside the supported range (int32 scores, plan capacity)";
     default: return "unknown error";
   }
 }
 
 int ga_version(void) { return 100; }
+
+struct ga_plan {
+  ga::PlanImpl *impl;
+};
+
+int ga_plan_create(const ga_scoring *scoring, int32_t mode, int64_t max_pairs, int64_t max_residues,
+                   int32_t max_len, ga_plan **plan) {
+  if (!plan) return GA_ERR_ARG;
+  *plan = nullptr;
+  ga::PlanImpl *impl = nullptr;
+  const int rc = ga::plan_create(scoring, mode, max_pairs, max_residues, max_len, &impl);
+  if (rc) return rc;
+  *plan = new ga_plan{impl};
+  return GA_OK;
+}
+
+int ga_plan_run(ga_plan *plan, const uint8_t *q_codes, const int64_t *q_off, const uint8_t *t_codes,
+                const int64_t *t_off, int64_t npairs, int32_t *scores, void *stream) {
+  if (!plan) return GA_ERR_ARG;
+  return ga::plan_enqueue(*plan->impl, q_codes, q_off, t_codes, t_off, npairs, scores, (cudaStream_t)stream);
+}
+
+int ga_plan_capture(ga_plan *plan, const uint8_t *q_codes, const int64_t *q_off, const uint8_t *t_codes,
+                    const int64_t *t_off, int64_t npairs, int32_t *scores) {
+  if (!plan) return GA_ERR_ARG;
+  return ga::plan_capture(*plan->impl, q_codes, q_off, t_codes, t_off, npairs, scores);
+}
+
+int ga_plan_launch(ga_plan *plan, void *stream) {
+  if (!plan || !plan->impl->exec) return GA_ERR_ARG;
+  return cudaGraphLaunch(plan->impl->exec, (cudaStream_t)stream) == cudaSuccess ? GA_OK : GA_ERR_CUDA;
+}
+
+int ga_plan_stats(ga_plan *plan, void *stream, ga_stats *stats) {
+  if (!plan || !stats) return GA_ERR_ARG;
+  return ga::plan_stats(*plan->impl, (cudaStream_t)stream, stats);
+}
+
+int ga_plan_autotune(ga_plan *plan, const uint8_t *q_codes, const int64_t *q_off, const uint8_t *t_codes,
+                     const int64_t *t_off, int64_t npairs, int32_t *scores, int32_t reps, void *stream,
+                     ga_tuning *out, float *ms_best) {
+  if (!plan) return GA_ERR_ARG;
+  return ga::plan_autotune(*plan->impl, q_codes, q_off, t_codes, t_off, npairs, scores, reps,
+                           (cudaStream_t)stream, out, ms_best);
+}
+
+int ga_plan_get_tuning(const ga_plan *plan, ga_tuning *out) {
+  if (!plan || !out) return GA_ERR_ARG;
+  *out = plan->impl->tune;
+  return GA_OK;
+}
+
+int ga_plan_set_tuning(ga_plan *plan, const ga_tuning *tuning) {
+  if (!plan || !tuning) return GA_ERR_ARG;
+  const uint32_t all = (1u << GA_TILE_COUNT) - 1;
+  if ((tuning->tiles16 & ~all) || (tuning->tiles32 & ~all) || tuning->concurrent < 0 || tuning->concurrent > 1)
+    return GA_ERR_ARG;
+  plan->impl->drop_graph();
+  plan->impl->tune = *tuning;
+  return GA_OK;
+}
+
+int ga_plan_destroy(ga_plan *plan) {
+  if (!plan) return GA_ERR_ARG;
+  cudaDeviceSynchronize();
+  delete plan->impl;
+  delete plan;
+  return GA_OK;
+}
 
 }  // extern "C"

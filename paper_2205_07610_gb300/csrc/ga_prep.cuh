@@ -62,8 +62,8 @@ __device__ __forceinline__ uint32_t pack4(uint32_t x) {
 // Flat 2-bit packing of the whole code buffer (residue x -> word x/16),
 // one thread per word with a 16-byte load; any code >= A anywhere raises
 // *invalid (per-sequence validation then runs its slow path).
-__global__ void flat_pack_kernel(const uint8_t *codes, int64_t start, int64_t total, int A,
-                                 uint32_t *packed, int32_t *invalid) {
+__device__ __forceinline__ void flat_pack_body(const uint8_t *codes, int64_t start, int64_t total, int A,
+                                               uint32_t *packed, int32_t *invalid) {
   // words start/16 .. (total+15)/16 - 1: the residues [start, total) and the
   // bytes before `start` in its word (which exist: they are codes of the
   // same buffer)
@@ -100,6 +100,43 @@ __global__ void flat_pack_kernel(const uint8_t *codes, int64_t start, int64_t to
   if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(invalid, 1);
 }
 
+__global__ void flat_pack_kernel(const uint8_t *codes, int64_t start, int64_t total, int A,
+                                 uint32_t *packed, int32_t *invalid) {
+  flat_pack_body(codes, start, total, A, packed, invalid);
+}
+
+// Batch plans: the residue range [off[0], off[nseq]) of a set is read on
+// the device and clamped to the plan's capacity `cap` (residues at or
+// beyond cap are never read; validation marks their sequences).
+__global__ void plan_pack_kernel(const uint8_t *codes, const int64_t *off, int64_t nseq, int64_t cap, int A,
+                                 uint32_t *packed, int32_t *invalid) {
+  const int64_t e = off[nseq], b = off[0];
+  const int64_t total = e < 0 ? 0 : (e < cap ? e : cap);
+  const int64_t start = b < 0 ? 0 : (b < total ? b : total);
+  flat_pack_body(codes, start, total, A, packed, invalid);
+}
+
+// Thread per sequence of a plan run: 0 ok, 1 residue code >= A, 2 offsets
+// decreasing (or off[0] < 0), 3 sequence longer than max_len or ending
+// beyond cap.
+__global__ void plan_validate_kernel(const uint8_t *codes, const int64_t *off, int64_t nseq, int64_t cap,
+                                     int64_t max_len, int A, const int32_t *invalid, uint8_t *bad) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nseq) return;
+  const int64_t first = off[0], last = off[nseq];
+  const int64_t s = off[k], e = off[k + 1];
+  uint8_t b = 0;
+  if (first < 0 || s < first || e < s || e > last) {
+    b = 2;
+  } else if (e > cap || e - s > max_len) {
+    b = 3;
+  } else if (*invalid) {
+    for (int64_t x = s; x < e; ++x)
+      if (codes[x] >= (unsigned)A) { b = 1; break; }
+  }
+  bad[k] = b;
+}
+
 // Thread per sequence: 0 ok, 1 residue code >= A, 2 offsets decreasing or
 // outside [start, total] (start = off[0], total = off[nseq]).  Residues are scanned only when the packing pass saw
 // an invalid code somewhere.
@@ -134,7 +171,9 @@ __device__ __forceinline__ void plan_one(const PlanParams &p, int64_t i, unsigne
   const uint8_t qb = p.qbad[qi], tb = p.tbad[ti];
   if (qb || tb || m < 0 || n < 0) {
     p.scores[i] = INT32_MIN;
-    set_status(p.status, (qb == 2 || tb == 2 || m < 0 || n < 0) ? GA_ERR_ARG : GA_ERR_RESIDUE);
+    set_status(p.status, (qb == 2 || tb == 2 || m < 0 || n < 0) ? GA_ERR_ARG
+                         : (qb == 3 || tb == 3)                  ? GA_ERR_RANGE
+                                                                 : GA_ERR_RESIDUE);
   } else if (m == 0 || n == 0) {
     p.scores[i] = (p.mode == GA_GLOBAL) ? global_gap(p.alpha, p.beta, m + n) : 0;
   } else {
