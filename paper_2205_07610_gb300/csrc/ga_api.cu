@@ -771,6 +771,23 @@ int launch_kp(Call &c, KPParams &kp, int64_t max_grid) {
   return cudaGetLastError() == cudaSuccess ? GA_OK : GA_ERR_CUDA;
 }
 
+// Tile (K = 8, 16, 24, 32) of a query of m columns in the protein search.
+int kp_bin_for(int64_t m) {
+  static const double kRate[4] = {0.71, 0.91, 1.0, 0.96};  // per computed cell, K = 8 .. 32
+  int best = 3;
+  double tbest = 1e300;
+  for (int b = 0; b < 4; ++b) {
+    const int64_t w = (int64_t)kKpG * 8 * (b + 1);
+    const int64_t nst = (m + w - 1) / w;
+    const double t = (double)(nst * w) / (kRate[b] * (nst > 1 ? 0.93 : 1.0));
+    if (t < tbest) {
+      tbest = t;
+      best = b;
+    }
+  }
+  return best;
+}
+
 int cross_protein_local(Call &c, const uint8_t *q_codes, const int64_t *q_off, int64_t nq,
                         const uint8_t *t_codes, const int64_t *t_off, int64_t nt, int32_t *scores,
                         ga_stats *stats, cudaEvent_t e0, cudaEvent_t e1) {
@@ -813,13 +830,17 @@ int cross_protein_local(Call &c, const uint8_t *q_codes, const int64_t *q_off, i
                         256, 0, c.s>>>(Q.bad, nq, T.bad, nt, scores, &c.small->status);
     ++c.launches;
   }
-  // query bins
+  // query bins: tile width 16K (K = 8, 16, 24, 32) per query, chosen to
+  // minimise the estimated time ceil(m / 16K) * 16K / rate(K), with the
+  // measured relative rates of the kernel per computed cell (GB300: wider
+  // tiles amortise the per-row work; a query of several stages pays for
+  // its profile rebuilds and stage edges)
   std::vector<int32_t> bins[4];
   int64_t cells = 0, tcells = 0;
   for (int64_t k = 0; k < nq; ++k) {
     if (hqb[k]) continue;
     const int64_t m = hqo[k + 1] - hqo[k];
-    bins[m <= 128 ? 0 : m <= 256 ? 1 : m <= 384 ? 2 : 3].push_back((int32_t)k);
+    bins[kp_bin_for(m)].push_back((int32_t)k);
     cells += m;
   }
   {

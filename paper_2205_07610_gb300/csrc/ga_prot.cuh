@@ -4,7 +4,9 @@
 // The query runs along the columns and its scoring profile
 // P[c][x] = sigma(query residue x, target residue c) lives in shared memory
 // as int8 (Sec. 3.1, "scoring profile"), one copy per warp for the stage of
-// columns it is working on; targets run along the rows.  As in the DNA
+// columns it is working on (rebuilt, one 32-bit word per lane and row, from a
+// transposed sigma table whenever the warp's query or stage changes);
+// targets run along the rows.  As in the DNA
 // inter-sequence kernel, a group of 16 lanes computes one wavefront with K
 // columns per lane, and every lane carries two targets in the two int16
 // halves of each register (int16x2).  For each row a lane loads the K
@@ -55,6 +57,23 @@ struct KPParams {
   int32_t prof_bytes;       // per warp: (A + 1) * 16K
 };
 
+// Profile layout: row c holds the stage's 16K columns; DP lane t reads its K
+// columns at byte t*K.  With K = 32 the two 16-byte halves of lanes whose
+// bit 2 is set are swapped, so that the 8 lanes of a shared-memory phase
+// (two 16-byte loads each) hit 8 different 16-byte bank groups (rows are
+// multiples of 128 bytes, so the row never changes the bank).
+template <int K>
+__device__ __forceinline__ int prof_swizzle(int t) {
+  return K == 32 ? ((t >> 2) & 1) : 0;
+}
+// Byte offset in a row of the K/2 columns L*K/2 .. written by lane L of the
+// rebuild (lane L covers half L&1 of DP lane L/2 when K = 32).
+template <int K>
+__device__ __forceinline__ int prof_offset(int L) {
+  if constexpr (K == 32) return (L >> 1) * 32 + 16 * ((L & 1) ^ prof_swizzle<K>(L >> 1));
+  else return L * (K / 2);
+}
+
 template <int K>
 __global__ void __launch_bounds__(32 * kKpWarps) kp_kernel(const __grid_constant__ KPParams p) {
   using Cell = CellS16x2;
@@ -62,14 +81,19 @@ __global__ void __launch_bounds__(32 * kKpWarps) kp_kernel(const __grid_constant
   constexpr int G = kKpG, W = G * K, kRing = 4 * G;
   static_assert(K % 8 == 0, "profile loads are 8 columns wide");
   extern __shared__ __align__(16) uint8_t kp_smem[];
-  __shared__ int8_t sig_s[32 * 32];
+  // sigma transposed: sigT_s[c * 32 + x] = sigma(query code x, target code c);
+  // rows c >= A and columns x >= A are 0 (x = 31 is the pad column)
+  __shared__ __align__(16) uint8_t sigT_s[32 * 32];
   __shared__ uint32_t ring_s[kKpWarps][2][5 * G];  // row codes of both halves, mirrored ring
   __shared__ uint2 in_ring_s[kKpWarps][2][64];
   __shared__ uint2 out_ring_s[kKpWarps][2][64];
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int g = lane / G, t = lane % G;
-  for (int i = threadIdx.x; i < 32 * 32; i += blockDim.x) sig_s[i] = p.sigma[i];
+  for (int i = threadIdx.x; i < 32 * 32; i += blockDim.x) {
+    const int c = i >> 5, x = i & 31;
+    sigT_s[i] = (uint8_t)((c < p.A && x < p.A) ? p.sigma[x * p.A + c] : 0);
+  }
   __syncthreads();
   uint8_t *prof = kp_smem + (size_t)warp * (size_t)p.prof_bytes;
   uint32_t *ring = ring_s[warp][g];
@@ -107,14 +131,35 @@ __global__ void __launch_bounds__(32 * kKpWarps) kp_kernel(const __grid_constant
 
     for (int s = 0; s < nstage; ++s) {
       // ---- profile of this stage's columns (the whole warp) -------------
+      // Lane L writes the K/2 columns L*K/2 .. of every profile row, one
+      // row at a time, from the transposed sigma table (pad columns and the
+      // pad row A are 0).
       if (k != cur_q || s != cur_stage) {
         __syncwarp();
-        for (int e = lane; e < (A + 1) * W; e += 32) {
-          const int c = e / W, x = e - c * W;
-          const int col = s * W + x;
-          int v = 0;
-          if (c < A && col < m) v = sig_s[(int)p.q_codes[qs + col] * A + c];
-          prof[e] = (uint8_t)(int8_t)v;
+        constexpr int CPL = K / 2;
+        int qx[CPL];
+#pragma unroll
+        for (int j = 0; j < CPL; ++j) {
+          const int col = s * W + lane * CPL + j;
+          qx[j] = col < m ? (int)p.q_codes[qs + col] : 31;
+        }
+        const int pofs = prof_offset<K>(lane);
+        for (int c = 0; c <= A; ++c) {
+          const uint8_t *row = sigT_s + c * 32;
+          uint32_t w[CPL / 4];
+#pragma unroll
+          for (int u = 0; u < CPL / 4; ++u)
+            w[u] = (uint32_t)row[qx[4 * u]] | ((uint32_t)row[qx[4 * u + 1]] << 8) |
+                   ((uint32_t)row[qx[4 * u + 2]] << 16) | ((uint32_t)row[qx[4 * u + 3]] << 24);
+          uint8_t *dst = prof + (size_t)c * W + pofs;
+          if constexpr (CPL == 16) {
+            *reinterpret_cast<uint4 *>(dst) = make_uint4(w[0], w[1], w[2], w[3]);
+          } else if constexpr (CPL == 8) {
+            *reinterpret_cast<uint2 *>(dst) = make_uint2(w[0], w[1]);
+          } else {
+#pragma unroll
+            for (int u = 0; u < CPL / 4; ++u) reinterpret_cast<uint32_t *>(dst)[u] = w[u];
+          }
         }
         cur_q = k;
         cur_stage = s;
@@ -186,9 +231,10 @@ __global__ void __launch_bounds__(32 * kKpWarps) kp_kernel(const __grid_constant
           const uint4 *p1 = reinterpret_cast<const uint4 *>(prof + (size_t)(rc >> 16) * W + t * K);
           uint32_t w0[K / 4], w1[K / 4];
           if constexpr ((K % 16) == 0) {  // lane slices start on 16-byte boundaries
+            const int swz = prof_swizzle<K>(t);
 #pragma unroll
             for (int q = 0; q < K / 16; ++q) {
-              const uint4 a = p0[q], b = p1[q];
+              const uint4 a = p0[q ^ swz], b = p1[q ^ swz];
               w0[4 * q] = a.x; w0[4 * q + 1] = a.y; w0[4 * q + 2] = a.z; w0[4 * q + 3] = a.w;
               w1[4 * q] = b.x; w1[4 * q + 1] = b.y; w1[4 * q + 2] = b.z; w1[4 * q + 3] = b.w;
             }
