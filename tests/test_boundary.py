@@ -73,3 +73,30 @@ def test_argument_errors_are_synchronous(libpath):
     sc, keep = ga.make_scoring(m, 5, 2)
     assert lib.ga_align_batch(None, None, None, None, 0, ctypes.byref(sc), 7, None, None, None) == 1
     assert lib.ga_align_batch(None, None, None, None, -1, ctypes.byref(sc), 0, None, None, None) == 1
+
+
+def test_plan_arguments_rejected_before_any_cuda_call(libpath):
+    """Batch-plan argument errors are returned before the device is touched."""
+    import numpy as np
+    import paper_2205_07610_gb300 as ga
+    lib = ga.load()
+    m = np.zeros((4, 4), dtype=np.int8)
+    sc, keep = ga.make_scoring(m, 5, 2)
+    h = ctypes.c_void_p()
+    # bad mode, max_pairs < 1, negative residues, max_len < 1, null out pointer
+    for mode, mp, mr, ml in ((3, 10, 10, 10), (0, 0, 10, 10), (0, 10, -1, 10), (0, 10, 10, 0)):
+        assert lib.ga_plan_create(ctypes.byref(sc), mode, mp, mr, ml, ctypes.byref(h)) == 1
+    assert lib.ga_plan_create(ctypes.byref(sc), 0, 10, 10, 10, None) == 1
+    bad, keep2 = ga.make_scoring(m, 2, 3)  # gap_extend > gap_open
+    assert lib.ga_plan_create(ctypes.byref(bad), 0, 10, 10, 10, ctypes.byref(h)) == 1
+    tu = ga.Tuning(0x1ff, 0x1ff, 0, 0)
+    for fn, args in (("ga_plan_run", (None, None, None, None, None, 0, None, None)),
+                     ("ga_plan_capture", (None, None, None, None, None, 0, None)),
+                     ("ga_plan_launch", (None, None)),
+                     ("ga_plan_stats", (None, None, None)),
+                     ("ga_plan_get_tuning", (None, ctypes.byref(tu))),
+                     ("ga_plan_set_tuning", (None, ctypes.byref(tu))),
+                     ("ga_plan_destroy", (None,))):
+        assert getattr(lib, fn)(*args) == 1, fn
+    assert ctypes.sizeof(ga.Tuning) == 16
+    assert ga.Tuning(0b100000101, 0, 1, 0).as_dict() == {"tiles16": [8, 12, 32], "tiles32": [], "concurrent": 1}
