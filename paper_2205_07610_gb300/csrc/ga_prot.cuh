@@ -57,25 +57,36 @@ struct KPParams {
   int32_t prof_bytes;       // per warp: (A + 1) * 16K
 };
 
-// Profile layout: row c holds the stage's 16K columns; DP lane t reads its K
-// columns at byte t*K.  With K = 32 the two 16-byte halves of lanes whose
-// bit 2 is set are swapped, so that the 8 lanes of a shared-memory phase
-// (two 16-byte loads each) hit 8 different 16-byte bank groups (rows are
+// Profile layout: row c holds the stage's 16K columns.  With K = 8 or 24
+// (8-byte loads) DP lane t reads its K columns at byte t*K; with K = 16 or
+// 32 (16-byte loads) the row is chunk-major: 16-column chunk q of lane t
+// sits at byte q*256 + t*16, so that the 8 lanes of a shared-memory phase
+// read 8 different 16-byte bank groups with compile-time offsets (rows are
 // multiples of 128 bytes, so the row never changes the bank).
 template <int K>
-__device__ __forceinline__ int prof_swizzle(int t) {
-  return K == 32 ? ((t >> 2) & 1) : 0;
+__device__ __forceinline__ int prof_lane_offset(int t) {
+  return (K % 16) == 0 ? t * 16 : t * K;
 }
 // Byte offset in a row of the K/2 columns L*K/2 .. written by lane L of the
-// rebuild (lane L covers half L&1 of DP lane L/2 when K = 32).
+// rebuild (they belong to DP lane L*K/2 / K).
 template <int K>
 __device__ __forceinline__ int prof_offset(int L) {
-  if constexpr (K == 32) return (L >> 1) * 32 + 16 * ((L & 1) ^ prof_swizzle<K>(L >> 1));
-  else return L * (K / 2);
+  constexpr int CPL = K / 2;
+  const int t = L * CPL / K, c0 = L * CPL - t * K;
+  if constexpr ((K % 16) == 0) return (c0 / 16) * 256 + t * 16 + (c0 % 16);
+  else return L * CPL;
 }
 
+// Resident blocks per SM requested from ptxas: what shared memory allows for
+// BLOSUM-sized alphabets (24 symbols + pad: (A+1) x 16K bytes of profile per
+// warp plus 11.5 KB of static rings per block).
 template <int K>
-__global__ void __launch_bounds__(32 * kKpWarps) kp_kernel(const __grid_constant__ KPParams p) {
+struct KPMinBlocks {
+  static constexpr int value = K <= 8 ? 8 : K <= 16 ? 6 : K <= 24 ? 4 : 3;
+};
+
+template <int K>
+__global__ void __launch_bounds__(32 * kKpWarps, KPMinBlocks<K>::value) kp_kernel(const __grid_constant__ KPParams p) {
   using Cell = CellS16x2;
   using T = uint32_t;
   constexpr int G = kKpG, W = G * K, kRing = 4 * G;
@@ -137,11 +148,16 @@ __global__ void __launch_bounds__(32 * kKpWarps) kp_kernel(const __grid_constant
       if (k != cur_q || s != cur_stage) {
         __syncwarp();
         constexpr int CPL = K / 2;
-        int qx[CPL];
+        uint32_t qx4[CPL / 4];  // 4 codes per word
 #pragma unroll
-        for (int j = 0; j < CPL; ++j) {
-          const int col = s * W + lane * CPL + j;
-          qx[j] = col < m ? (int)p.q_codes[qs + col] : 31;
+        for (int u = 0; u < CPL / 4; ++u) {
+          uint32_t v = 0;
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const int col = s * W + lane * CPL + 4 * u + i;
+            v |= (uint32_t)(col < m ? p.q_codes[qs + col] : 31) << (8 * i);
+          }
+          qx4[u] = v;
         }
         const int pofs = prof_offset<K>(lane);
         for (int c = 0; c <= A; ++c) {
@@ -149,8 +165,8 @@ __global__ void __launch_bounds__(32 * kKpWarps) kp_kernel(const __grid_constant
           uint32_t w[CPL / 4];
 #pragma unroll
           for (int u = 0; u < CPL / 4; ++u)
-            w[u] = (uint32_t)row[qx[4 * u]] | ((uint32_t)row[qx[4 * u + 1]] << 8) |
-                   ((uint32_t)row[qx[4 * u + 2]] << 16) | ((uint32_t)row[qx[4 * u + 3]] << 24);
+            w[u] = (uint32_t)row[qx4[u] & 0xffu] | ((uint32_t)row[(qx4[u] >> 8) & 0xffu] << 8) |
+                   ((uint32_t)row[(qx4[u] >> 16) & 0xffu] << 16) | ((uint32_t)row[qx4[u] >> 24] << 24);
           uint8_t *dst = prof + (size_t)c * W + pofs;
           if constexpr (CPL == 16) {
             *reinterpret_cast<uint4 *>(dst) = make_uint4(w[0], w[1], w[2], w[3]);
@@ -227,22 +243,22 @@ __global__ void __launch_bounds__(32 * kKpWarps) kp_kernel(const __grid_constant
         T Hout = H[K - 1], Fout = Cell::splat(CellInfo<Cell>::kNeg);
         if ((unsigned)(r - 1) < (unsigned)Rtask) {
           const uint32_t rc = ring[r & (kRing - 1)];
-          const uint4 *p0 = reinterpret_cast<const uint4 *>(prof + (size_t)(rc & 0xffffu) * W + t * K);
-          const uint4 *p1 = reinterpret_cast<const uint4 *>(prof + (size_t)(rc >> 16) * W + t * K);
+          const uint8_t *b0 = prof + (size_t)(rc & 0xffffu) * W + prof_lane_offset<K>(t);
+          const uint8_t *b1 = prof + (size_t)(rc >> 16) * W + prof_lane_offset<K>(t);
           uint32_t w0[K / 4], w1[K / 4];
-          if constexpr ((K % 16) == 0) {  // lane slices start on 16-byte boundaries
-            const int swz = prof_swizzle<K>(t);
+          if constexpr ((K % 16) == 0) {  // chunk-major rows, 16-byte loads
 #pragma unroll
             for (int q = 0; q < K / 16; ++q) {
-              const uint4 a = p0[q ^ swz], b = p1[q ^ swz];
+              const uint4 a = *reinterpret_cast<const uint4 *>(b0 + q * 256);
+              const uint4 b = *reinterpret_cast<const uint4 *>(b1 + q * 256);
               w0[4 * q] = a.x; w0[4 * q + 1] = a.y; w0[4 * q + 2] = a.z; w0[4 * q + 3] = a.w;
               w1[4 * q] = b.x; w1[4 * q + 1] = b.y; w1[4 * q + 2] = b.z; w1[4 * q + 3] = b.w;
             }
           } else {  // 8-byte boundaries (K = 8, 24)
 #pragma unroll
             for (int q = 0; q < K / 8; ++q) {
-              const uint2 a = reinterpret_cast<const uint2 *>(p0)[q];
-              const uint2 b = reinterpret_cast<const uint2 *>(p1)[q];
+              const uint2 a = reinterpret_cast<const uint2 *>(b0)[q];
+              const uint2 b = reinterpret_cast<const uint2 *>(b1)[q];
               w0[2 * q] = a.x; w0[2 * q + 1] = a.y;
               w1[2 * q] = b.x; w1[2 * q + 1] = b.y;
             }
