@@ -72,6 +72,8 @@ def parse_args():
     ap.add_argument("--no-plan", action="store_true", help="skip the batch-plan / graph measurement")
     ap.add_argument("--protein-queries", type=int, default=512)
     ap.add_argument("--protein-targets", type=int, default=200_000)
+    ap.add_argument("--protein-qmin", type=int, default=100, help="shortest protein query")
+    ap.add_argument("--protein-qmax", type=int, default=1000, help="longest protein query")
     ap.add_argument("--serve-requests", type=int, default=200_000)
     return ap.parse_args()
 
@@ -351,7 +353,8 @@ def serve_section(ga, dev, nreq: int, load: float = 0.7, burst: int = 50_000):
     }
 
 
-def protein_section(ga, dev, stream, nq: int, nt: int, reps: int = 2, check_targets: int = 512):
+def protein_section(ga, dev, stream, nq: int, nt: int, qmin: int = 100, qmax: int = 1000, reps: int = 2,
+                    check_targets: int = 512):
     """Protein database search: every query against every target, local mode.
 
     512 queries |Q| ~ U{100..1000} against 200k targets |T| ~ LogNormal(ln 300,
@@ -364,7 +367,7 @@ def protein_section(ga, dev, stream, nq: int, nt: int, reps: int = 2, check_targ
     """
     import torch
     t0 = time.perf_counter()
-    cr = synth.protein_database(nq=nq, nt=nt)
+    cr = synth.protein_database(nq=nq, nt=nt, qmin=qmin, qmax=qmax)
     gen_s = time.perf_counter() - t0
     d = [torch.from_numpy(np.ascontiguousarray(a)).to(dev) for a in (cr.q_codes, cr.q_off, cr.t_codes, cr.t_off)]
     scores = torch.empty((cr.nq, cr.nt), dtype=torch.int32, device=dev)
@@ -403,7 +406,7 @@ def protein_section(ga, dev, stream, nq: int, nt: int, reps: int = 2, check_targ
     exact = bool(torch.equal(ref, got))
     return {
         "metric": "GCUPS", "higher_is_better": True,
-        "workload": f"{cr.nq} protein queries L~U{{100..1000}} x {cr.nt} targets L~LogNormal(ln 300, 0.6) "
+        "workload": f"{cr.nq} protein queries L~U{{{qmin}..{qmax}}} x {cr.nt} targets L~LogNormal(ln 300, 0.6) "
                     "in [10, 5000]; local, BLOSUM62, gap open 11, extend 1",
         "ms": ms, "ms_runs": times, "cells": cells, "gcups": cells / ms / 1e6,
         "dp_ms": st["dp_ms"], "dp_gcups": cells / st["dp_ms"] / 1e6 if st["dp_ms"] > 0 else None,
@@ -671,7 +674,8 @@ def main():
         plan_res = plan_section(ga, dev, stream, b, (q, qo, t, to))
     prot_res = None
     if world == 1 and not args.no_protein:
-        prot_res = protein_section(ga, dev, stream, args.protein_queries, args.protein_targets)
+        prot_res = protein_section(ga, dev, stream, args.protein_queries, args.protein_targets,
+                                   args.protein_qmin, args.protein_qmax)
     serve_res = None
     if world == 1 and not args.no_serve:
         serve_res = serve_section(ga, dev, args.serve_requests)

@@ -58,6 +58,30 @@ cudaMemPool_t pool_for_current_device() {
   return g_pool[dev];
 }
 
+// Side streams per device for the DP launches of one call: the bins of a
+// batch run as concurrent persistent kernels (forked from and joined back to
+// the caller's stream with events), so that one bin's last tasks overlap the
+// next bin's first.  Created on first use, kept until the process ends.
+constexpr int kSideStreams = 4;
+static std::mutex g_side_mu;
+static cudaStream_t g_side[64][kSideStreams] = {};
+
+cudaStream_t *side_streams_for_current_device() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  std::lock_guard<std::mutex> lock(g_side_mu);
+  if (!g_side[dev][0]) {
+    cudaStream_t st[kSideStreams] = {};
+    for (int i = 0; i < kSideStreams; ++i)
+      if (cudaStreamCreateWithFlags(&st[i], cudaStreamNonBlocking) != cudaSuccess) {
+        for (int k = 0; k < i; ++k) cudaStreamDestroy(st[k]);
+        return nullptr;
+      }
+    for (int i = 0; i < kSideStreams; ++i) g_side[dev][i] = st[i];
+  }
+  return g_side[dev];
+}
+
 cudaError_t pool_malloc(void **p, size_t bytes, cudaStream_t s) {
   cudaMemPool_t pool = pool_for_current_device();
   return pool ? cudaMallocFromPoolAsync(p, bytes, pool, s) : cudaMallocAsync(p, bytes, s);
@@ -219,6 +243,19 @@ struct Call {
       cudaEventRecord(e, s);
     }
   }
+  // Concurrent DP launches: one timed region around the fork / join.
+  void count_dp() {
+    ++launches;
+    ++dp_launches;
+  }
+  void dp_mark() {
+    if (!timing) return;
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) == cudaSuccess) {
+      dp_ev.push_back(e);
+      cudaEventRecord(e, s);
+    }
+  }
   float dp_ms() const {
     float tot = 0.f;
     for (size_t i = 0; i + 1 < dp_ev.size(); i += 2) {
@@ -296,6 +333,56 @@ struct SetView {
   uint8_t *bad;
 };
 
+// The DP launches of one call on the device's side streams (two or more
+// launches), or in order on the caller's stream.
+struct DpFork {
+  Call &c;
+  bool on = false;
+  int n = 0;
+  cudaStream_t *side = nullptr;
+  cudaEvent_t fork = nullptr, join[kSideStreams] = {};
+  explicit DpFork(Call &cc) : c(cc) {}
+  int begin(int nlaunch) {
+    if (nlaunch < 2 || !(side = side_streams_for_current_device())) return GA_OK;
+    if (cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) != cudaSuccess) return GA_ERR_CUDA;
+    for (int i = 0; i < kSideStreams; ++i)
+      if (cudaEventCreateWithFlags(&join[i], cudaEventDisableTiming) != cudaSuccess) return GA_ERR_CUDA;
+    c.dp_mark();
+    if (cudaEventRecord(fork, c.s) != cudaSuccess) return GA_ERR_CUDA;
+    for (int i = 0; i < kSideStreams; ++i)
+      if (cudaStreamWaitEvent(side[i], fork, 0) != cudaSuccess) return GA_ERR_CUDA;
+    on = true;
+    return GA_OK;
+  }
+  // Stream of the next launch; brackets it with timing events when in order.
+  cudaStream_t launch_begin() {
+    if (on) {
+      c.count_dp();
+      return side[n++ % kSideStreams];
+    }
+    c.dp_begin();
+    return c.s;
+  }
+  void launch_end() {
+    if (!on) c.dp_end();
+  }
+  int end() {
+    if (!on) return GA_OK;
+    on = false;
+    for (int i = 0; i < kSideStreams; ++i)
+      if (cudaEventRecord(join[i], side[i]) != cudaSuccess || cudaStreamWaitEvent(c.s, join[i], 0) != cudaSuccess)
+        return GA_ERR_CUDA;
+    c.dp_mark();
+    return GA_OK;
+  }
+  ~DpFork() {
+    end();
+    if (fork) cudaEventDestroy(fork);
+    for (cudaEvent_t e : join)
+      if (e) cudaEventDestroy(e);
+  }
+};
+
 // Plan, sort and run one chunk of pairs.  nt == 0: pair p = (q_p, t_p);
 // nt > 0: pair p = (query q0 + p / nt, target p % nt).
 int run_chunk(Call &c, const SetView &Q, const SetView &T, int64_t npairs, int64_t nt, int64_t q0,
@@ -364,9 +451,40 @@ int run_chunk(Call &c, const SetView &Q, const SetView &T, int64_t npairs, int64
   ka.nt = nt;
   ka.q0 = q0;
 
+  // launches of this chunk: the non-empty bins and the long class
+  const int long_key = kClassLong * kBins;
+  const int long_cnt = r.ranges[2 * long_key + 1] - r.ranges[2 * long_key];
+  int nlaunch = long_cnt > 0;
+  for (int cls = 0; cls < 2; ++cls)
+    for (int bin = 0; bin < kKaNumBins; ++bin)
+      nlaunch += r.ranges[2 * (cls * kBins + bin) + 1] > r.ranges[2 * (cls * kBins + bin)];
+  const bool profile = !c.dna;
+  const size_t long_smem = profile ? (size_t)kKbWarps * (size_t)(c.sc.A + 1) * (32 * kKbK) : 0;
+  int long_grid = 0;
+  int64_t long_stride = 0;
+  int2 *long_bnd = nullptr;
+  if (long_cnt > 0) {  // allocated before the fork: the side streams start after it
+    int occ = 0;
+    if (profile)
+      occ = c.mode == GA_LOCAL ? blocks_per_sm_kb_local_prof(long_smem)
+          : c.mode == GA_GLOBAL ? blocks_per_sm_kb_global_prof(long_smem)
+                                : blocks_per_sm_kb_semi_prof(long_smem);
+    else
+      occ = c.mode == GA_LOCAL ? blocks_per_sm_kb_local_sel(long_smem)
+          : c.mode == GA_GLOBAL ? blocks_per_sm_kb_global_sel(long_smem)
+                                : blocks_per_sm_kb_semi_sel(long_smem);
+    const int64_t want = (long_cnt + kKbWarps - 1) / kKbWarps;
+    long_grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)c.nsm * std::max(occ, 1)));
+    long_stride = (int64_t)r.rmax_long + 128;
+    long_bnd = c.al.get<int2>((size_t)long_grid * kKbWarps * (size_t)long_stride);
+    if (c.al.failed) return GA_ERR_OOM;
+  }
+  DpFork fk(c);
+  if (int rc = fk.begin(nlaunch)) return rc;
+
   int counter = 0;
-  for (int cls = 0; cls < 2; ++cls) {
-    for (int bin = 0; bin < kKaNumBins; ++bin) {
+  for (int cls = 1; cls >= 0; --cls) {  // widest tiles first
+    for (int bin = kKaNumBins - 1; bin >= 0; --bin) {
       const int key = cls * kBins + bin;
       const int cnt = r.ranges[2 * key + 1] - r.ranges[2 * key];
       if (cnt <= 0) continue;
@@ -388,43 +506,31 @@ int run_chunk(Call &c, const SetView &Q, const SetView &T, int64_t npairs, int64
       const int64_t want = (ntasks + (kKaThreads / 32) - 1) / (kKaThreads / 32);
       const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)c.nsm * std::max(occ, 1)));
       cudaError_t e;
-      c.dp_begin();
+      const cudaStream_t ls = fk.launch_begin();
       if (cls == 0) {
-        e = c.mode == GA_LOCAL ? launch_ka16_local(bin, ka, grid, c.s)
-          : c.mode == GA_GLOBAL ? launch_ka16_global(bin, ka, grid, c.s)
-                                : launch_ka16_semi(bin, ka, grid, c.s);
+        e = c.mode == GA_LOCAL ? launch_ka16_local(bin, ka, grid, ls)
+          : c.mode == GA_GLOBAL ? launch_ka16_global(bin, ka, grid, ls)
+                                : launch_ka16_semi(bin, ka, grid, ls);
       } else {
-        e = c.mode == GA_LOCAL ? launch_ka32_local(bin, ka, grid, c.s)
-          : c.mode == GA_GLOBAL ? launch_ka32_global(bin, ka, grid, c.s)
-                                : launch_ka32_semi(bin, ka, grid, c.s);
+        e = c.mode == GA_LOCAL ? launch_ka32_local(bin, ka, grid, ls)
+          : c.mode == GA_GLOBAL ? launch_ka32_global(bin, ka, grid, ls)
+                                : launch_ka32_semi(bin, ka, grid, ls);
       }
-      c.dp_end();
+      fk.launch_end();
       if (e != cudaSuccess) return GA_ERR_CUDA;
     }
   }
 
   // Long pairs (and every pair of an alphabet of more than 4 symbols).
   {
-    const int key = kClassLong * kBins;
-    const int cnt = r.ranges[2 * key + 1] - r.ranges[2 * key];
+    const int key = long_key;
+    const int cnt = long_cnt;
     if (cnt > 0) {
       c.pairs32 += cnt;
-      const bool profile = !c.dna;
-      const size_t smem = profile ? (size_t)kKbWarps * (size_t)(c.sc.A + 1) * (32 * kKbK) : 0;
-      int occ = 0;
-      if (profile)
-        occ = c.mode == GA_LOCAL ? blocks_per_sm_kb_local_prof(smem)
-            : c.mode == GA_GLOBAL ? blocks_per_sm_kb_global_prof(smem)
-                                  : blocks_per_sm_kb_semi_prof(smem);
-      else
-        occ = c.mode == GA_LOCAL ? blocks_per_sm_kb_local_sel(smem)
-            : c.mode == GA_GLOBAL ? blocks_per_sm_kb_global_sel(smem)
-                                  : blocks_per_sm_kb_semi_sel(smem);
-      const int64_t want = (cnt + kKbWarps - 1) / kKbWarps;
-      const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)c.nsm * std::max(occ, 1)));
-      const int64_t stride = (int64_t)r.rmax_long + 128;
-      int2 *bnd = c.al.get<int2>((size_t)grid * kKbWarps * (size_t)stride);
-      if (c.al.failed) return GA_ERR_OOM;
+      const size_t smem = long_smem;
+      const int grid = long_grid;
+      const int64_t stride = long_stride;
+      int2 *bnd = long_bnd;
       KBParams kb{};
       kb.packed_q = Q.packed;
       kb.packed_t = T.packed;
@@ -447,19 +553,20 @@ int run_chunk(Call &c, const SetView &Q, const SetView &T, int64_t npairs, int64
       kb.nt = nt;
       kb.q0 = q0;
       cudaError_t e;
-      c.dp_begin();
+      const cudaStream_t ls = fk.launch_begin();
       if (profile)
-        e = c.mode == GA_LOCAL ? launch_kb_local_prof(kb, grid, smem, c.s)
-          : c.mode == GA_GLOBAL ? launch_kb_global_prof(kb, grid, smem, c.s)
-                                : launch_kb_semi_prof(kb, grid, smem, c.s);
+        e = c.mode == GA_LOCAL ? launch_kb_local_prof(kb, grid, smem, ls)
+          : c.mode == GA_GLOBAL ? launch_kb_global_prof(kb, grid, smem, ls)
+                                : launch_kb_semi_prof(kb, grid, smem, ls);
       else
-        e = c.mode == GA_LOCAL ? launch_kb_local_sel(kb, grid, smem, c.s)
-          : c.mode == GA_GLOBAL ? launch_kb_global_sel(kb, grid, smem, c.s)
-                                : launch_kb_semi_sel(kb, grid, smem, c.s);
-      c.dp_end();
+        e = c.mode == GA_LOCAL ? launch_kb_local_sel(kb, grid, smem, ls)
+          : c.mode == GA_GLOBAL ? launch_kb_global_sel(kb, grid, smem, ls)
+                                : launch_kb_semi_sel(kb, grid, smem, ls);
+      fk.launch_end();
       if (e != cudaSuccess) return GA_ERR_CUDA;
     }
   }
+  if (int rc = fk.end()) return rc;
 
   // Exact int32 rerun of local int16 pairs whose running max reached the
   // int16 limit (queued by the int16x2 kernels on the device).
