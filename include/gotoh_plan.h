@@ -60,8 +60,8 @@ extern "C" {
 #endif
 
 /* Tiles of the inter-sequence kernels: 16 lanes x K columns per pair,
- * K = 8, 10, 12, 14, 16, 18, 20, 24, 32 for tile index 0..8. */
-#define GA_TILE_COUNT 9
+ * K = 6, 7, ..., 20, 24, 32 for tile index 0..16. */
+#define GA_TILE_COUNT 17
 
 /* Launch configuration of a plan.  A set bit k of tiles16 makes tile k a
  * bin of the packed int16x2 kernel: a pair goes to the narrowest active

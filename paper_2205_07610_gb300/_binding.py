@@ -36,7 +36,7 @@ EXPORTED = ("ga_align_batch", "ga_align_batch_host", "ga_align_cross", "ga_align
             "ga_server_destroy", "ga_plan_create", "ga_plan_run", "ga_plan_capture",
             "ga_plan_launch", "ga_plan_stats", "ga_plan_autotune", "ga_plan_get_tuning",
             "ga_plan_set_tuning", "ga_plan_destroy")
-TILE_K = (8, 10, 12, 14, 16, 18, 20, 24, 32)  # columns per lane of tile 0..8 (16 lanes per pair)
+TILE_K = (6, 7, 8, 9, 10, 11, 12, 13, 14, 15, 16, 17, 18, 19, 20, 24, 32)  # columns per lane of tile 0..16
 SERVE_MAX_LEN = 65536
 BAND_NFEAT = 32
 MLP_NPARAMS = 6337

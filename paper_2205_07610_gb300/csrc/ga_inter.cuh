@@ -63,6 +63,18 @@ struct KAGroupDesc {
   int tab[2];                  // table word offset: 0 (rows = query) or 8
 };
 
+// Column tiles of the inter-sequence kernel: 16 lanes x K columns per pair
+// (widths 96 .. 320 in steps of 16, then 384 and 512), so a pair's padding
+// to its tile is at most 15 columns up to 320 columns.
+constexpr int kKaNumBins = 17;
+constexpr int kKaK[kKaNumBins] = {6, 7, 8, 9, 10, 11, 12, 13, 14, 15, 16, 17, 18, 19, 20, 24, 32};
+
+__host__ __device__ constexpr int ka_tile_index(int K) {
+  int i = 0;
+  while (i < kKaNumBins - 1 && kKaK[i] < K) ++i;
+  return i;
+}
+
 // Minimum resident blocks per SM requested from ptxas (__launch_bounds__):
 // the highest occupancy at which each (cell type, mode, K) instantiation
 // still compiles without register spills on sm_103a, as printed by
@@ -70,16 +82,16 @@ struct KAGroupDesc {
 // the kernel).
 template <class Cell, int MODE, int K>
 struct KAMinBlocks {
-  // columns per lane:                  8  10  12  14  16  18  20  24  32
-  static constexpr int kKs[9] = {8, 10, 12, 14, 16, 18, 20, 24, 32};
-  static constexpr int kIdx = K <= 8 ? 0 : K <= 10 ? 1 : K <= 12 ? 2 : K <= 14 ? 3 : K <= 16 ? 4
-                            : K <= 18 ? 5 : K <= 20 ? 6 : K <= 24 ? 7 : 8;
-  static constexpr int kPacked[3][9] = {{8, 6, 6, 8, 6, 6, 5, 4, 3},   // local
-                                         {8, 8, 5, 5, 5, 4, 4, 3, 1},   // global
-                                         {8, 8, 5, 4, 4, 3, 3, 1, 1}};  // semi-global
-  static constexpr int kScalar[3][9] = {{8, 8, 8, 8, 6, 6, 5, 4, 3},
-                                         {8, 6, 6, 6, 6, 5, 5, 1, 1},
-                                         {8, 8, 6, 5, 5, 4, 3, 3, 1}};
+  // columns per lane:    6  7  8  9 10 11 12 13 14 15 16 17 18 19 20 24 32
+  static constexpr int kPacked[3][kKaNumBins] = {
+      {8, 8, 8, 6, 6, 6, 6, 6, 8, 6, 6, 5, 6, 5, 5, 4, 3},   // local
+      {8, 8, 8, 8, 8, 6, 5, 5, 5, 5, 5, 5, 4, 4, 4, 3, 1},   // global
+      {8, 6, 8, 6, 8, 5, 5, 4, 4, 4, 4, 4, 3, 3, 3, 1, 1}};  // semi-global
+  static constexpr int kScalar[3][kKaNumBins] = {
+      {8, 8, 8, 8, 8, 6, 8, 8, 8, 6, 6, 6, 6, 6, 5, 4, 3},
+      {8, 8, 8, 6, 6, 8, 6, 8, 6, 5, 6, 5, 5, 5, 5, 1, 1},
+      {8, 8, 8, 8, 8, 6, 6, 6, 5, 6, 5, 4, 4, 4, 3, 3, 1}};
+  static constexpr int kIdx = ka_tile_index(K);
   static constexpr int value = CellInfo<Cell>::kPacked ? kPacked[MODE][kIdx] : kScalar[MODE][kIdx];
 };
 

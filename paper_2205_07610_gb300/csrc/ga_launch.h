@@ -10,11 +10,9 @@
 
 namespace ga {
 
-// Column tile per lane of the inter-sequence bins; a group has 16 lanes, so
-// bin b covers pairs whose shorter sequence has at most 16 * kKaK[b] residues.
+// Lanes per pair of the inter-sequence bins: bin b covers pairs whose
+// shorter sequence has at most 16 * kKaK[b] residues (kKaK in ga_inter.cuh).
 constexpr int kKaG = 16;
-constexpr int kKaNumBins = 9;
-constexpr int kKaK[kKaNumBins] = {8, 10, 12, 14, 16, 18, 20, 24, 32};
 constexpr int kKaThreads = 128;
 
 // Long kernel: 32 lanes x 16 columns per stage.
@@ -52,41 +50,39 @@ struct KCParams;
 cudaError_t launch_kc(const KCParams &p, int grid, cudaStream_t s);
 int blocks_per_sm_kc();
 
-#define GA_KA_OCC(CELL, MODE, K)                                                             \
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, ka_kernel<CELL, MODE, kKaG, K>, kKaThreads, 0)
-
-#define GA_KA_DEFINE(NAME, CELL, MODE)                                                         \
-  cudaError_t launch_##NAME(int bin, const KAParams &p, int grid, cudaStream_t s) {            \
-    switch (bin) {                                                                             \
-      case 0: ka_kernel<CELL, MODE, kKaG, 8><<<grid, kKaThreads, 0, s>>>(p); break;            \
-      case 1: ka_kernel<CELL, MODE, kKaG, 10><<<grid, kKaThreads, 0, s>>>(p); break;           \
-      case 2: ka_kernel<CELL, MODE, kKaG, 12><<<grid, kKaThreads, 0, s>>>(p); break;           \
-      case 3: ka_kernel<CELL, MODE, kKaG, 14><<<grid, kKaThreads, 0, s>>>(p); break;           \
-      case 4: ka_kernel<CELL, MODE, kKaG, 16><<<grid, kKaThreads, 0, s>>>(p); break;           \
-      case 5: ka_kernel<CELL, MODE, kKaG, 18><<<grid, kKaThreads, 0, s>>>(p); break;           \
-      case 6: ka_kernel<CELL, MODE, kKaG, 20><<<grid, kKaThreads, 0, s>>>(p); break;           \
-      case 7: ka_kernel<CELL, MODE, kKaG, 24><<<grid, kKaThreads, 0, s>>>(p); break;           \
-      case 8: ka_kernel<CELL, MODE, kKaG, 32><<<grid, kKaThreads, 0, s>>>(p); break;           \
-      default: return cudaErrorInvalidValue;                                                   \
-    }                                                                                          \
-    return cudaGetLastError();                                                                 \
-  }                                                                                            \
-  int blocks_per_sm_##NAME(int bin) {                                                          \
-    int n = 0;                                                                                 \
-    switch (bin) {                                                                             \
-      case 0: GA_KA_OCC(CELL, MODE, 8); break;                                                 \
-      case 1: GA_KA_OCC(CELL, MODE, 10); break;                                                \
-      case 2: GA_KA_OCC(CELL, MODE, 12); break;                                                \
-      case 3: GA_KA_OCC(CELL, MODE, 14); break;                                                \
-      case 4: GA_KA_OCC(CELL, MODE, 16); break;                                                \
-      case 5: GA_KA_OCC(CELL, MODE, 18); break;                                                \
-      case 6: GA_KA_OCC(CELL, MODE, 20); break;                                                \
-      case 7: GA_KA_OCC(CELL, MODE, 24); break;                                                \
-      case 8: GA_KA_OCC(CELL, MODE, 32); break;                                                \
-      default: break;                                                                          \
-    }                                                                                          \
-    return n;                                                                                  \
+// Launch / occupancy of tile `bin` (compile-time recursion over the tiles).
+template <class CELL, int MODE, int I = 0>
+cudaError_t launch_ka_tile(int bin, const KAParams &p, int grid, cudaStream_t s) {
+  if constexpr (I == kKaNumBins) {
+    return cudaErrorInvalidValue;
+  } else {
+    if (bin == I) {
+      ka_kernel<CELL, MODE, kKaG, kKaK[I]><<<grid, kKaThreads, 0, s>>>(p);
+      return cudaGetLastError();
+    }
+    return launch_ka_tile<CELL, MODE, I + 1>(bin, p, grid, s);
   }
+}
+
+template <class CELL, int MODE, int I = 0>
+int blocks_per_sm_ka_tile(int bin) {
+  if constexpr (I == kKaNumBins) {
+    return 0;
+  } else {
+    if (bin == I) {
+      int n = 0;
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, ka_kernel<CELL, MODE, kKaG, kKaK[I]>, kKaThreads, 0);
+      return n;
+    }
+    return blocks_per_sm_ka_tile<CELL, MODE, I + 1>(bin);
+  }
+}
+
+#define GA_KA_DEFINE(NAME, CELL, MODE)                                                  \
+  cudaError_t launch_##NAME(int bin, const KAParams &p, int grid, cudaStream_t s) {     \
+    return launch_ka_tile<CELL, MODE>(bin, p, grid, s);                                 \
+  }                                                                                     \
+  int blocks_per_sm_##NAME(int bin) { return blocks_per_sm_ka_tile<CELL, MODE>(bin); }
 
 #define GA_KB_DEFINE(NAME, MODE, PROFILE)                                                    \
   cudaError_t launch_##NAME(const KBParams &p, int grid, size_t smem, cudaStream_t s) {     \

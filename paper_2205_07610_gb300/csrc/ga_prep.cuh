@@ -17,7 +17,7 @@
 
 namespace ga {
 
-constexpr int kBins = 12;
+constexpr int kBins = 18;  // >= the inter-sequence tiles (17)
 constexpr int kRBuckets = 2048;  // exact rows below 1536, then 64-row steps
 constexpr int kClassesSorted = 3;  // inter16, inter32, long
 constexpr int kNumKeys = kClassesSorted * kBins * kRBuckets;

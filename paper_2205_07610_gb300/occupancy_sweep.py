@@ -21,7 +21,7 @@ import tempfile
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(HERE, "..", "include")
-KS = [8, 10, 12, 14, 16, 18, 20, 24, 32]
+KS = [6, 7, 8, 9, 10, 11, 12, 13, 14, 15, 16, 17, 18, 19, 20, 24, 32]
 MODES = {"local": "kModeLocal", "global": "kModeGlobal", "semi": "kModeSemi"}
 CELLS = {"packed": "CellS16x2", "scalar": "CellS32"}
 CANDIDATES = (1, 3, 4, 5, 6, 8)
@@ -76,4 +76,4 @@ if __name__ == "__main__":
     t = sweep(ap.parse_args().jobs)
     for c in CELLS:
         rows = ",\n".join("{" + ", ".join(str(v) for v in t[(c, m)]) + "}" for m in MODES)
-        print(f"k{c.capitalize()}[3][9] = {{{rows}}};")
+        print(f"k{c.capitalize()}[3][kKaNumBins] = {{{rows}}};")

@@ -99,4 +99,4 @@ def test_plan_arguments_rejected_before_any_cuda_call(libpath):
                      ("ga_plan_destroy", (None,))):
         assert getattr(lib, fn)(*args) == 1, fn
     assert ctypes.sizeof(ga.Tuning) == 16
-    assert ga.Tuning(0b100000101, 0, 1, 0).as_dict() == {"tiles16": [8, 12, 32], "tiles32": [], "concurrent": 1}
+    assert ga.Tuning((1 << 16) | 0b101, 0, 1, 0).as_dict() == {"tiles16": [6, 8, 32], "tiles32": [], "concurrent": 1}

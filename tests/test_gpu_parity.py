@@ -108,8 +108,10 @@ def test_config2_subset(mode):
 @pytest.mark.parametrize("mode", MODES)
 def test_bin_edges_and_small(mode):
     rng = np.random.default_rng(7)
-    edges = [1, 2, 3, 15, 16, 17, 31, 32, 33, 127, 128, 129, 191, 192, 193, 255, 256, 257, 319,
-             320, 321, 383, 384, 385, 511, 512, 513, 600]
+    # every tile width (16 lanes x K columns: 96 .. 320 in steps of 16, 384,
+    # 512) and its neighbours, short pairs and a pair past the widest tile
+    edges = [1, 2, 3, 15, 16, 17, 31, 32, 33] + [w + d for w in range(96, 321, 16) for d in (-1, 0, 1)] + \
+            [383, 384, 385, 511, 512, 513, 600]
     lq, lt = [], []
     for e in edges:
         for other in (1, e, e + 7, max(1, e - 9), 300):

@@ -111,7 +111,7 @@ def test_plan_graph_replay_reads_new_inputs():
 
     for mode in ("global", "semiglobal", "local"):
         with ga.Plan(mat, 5, 2, mode, n, cap, 400) as plan:
-            plan.tuning = ga.Tuning(0x1ff, 0x1ff, 1, 0)
+            plan.tuning = ga.Tuning((1 << 17) - 1, (1 << 17) - 1, 1, 0)
             load(batches[0])
             torch.cuda.synchronize()
             plan.capture(q, qo, t, to, scores)
