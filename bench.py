@@ -44,9 +44,10 @@ import synth  # noqa: E402
 # affine alignment (Sec. 4.2: 4 max + 3 add/sub); local adds 2.
 OPS_PER_CELL = 7
 # DRAM bytes (read + write) of one launch of the dominant DP kernel,
-# ka_kernel<CellS16x2, semi, 16, 18>, on this batch: one ncu capture
-# (dram__bytes_read.sum + dram__bytes_write.sum) of the current kernel code.
-KA_TRAFFIC_BYTES = 79.596032e6 + 2.576640e6
+# ka_kernel<CellS16x2, semi, 16, 18> (pairs of 273..288 columns), on this
+# batch: one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) of
+# the current kernel code and bins.
+KA_TRAFFIC_BYTES = 48453888 + 10496
 PEAK_SM_MHZ = 2070.0     # maximum SM clock of a GB300
 N_SM = 152
 LANES_PER_SM = 128       # 4 SM sub-partitions x 32 lanes, one integer op each per clock
