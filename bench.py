@@ -48,10 +48,29 @@ OPS_PER_CELL = 7
 # batch: one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) of
 # the current kernel code and bins.
 KA_TRAFFIC_BYTES = 48453888 + 10496
-PEAK_SM_MHZ = 2070.0     # maximum SM clock of a GB300
-N_SM = 152
 LANES_PER_SM = 128       # 4 SM sub-partitions x 32 lanes, one integer op each per clock
 SIMD = 2                 # int16x2: two cells per lane-op
+FALLBACK_SM_MHZ = 2070.0  # GB300 maximum SM clock, used only if no measured value is available
+
+
+def device_peak(dev, clocks=None):
+    """(SM count, maximum SM clock in MHz, source) of the device: the SM count
+    from the device properties, the clock from the nvidia-smi samples of the
+    run, else MEASURED_PEAKS.json, else the GB300 figure."""
+    import torch
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    mhz, src = None, None
+    if clocks and clocks.get("sm_max_mhz"):
+        mhz, src = float(clocks["sm_max_mhz"]), "nvidia-smi clocks.max.sm"
+    if mhz is None:
+        try:
+            with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+                mhz, src = float(json.load(f)["sm_max_mhz"]), "MEASURED_PEAKS.json sm_max_mhz"
+        except (OSError, KeyError, ValueError):
+            pass
+    if mhz is None:
+        mhz, src = FALLBACK_SM_MHZ, "GB300 nominal maximum"
+    return n_sm, mhz, src
 
 
 def parse_args():
@@ -355,7 +374,7 @@ def serve_section(ga, dev, nreq: int, load: float = 0.7, burst: int = 50_000):
 
 
 def protein_section(ga, dev, stream, nq: int, nt: int, qmin: int = 100, qmax: int = 1000, reps: int = 2,
-                    check_targets: int = 512):
+                    check_targets: int = 512, peak_ops: float = 0.0):
     """Protein database search: every query against every target, local mode.
 
     512 queries |Q| ~ U{100..1000} against 200k targets |T| ~ LogNormal(ln 300,
@@ -415,7 +434,8 @@ def protein_section(ga, dev, stream, nq: int, nt: int, qmin: int = 100, qmax: in
         "exact_vs_int32_sample": exact, "checked_pairs": int(len(qi)), "gen_s": gen_s,
         "roofline": {"bound": "alu", "ops_per_cell": 9,
                      "achieved": cells * 9 / (st["dp_ms"] / 1e3) / 1e12 if st["dp_ms"] > 0 else None,
-                     "peak": N_SM * LANES_PER_SM * SIMD * PEAK_SM_MHZ * 1e6 / 1e12,
+                     "peak": peak_ops / 1e12,
+                     "frac": cells * 9 / (st["dp_ms"] / 1e3) / peak_ops if st["dp_ms"] > 0 and peak_ops else None,
                      "unit": "Tops/s (int16, 9 ops per local cell)",
                      "kernel": "kp_kernel (packed int16x2 query-profile kernel)"},
     }
@@ -618,8 +638,9 @@ def main():
     int16_pairs = sum(s["pairs_int16"] for pair in sts for s in pair)
 
     # ---- roofline of the dominant kernel (packed int16x2 inter-sequence DP)
-    sm_mhz = clocks.get("sm_mhz") or PEAK_SM_MHZ
-    peak_ops = N_SM * LANES_PER_SM * SIMD * PEAK_SM_MHZ * 1e6           # int16 ops / s
+    n_sm, peak_mhz, peak_src = device_peak(dev, clocks)
+    sm_mhz = clocks.get("sm_mhz") or peak_mhz
+    peak_ops = n_sm * LANES_PER_SM * SIMD * peak_mhz * 1e6           # int16 ops / s
     alg_ops = step_cells * args.steps * OPS_PER_CELL
     achieved_ops = alg_ops / (dp_ms / 1e3) if dp_ms > 0 else 0.0
     roofline = {
@@ -632,7 +653,7 @@ def main():
         "dp_gcups": step_cells * args.steps / (dp_ms / 1e3) / 1e9 if dp_ms > 0 else None,
         "dp_launches_per_step": dp_launches / args.steps,
         "peak_gcups_at_7_ops": peak_ops / OPS_PER_CELL / 1e9,
-        "peak_basis": f"{N_SM} SM x {LANES_PER_SM} lanes x {SIMD} (int16x2) x {PEAK_SM_MHZ:.0f} MHz",
+        "peak_basis": f"{n_sm} SM x {LANES_PER_SM} lanes x {SIMD} (int16x2) x {peak_mhz:.0f} MHz ({peak_src})",
         "sm_mhz_measured": sm_mhz,
     }
 
@@ -676,7 +697,7 @@ def main():
     prot_res = None
     if world == 1 and not args.no_protein:
         prot_res = protein_section(ga, dev, stream, args.protein_queries, args.protein_targets,
-                                   args.protein_qmin, args.protein_qmax)
+                                   args.protein_qmin, args.protein_qmax, peak_ops=peak_ops)
     serve_res = None
     if world == 1 and not args.no_serve:
         serve_res = serve_section(ga, dev, args.serve_requests)

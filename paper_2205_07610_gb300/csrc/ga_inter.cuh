@@ -77,16 +77,19 @@ __host__ __device__ constexpr int ka_tile_index(int K) {
 
 // Minimum resident blocks per SM requested from ptxas (__launch_bounds__):
 // the highest occupancy at which each (cell type, mode, K) instantiation
-// still compiles without register spills on sm_103a, as printed by
-// `python -m paper_2205_07610_gb300.occupancy_sweep` (rerun after changing
-// the kernel).
+// compiles on sm_103a without register spills (local mode and the int32
+// cells) or with at most 16 bytes of spill stores (packed global and
+// semi-global: the extra resident block measured faster on GB300, local
+// measured slower), as printed by
+// `python -m paper_2205_07610_gb300.occupancy_sweep [--max-spill 16]`
+// (rerun after changing the kernel).
 template <class Cell, int MODE, int K>
 struct KAMinBlocks {
   // columns per lane:    6  7  8  9 10 11 12 13 14 15 16 17 18 19 20 24 32
   static constexpr int kPacked[3][kKaNumBins] = {
-      {8, 8, 8, 6, 6, 6, 6, 6, 8, 6, 6, 5, 6, 5, 5, 4, 3},   // local
-      {8, 8, 8, 8, 8, 6, 5, 5, 5, 5, 5, 5, 4, 4, 4, 3, 1},   // global
-      {8, 6, 8, 6, 8, 5, 5, 4, 4, 4, 4, 4, 3, 3, 3, 1, 1}};  // semi-global
+      {8, 8, 8, 6, 6, 6, 6, 6, 8, 6, 6, 5, 6, 5, 5, 4, 3},   // local (no spills)
+      {8, 8, 8, 8, 8, 6, 6, 5, 5, 5, 5, 6, 5, 4, 4, 3, 1},   // global (<= 16 bytes)
+      {8, 8, 8, 6, 8, 6, 6, 5, 6, 5, 5, 4, 4, 4, 4, 3, 3}};  // semi-global (<= 16 bytes)
   static constexpr int kScalar[3][kKaNumBins] = {
       {8, 8, 8, 8, 8, 6, 8, 8, 8, 6, 6, 6, 6, 6, 5, 4, 3},
       {8, 8, 8, 6, 6, 8, 6, 8, 6, 5, 6, 5, 5, 5, 5, 1, 1},

@@ -1,12 +1,15 @@
-"""Spill-free occupancy table of the inter-sequence kernel (maintenance tool).
+"""Occupancy table of the inter-sequence kernel (maintenance tool).
 
-    python -m paper_2205_07610_gb300.occupancy_sweep [--jobs N]
+    python -m paper_2205_07610_gb300.occupancy_sweep [--jobs N] [--max-spill BYTES]
 
 Compiles every (cell type, mode, K) instantiation of ka_kernel for sm_103a at
 each candidate __launch_bounds__ minimum-blocks value and prints, per
-instantiation, the largest value at which ptxas allocates registers without
-spilling, as the C++ initialisers of KAMinBlocks in csrc/ga_inter.cuh.  Run it
-after changing the kernel; a CPU test checks that the library has no spills.
+instantiation, the largest value at which ptxas allocates registers with at
+most --max-spill bytes of spill stores (default 0), as the C++ initialisers of
+KAMinBlocks in csrc/ga_inter.cuh.  The library takes the packed global and
+semi-global rows from --max-spill 16 and every other row from the default
+(which limit pays off was measured on GB300).  Run it after changing the
+kernel; a CPU test checks the spill limits of the built library.
 """
 from __future__ import annotations
 
@@ -54,7 +57,7 @@ def _compile(args):
         shutil.rmtree(d, ignore_errors=True)
 
 
-def sweep(jobs: int = 8) -> dict:
+def sweep(jobs: int = 8, max_spill: int = 0) -> dict:
     nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
     work = [(c, m, k, mb, nvcc) for c in CELLS for m in MODES for k in KS for mb in CANDIDATES]
     res = {}
@@ -65,7 +68,7 @@ def sweep(jobs: int = 8) -> dict:
     for c in CELLS:
         for m in MODES:
             table[(c, m)] = [max([mb for mb in CANDIDATES
-                                  if res[(c, m, k, mb)] and res[(c, m, k, mb)][1] == 0] or [1])
+                                  if res[(c, m, k, mb)] and res[(c, m, k, mb)][1] <= max_spill] or [1])
                              for k in KS]
     return table
 
@@ -73,7 +76,9 @@ def sweep(jobs: int = 8) -> dict:
 if __name__ == "__main__":
     ap = argparse.ArgumentParser()
     ap.add_argument("--jobs", type=int, default=os.cpu_count() or 8)
-    t = sweep(ap.parse_args().jobs)
+    ap.add_argument("--max-spill", type=int, default=0, help="bytes of spill stores allowed")
+    a = ap.parse_args()
+    t = sweep(a.jobs, a.max_spill)
     for c in CELLS:
         rows = ",\n".join("{" + ", ".join(str(v) for v in t[(c, m)]) + "}" for m in MODES)
         print(f"k{c.capitalize()}[3][kKaNumBins] = {{{rows}}};")
