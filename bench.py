@@ -47,7 +47,7 @@ OPS_PER_CELL = 7
 # ka_kernel<CellS16x2, semi, 16, 18> (pairs of 273..288 columns), on this
 # batch: one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) of
 # the current kernel code and bins.
-KA_TRAFFIC_BYTES = 48453888 + 10496
+KA_TRAFFIC_BYTES = 48514304 + 5376
 LANES_PER_SM = 128       # 4 SM sub-partitions x 32 lanes, one integer op each per clock
 SIMD = 2                 # int16x2: two cells per lane-op
 FALLBACK_SM_MHZ = 2070.0  # GB300 maximum SM clock, used only if no measured value is available
