@@ -37,8 +37,14 @@
  * Execution: work is enqueued asynchronously on `stream` (a cudaStream_t;
  * NULL = legacy default stream).  Scores are valid once the stream has
  * been synchronised.  If `stats` is non-NULL the call synchronises the
- * stream before returning and fills it.  Calls on different streams may
- * run concurrently; the library keeps no mutable global state.
+ * stream before returning and fills it.  The batch and cross entry points
+ * read the bin populations back once per call (a short synchronisation of
+ * `stream` between planning and the DP kernels) and run the bins as
+ * concurrent kernels on four side streams of the library (created once per
+ * device, forked from and joined back to `stream` with events).  Calls from
+ * different host threads on different streams are safe; their DP kernels
+ * may queue behind each other on the shared side streams.  Apart from those
+ * streams and the device memory pool the library keeps no global state.
  *
  * Errors returned synchronously (nothing has been enqueued):
  *   GA_ERR_ARG       null pointer where data is required, gap_open <= 0,
