@@ -147,6 +147,24 @@ int ga_align_batch_host(const uint8_t *q_codes, const int64_t *q_off, const uint
                         int32_t mode, int32_t *scores, void *stream, ga_stats *stats);
 
 /*
+ * ga_align_batch_host_modes -- ga_align_batch_host for several modes of the
+ * same pairs: the inputs are copied in once (chunk by chunk, as above) and
+ * every mode in modes[0 .. nmodes) runs on each chunk, so scoring a batch
+ * under, e.g., global and semi-global moves its residues over the host link
+ * once instead of once per mode.
+ *   modes  : host, int32[nmodes], each GA_LOCAL / GA_GLOBAL / GA_SEMIGLOBAL
+ *            (repetitions allowed), 1 <= nmodes <= 8
+ *   scores : host, int32[nmodes * npairs]; scores[k * npairs + p] is pair p
+ *            in mode modes[k]
+ * Errors as for ga_align_batch_host (GA_ERR_ARG for a bad nmodes or mode);
+ * stats (nullable) sums all modes and chunks.
+ */
+int ga_align_batch_host_modes(const uint8_t *q_codes, const int64_t *q_off, const uint8_t *t_codes,
+                              const int64_t *t_off, int64_t npairs, const ga_scoring *scoring,
+                              const int32_t *modes, int32_t nmodes, int32_t *scores, void *stream,
+                              ga_stats *stats);
+
+/*
  * ga_align_cross -- database search: every query k = 0..nq-1 against
  * every target l = 0..nt-1; scores[k*nt + l] (row-major, device,
  * int32[nq*nt]).  Offsets as in ga_align_batch.  The query's scoring

@@ -27,7 +27,7 @@ GA_ERR_TIMEOUT = 6
 GA_ERR_RANGE = 7
 
 # Symbols declared in include/gotoh_align.h (checked by the CPU tests).
-EXPORTED = ("ga_align_batch", "ga_align_batch_host", "ga_align_cross", "ga_align_long",
+EXPORTED = ("ga_align_batch", "ga_align_batch_host", "ga_align_batch_host_modes", "ga_align_cross", "ga_align_long",
             "ga_align_long_noalloc", "ga_align_banded", "ga_strerror", "ga_version",
             "ga_probe_issue_rate", "ga_band_features", "ga_band_min_w", "ga_band_predict",
             "ga_mlp_forward", "ga_mlp_loss_grad", "ga_mlp_train", "ga_mlp_cast",
@@ -126,6 +126,7 @@ def load(build_if_missing: bool = False):
     stp = ctypes.POINTER(Stats)
     lib.ga_align_batch.argtypes = [P, P, P, P, i64, sp, i32, P, P, stp]
     lib.ga_align_batch_host.argtypes = [P, P, P, P, i64, sp, i32, P, P, stp]
+    lib.ga_align_batch_host_modes.argtypes = [P, P, P, P, i64, sp, P, i32, P, P, stp]
     lib.ga_align_cross.argtypes = [P, P, i64, P, P, i64, sp, i32, P, P, stp]
     lib.ga_align_long.argtypes = [P, i64, P, i64, sp, i32, P, P, stp]
     lib.ga_align_banded.argtypes = [P, P, P, P, i64, sp, P, i32, P, P, P, stp]
@@ -161,7 +162,8 @@ def load(build_if_missing: bool = False):
     lib.ga_plan_get_tuning.argtypes = [P, tp]
     lib.ga_plan_set_tuning.argtypes = [P, tp]
     lib.ga_plan_destroy.argtypes = [P]
-    for f in ("ga_align_batch", "ga_align_batch_host", "ga_align_cross", "ga_align_long",
+    for f in ("ga_align_batch", "ga_align_batch_host", "ga_align_batch_host_modes", "ga_align_cross",
+              "ga_align_long",
               "ga_align_long_noalloc", "ga_align_banded", "ga_band_features", "ga_band_min_w",
               "ga_band_predict", "ga_mlp_forward", "ga_mlp_loss_grad", "ga_mlp_train",
               "ga_mlp_cast", "ga_plan_create", "ga_plan_run", "ga_plan_capture", "ga_plan_launch",
@@ -274,6 +276,33 @@ def align_batch_host(q_codes, q_off, t_codes, t_off, matrix, gap_open, gap_exten
                                     _stream_ptr(stream), ctypes.byref(st) if stats else None)
     if rc:
         raise GotohError(rc, "ga_align_batch_host")
+    return (scores, st.as_dict()) if stats else scores
+
+
+def align_batch_host_modes(q_codes, q_off, t_codes, t_off, matrix, gap_open, gap_extend, modes,
+                           scores=None, stream=None, stats: bool = False):
+    """ga_align_batch_host_modes: host arrays in, host scores [len(modes), npairs] out; the
+    inputs cross the host link once for all modes."""
+    def host_ptr(a, dtype):
+        if hasattr(a, "data_ptr"):
+            return a, int(a.data_ptr())
+        a = np.ascontiguousarray(a, dtype=dtype)
+        return a, a.ctypes.data
+    q_codes, qc = host_ptr(q_codes, np.uint8)
+    q_off, qo = host_ptr(q_off, np.int64)
+    t_codes, tc = host_ptr(t_codes, np.uint8)
+    t_off, to = host_ptr(t_off, np.int64)
+    npairs = (q_off.numel() if hasattr(q_off, "numel") else len(q_off)) - 1
+    md = np.ascontiguousarray([_mode(m) for m in modes], dtype=np.int32)
+    if scores is None:
+        scores = np.empty((len(md), max(npairs, 0)), dtype=np.int32)
+    scores, sp = host_ptr(scores, np.int32)
+    sc, keep = make_scoring(matrix, gap_open, gap_extend)
+    st = Stats()
+    rc = load().ga_align_batch_host_modes(qc, qo, tc, to, npairs, ctypes.byref(sc), md.ctypes.data, len(md), sp,
+                                          _stream_ptr(stream), ctypes.byref(st) if stats else None)
+    if rc:
+        raise GotohError(rc, "ga_align_batch_host_modes")
     return (scores, st.as_dict()) if stats else scores
 
 

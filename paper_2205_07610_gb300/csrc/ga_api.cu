@@ -1498,12 +1498,15 @@ int ga_align_batch(const uint8_t *q_codes, const int64_t *q_off, const uint8_t *
   return batch_impl(q_codes, q_off, t_codes, t_off, npairs, scoring, mode, scores, stream, stats, 0);
 }
 
-int ga_align_batch_host(const uint8_t *q_codes, const int64_t *q_off, const uint8_t *t_codes,
-                        const int64_t *t_off, int64_t npairs, const ga_scoring *scoring,
-                        int32_t mode, int32_t *scores, void *stream, ga_stats *stats) {
-  if (npairs < 0) return GA_ERR_ARG;
+static int batch_host_impl(const uint8_t *q_codes, const int64_t *q_off, const uint8_t *t_codes,
+                           const int64_t *t_off, int64_t npairs, const ga_scoring *scoring,
+                           const int32_t *modes, int32_t nmodes, int32_t *scores, void *stream,
+                           ga_stats *stats) {
+  if (npairs < 0 || !modes || nmodes < 1 || nmodes > 8) return GA_ERR_ARG;
+  for (int k = 0; k < nmodes; ++k)
+    if (modes[k] < 0 || modes[k] > 2) return GA_ERR_ARG;
   if (npairs > 0 && (!q_codes || !q_off || !t_codes || !t_off || !scores)) return GA_ERR_ARG;
-  if (npairs == 0) return batch_impl(nullptr, nullptr, nullptr, nullptr, 0, scoring, mode, nullptr, stream,
+  if (npairs == 0) return batch_impl(nullptr, nullptr, nullptr, nullptr, 0, scoring, modes[0], nullptr, stream,
                                      stats, 0);
   cudaStream_t s = (cudaStream_t)stream;
   const int64_t qn = q_off[npairs], tn = t_off[npairs];
@@ -1539,7 +1542,7 @@ int ga_align_batch_host(const uint8_t *q_codes, const int64_t *q_off, const uint
               pool_malloc((void **)&dt, (size_t)tn + 16, s) != cudaSuccess ||
               pool_malloc((void **)&dqo, sizeof(int64_t) * (size_t)(npairs + 1), s) != cudaSuccess ||
               pool_malloc((void **)&dto, sizeof(int64_t) * (size_t)(npairs + 1), s) != cudaSuccess ||
-              pool_malloc((void **)&ds, sizeof(int32_t) * (size_t)(npairs + 1), s) != cudaSuccess))
+              pool_malloc((void **)&ds, sizeof(int32_t) * (size_t)(nmodes * npairs + 1), s) != cudaSuccess))
     rc = GA_ERR_OOM;
   cudaEvent_t ready = nullptr;  // the allocations above are ordered on `s`
   if (!rc && (cudaEventCreateWithFlags(&ready, cudaEventDisableTiming) != cudaSuccess ||
@@ -1573,25 +1576,30 @@ int ga_align_batch_host(const uint8_t *q_codes, const int64_t *q_off, const uint
       rc = GA_ERR_CUDA;
       break;
     }
-    ga_stats st{};
     KnownRange qr, tr;
     qr.known = tr.known = true;
     qr.start = q_off[a];
     qr.total = q_off[b];
     tr.start = t_off[a];
     tr.total = t_off[b];
-    rc = batch_impl(dq, dqo + a, dt, dto + a, b - a, scoring, mode, ds + a, stream, stats ? &st : nullptr, 0,
-                    qr, tr);
-    if (rc) break;
-    if (stats) {
-      tot.cells += st.cells; tot.pairs += st.pairs; tot.pairs_int16 += st.pairs_int16;
-      tot.pairs_int32 += st.pairs_int32; tot.pairs_int32_rerun += st.pairs_int32_rerun;
-      tot.dp_ms += st.dp_ms; tot.dp_launches += st.dp_launches; tot.launches += st.launches;
-      if (!tot.status) tot.status = st.status;
+    for (int md = 0; !rc && md < nmodes; ++md) {  // every mode on the chunk copied once
+      ga_stats st{};
+      rc = batch_impl(dq, dqo + a, dt, dto + a, b - a, scoring, modes[md], ds + (size_t)md * npairs + a, stream,
+                      stats ? &st : nullptr, 0, qr, tr);
+      if (!rc && stats) {
+        tot.cells += st.cells; tot.pairs += st.pairs; tot.pairs_int16 += st.pairs_int16;
+        tot.pairs_int32 += st.pairs_int32; tot.pairs_int32_rerun += st.pairs_int32_rerun;
+        tot.dp_ms += st.dp_ms; tot.dp_launches += st.dp_launches; tot.launches += st.launches;
+        if (!tot.status) tot.status = st.status;
+      }
     }
-    if (cudaEventRecord(ev_done[k], s) != cudaSuccess || cudaStreamWaitEvent(cs, ev_done[k], 0) != cudaSuccess ||
-        cudaMemcpyAsync(scores + a, ds + a, sizeof(int32_t) * (size_t)(b - a), cudaMemcpyDeviceToHost, cs) != cudaSuccess)
+    if (rc) break;
+    if (cudaEventRecord(ev_done[k], s) != cudaSuccess || cudaStreamWaitEvent(cs, ev_done[k], 0) != cudaSuccess)
       rc = GA_ERR_CUDA;
+    for (int md = 0; !rc && md < nmodes; ++md)
+      if (cudaMemcpyAsync(scores + (size_t)md * npairs + a, ds + (size_t)md * npairs + a,
+                          sizeof(int32_t) * (size_t)(b - a), cudaMemcpyDeviceToHost, cs) != cudaSuccess)
+        rc = GA_ERR_CUDA;
   }
   // the frees are ordered after the last score copy
   cudaEvent_t copied = nullptr;
@@ -1617,6 +1625,19 @@ int ga_align_batch_host(const uint8_t *q_codes, const int64_t *q_off, const uint
   if (e1) cudaEventDestroy(e1);
   if (cs) cudaStreamDestroy(cs);
   return rc;
+}
+
+int ga_align_batch_host(const uint8_t *q_codes, const int64_t *q_off, const uint8_t *t_codes,
+                        const int64_t *t_off, int64_t npairs, const ga_scoring *scoring,
+                        int32_t mode, int32_t *scores, void *stream, ga_stats *stats) {
+  return batch_host_impl(q_codes, q_off, t_codes, t_off, npairs, scoring, &mode, 1, scores, stream, stats);
+}
+
+int ga_align_batch_host_modes(const uint8_t *q_codes, const int64_t *q_off, const uint8_t *t_codes,
+                              const int64_t *t_off, int64_t npairs, const ga_scoring *scoring,
+                              const int32_t *modes, int32_t nmodes, int32_t *scores, void *stream,
+                              ga_stats *stats) {
+  return batch_host_impl(q_codes, q_off, t_codes, t_off, npairs, scoring, modes, nmodes, scores, stream, stats);
 }
 
 int ga_align_cross(const uint8_t *q_codes, const int64_t *q_off, int64_t nq, const uint8_t *t_codes,

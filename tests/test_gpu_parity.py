@@ -250,6 +250,28 @@ def test_host_entry_point_in_chunks():
     assert_same(host[sub], want, "host chunks vs oracle")
 
 
+def test_host_modes_entry_point():
+    # several modes of the same pairs from one host copy, over several copy
+    # chunks; every row equals the device entry point in its mode, and the
+    # global row a sample of the oracle
+    rng = np.random.default_rng(6)
+    n = 600_000
+    qc, qo = synth.random_sequences(rng, rng.integers(0, 60, size=n))
+    tc, to = synth.random_sequences(rng, rng.integers(0, 60, size=n))
+    b = synth.Batch(qc, qo, tc, to, synth.dna_matrix(2, -3), 5, 2, "modes")
+    modes = ["global", "semiglobal", "local", "global"]
+    host, st = ga.align_batch_host_modes(qc, qo, tc, to, b.matrix, 5, 2, modes, stats=True)
+    assert host.shape == (4, n) and st["status"] == 0 and st["pairs"] == 4 * n
+    for k, mode in enumerate(modes):
+        assert_same(host[k], gpu_batch(b, mode), f"host modes row {k} {mode}")
+    sub = rng.choice(n, size=300, replace=False)
+    want, _ = oracle.batch(*_subset(b, sub), b.matrix, 5, 2, "local", nthreads=NTHREADS)
+    assert_same(host[2][sub], want, "host modes local vs oracle")
+    with pytest.raises(ga.GotohError) as e:
+        ga.align_batch_host_modes(qc[:10], qo[:3], tc[:10], to[:3], b.matrix, 5, 2, [0, 3])
+    assert e.value.code == 1
+
+
 def _subset(b, idx):
     qs = [b.q_codes[b.q_off[i]:b.q_off[i + 1]] for i in idx]
     ts = [b.t_codes[b.t_off[i]:b.t_off[i + 1]] for i in idx]
