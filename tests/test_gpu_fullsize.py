@@ -1,7 +1,8 @@
 """GPU parity at the full benchmark sizes, in the launch configuration the
-bench times: the whole workload runs on the GPU in one call, and a sample of
-its outputs (the longest pairs / targets included) is compared with the CPU
-oracle, which computes them one by one.  Properties that hold at any size
+bench times: the whole workload runs on the GPU in one call (the serving
+stream in one submission), and a sample of its outputs (the longest pairs,
+targets and requests included) is compared with the CPU oracle, which
+computes them one by one.  Properties that hold at any size
 (banded scores equal full-DP scores) are checked on every pair.
 """
 import os
@@ -93,3 +94,36 @@ def test_config4_full_dp_and_band_sampled():
                               "global", nthreads=NTHREADS)
     assert not errs.any()
     np.testing.assert_array_equal(full.cpu().numpy()[idx].astype(np.int64), want)
+
+
+def test_config5_full_serving_stream_sampled():
+    # the whole 200k-request serving stream submitted to the server at once
+    # (mixed DNA / protein, local / global, lengths up to 50k); a sample of
+    # the results, the 3 largest requests included, equals the oracle
+    s = synth.serving_stream()
+    cells = np.diff(s.q_off) * np.diff(s.t_off)
+    with ga.Server(arena_bytes=32 << 30, max_inflight=65536, max_tasks=1 << 22) as srv:
+        d = srv.add_scoring(*s.dna_scoring)
+        p = srv.add_scoring(*s.protein_scoring)
+        sid = np.where(s.protein, p, d).astype(np.int32)
+        first = srv.submit(s.q_codes, s.q_off, s.t_codes, s.t_off, s.mode, sid)
+        srv.drain(600_000)
+        res = srv.poll(s.nreq + 16)
+    assert len(res) == s.nreq
+    res = res[np.argsort(res["id"])]
+    assert np.array_equal(res["id"], first + np.arange(s.nreq))
+    assert np.all(res["status"] == 0)
+    assert np.array_equal(res["cells"], cells)
+    idx = _sample(np.random.default_rng(5), cells, 120, 3)
+    for prot in (False, True):  # the oracle on the sample, by scoring and mode
+        for md in (0, 1):
+            sel = idx[(s.protein[idx] == prot) & (s.mode[idx] == md)]
+            if not len(sel):
+                continue
+            mat, al, be = s.protein_scoring if prot else s.dna_scoring
+            qc, qo = synth.pack_csr([s.q_codes[s.q_off[i]:s.q_off[i + 1]] for i in sel])
+            tc, to = synth.pack_csr([s.t_codes[s.t_off[i]:s.t_off[i + 1]] for i in sel])
+            want, errs = oracle.batch(qc, qo, tc, to, mat, al, be, "global" if md else "local",
+                                      nthreads=NTHREADS)
+            assert not errs.any()
+            np.testing.assert_array_equal(res["score"][sel].astype(np.int64), want)
