@@ -132,6 +132,23 @@ int ga_align_batch(const uint8_t *q_codes, const int64_t *q_off, const uint8_t *
                    int32_t mode, int32_t *scores, void *stream, ga_stats *stats);
 
 /*
+ * ga_align_batch_modes -- ga_align_batch for several modes of the same
+ * pairs in one call: both sequence sets are validated and packed once, then
+ * each mode in modes[0 .. nmodes) is planned and aligned on the packed
+ * copies.
+ *   modes  : HOST int32[nmodes], each GA_LOCAL / GA_GLOBAL / GA_SEMIGLOBAL
+ *            (repetitions allowed), 1 <= nmodes <= 8
+ *   scores : device int32[nmodes * npairs]; scores[k * npairs + p] is pair p
+ *            in mode modes[k]
+ * Other arguments and errors as for ga_align_batch (GA_ERR_ARG for a bad
+ * nmodes or mode); stats (nullable) sums the modes.
+ */
+int ga_align_batch_modes(const uint8_t *q_codes, const int64_t *q_off, const uint8_t *t_codes,
+                         const int64_t *t_off, int64_t npairs, const ga_scoring *scoring,
+                         const int32_t *modes, int32_t nmodes, int32_t *scores, void *stream,
+                         ga_stats *stats);
+
+/*
  * ga_align_batch_host -- ga_align_batch with every array in HOST memory
  * (pinned memory gives the fastest copies).  The pairs are cut into up to 8
  * chunks of geometrically growing size (one chunk per 2^18 pairs, the
@@ -149,9 +166,10 @@ int ga_align_batch_host(const uint8_t *q_codes, const int64_t *q_off, const uint
 /*
  * ga_align_batch_host_modes -- ga_align_batch_host for several modes of the
  * same pairs: the inputs are copied in once (chunk by chunk, as above) and
- * every mode in modes[0 .. nmodes) runs on each chunk, so scoring a batch
- * under, e.g., global and semi-global moves its residues over the host link
- * once instead of once per mode.
+ * every mode in modes[0 .. nmodes) runs on each chunk (packed once, as in
+ * ga_align_batch_modes), so scoring a batch under, e.g., global and
+ * semi-global moves its residues over the host link once instead of once
+ * per mode.
  *   modes  : host, int32[nmodes], each GA_LOCAL / GA_GLOBAL / GA_SEMIGLOBAL
  *            (repetitions allowed), 1 <= nmodes <= 8
  *   scores : host, int32[nmodes * npairs]; scores[k * npairs + p] is pair p

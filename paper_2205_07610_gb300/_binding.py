@@ -27,7 +27,8 @@ GA_ERR_TIMEOUT = 6
 GA_ERR_RANGE = 7
 
 # Symbols declared in include/gotoh_align.h (checked by the CPU tests).
-EXPORTED = ("ga_align_batch", "ga_align_batch_host", "ga_align_batch_host_modes", "ga_align_cross", "ga_align_long",
+EXPORTED = ("ga_align_batch", "ga_align_batch_modes", "ga_align_batch_host", "ga_align_batch_host_modes",
+            "ga_align_cross", "ga_align_long",
             "ga_align_long_noalloc", "ga_align_banded", "ga_strerror", "ga_version",
             "ga_probe_issue_rate", "ga_band_features", "ga_band_min_w", "ga_band_predict",
             "ga_mlp_forward", "ga_mlp_loss_grad", "ga_mlp_train", "ga_mlp_cast",
@@ -127,6 +128,7 @@ def load(build_if_missing: bool = False):
     lib.ga_align_batch.argtypes = [P, P, P, P, i64, sp, i32, P, P, stp]
     lib.ga_align_batch_host.argtypes = [P, P, P, P, i64, sp, i32, P, P, stp]
     lib.ga_align_batch_host_modes.argtypes = [P, P, P, P, i64, sp, P, i32, P, P, stp]
+    lib.ga_align_batch_modes.argtypes = [P, P, P, P, i64, sp, P, i32, P, P, stp]
     lib.ga_align_cross.argtypes = [P, P, i64, P, P, i64, sp, i32, P, P, stp]
     lib.ga_align_long.argtypes = [P, i64, P, i64, sp, i32, P, P, stp]
     lib.ga_align_banded.argtypes = [P, P, P, P, i64, sp, P, i32, P, P, P, stp]
@@ -162,7 +164,8 @@ def load(build_if_missing: bool = False):
     lib.ga_plan_get_tuning.argtypes = [P, tp]
     lib.ga_plan_set_tuning.argtypes = [P, tp]
     lib.ga_plan_destroy.argtypes = [P]
-    for f in ("ga_align_batch", "ga_align_batch_host", "ga_align_batch_host_modes", "ga_align_cross",
+    for f in ("ga_align_batch", "ga_align_batch_modes", "ga_align_batch_host", "ga_align_batch_host_modes",
+              "ga_align_cross",
               "ga_align_long",
               "ga_align_long_noalloc", "ga_align_banded", "ga_band_features", "ga_band_min_w",
               "ga_band_predict", "ga_mlp_forward", "ga_mlp_loss_grad", "ga_mlp_train",
@@ -251,6 +254,25 @@ def align_batch(q_codes, q_off, t_codes, t_off, matrix, gap_open, gap_extend, mo
                                ctypes.byref(st) if stats else None)
     if rc:
         raise GotohError(rc, "ga_align_batch")
+    return (scores, st.as_dict()) if stats else scores
+
+
+def align_batch_modes(q_codes, q_off, t_codes, t_off, matrix, gap_open, gap_extend, modes, scores=None,
+                      stream=None, stats: bool = False):
+    """Scores [len(modes), npairs] of the pairs in several modes; the inputs are packed once."""
+    import torch
+    _check_dev(q_codes, q_off, t_codes, t_off)
+    npairs = q_off.numel() - 1
+    md = np.ascontiguousarray([_mode(m) for m in modes], dtype=np.int32)
+    if scores is None:
+        scores = torch.empty((len(md), max(npairs, 0)), dtype=torch.int32, device=q_codes.device)
+    sc, keep = make_scoring(matrix, gap_open, gap_extend)
+    st = Stats()
+    rc = load().ga_align_batch_modes(_ptr(q_codes), _ptr(q_off), _ptr(t_codes), _ptr(t_off), npairs,
+                                     ctypes.byref(sc), md.ctypes.data, len(md), _ptr(scores),
+                                     _stream_ptr(stream), ctypes.byref(st) if stats else None)
+    if rc:
+        raise GotohError(rc, "ga_align_batch_modes")
     return (scores, st.as_dict()) if stats else scores
 
 

@@ -632,17 +632,22 @@ struct Events {
   }
 };
 
-int batch_impl(const uint8_t *q_codes, const int64_t *q_off, const uint8_t *t_codes,
-               const int64_t *t_off, int64_t npairs, const ga_scoring *scoring, int32_t mode,
-               int32_t *scores, void *stream, ga_stats *stats, int force_long,
-               KnownRange qr = KnownRange(), KnownRange tr = KnownRange()) {
-  if (npairs < 0 || mode < 0 || mode > 2) return GA_ERR_ARG;
+// Independent pairs in one or more modes: both sequence sets are validated
+// and packed once, then every mode is planned and aligned on the packed
+// copies; the scores of mode k go to scores + k * score_stride.
+int batch_modes_impl(const uint8_t *q_codes, const int64_t *q_off, const uint8_t *t_codes,
+                     const int64_t *t_off, int64_t npairs, const ga_scoring *scoring, const int32_t *modes,
+                     int32_t nmodes, int32_t *scores, int64_t score_stride, void *stream, ga_stats *stats,
+                     int force_long, KnownRange qr = KnownRange(), KnownRange tr = KnownRange()) {
+  if (npairs < 0 || !modes || nmodes < 1 || nmodes > 8) return GA_ERR_ARG;
+  for (int k = 0; k < nmodes; ++k)
+    if (modes[k] < 0 || modes[k] > 2) return GA_ERR_ARG;
   if (npairs > 0 && (!q_codes || !q_off || !t_codes || !t_off || !scores)) return GA_ERR_ARG;
   if (npairs >= (1ll << 31) - 64) return GA_ERR_ARG;
   Call c((cudaStream_t)stream);
   int rc = check_scoring(scoring, &c.sc);
   if (rc) return rc;
-  c.mode = mode;
+  c.mode = modes[0];
   c.timing = stats != nullptr;
   Events ev(stats != nullptr, c.s);
   if ((rc = setup(c))) return rc;
@@ -654,8 +659,21 @@ int batch_impl(const uint8_t *q_codes, const int64_t *q_off, const uint8_t *t_co
   int32_t *sorted = c.al.get<int32_t>((size_t)npairs);
   int32_t *rerun = c.al.get<int32_t>((size_t)npairs);
   if (c.al.failed) return GA_ERR_OOM;
-  if ((rc = run_chunk(c, Q, T, npairs, 0, 0, scores, force_long, keys, info, sorted, rerun))) return rc;
-  return finish(c, stats, ev.e0, ev.e1, npairs);
+  for (int k = 0; k < nmodes; ++k) {
+    c.mode = modes[k];
+    if ((rc = run_chunk(c, Q, T, npairs, 0, 0, scores + (size_t)k * (size_t)score_stride, force_long, keys, info,
+                        sorted, rerun)))
+      return rc;
+  }
+  return finish(c, stats, ev.e0, ev.e1, npairs * nmodes);
+}
+
+int batch_impl(const uint8_t *q_codes, const int64_t *q_off, const uint8_t *t_codes,
+               const int64_t *t_off, int64_t npairs, const ga_scoring *scoring, int32_t mode,
+               int32_t *scores, void *stream, ga_stats *stats, int force_long,
+               KnownRange qr = KnownRange(), KnownRange tr = KnownRange()) {
+  return batch_modes_impl(q_codes, q_off, t_codes, t_off, npairs, scoring, &mode, 1, scores, 0, stream, stats,
+                          force_long, qr, tr);
 }
 
 __global__ void fill_i32_kernel(int32_t *p, int64_t n, int32_t v) {
@@ -1582,10 +1600,10 @@ static int batch_host_impl(const uint8_t *q_codes, const int64_t *q_off, const u
     qr.total = q_off[b];
     tr.start = t_off[a];
     tr.total = t_off[b];
-    for (int md = 0; !rc && md < nmodes; ++md) {  // every mode on the chunk copied once
+    {  // every mode on the chunk copied once (packed once)
       ga_stats st{};
-      rc = batch_impl(dq, dqo + a, dt, dto + a, b - a, scoring, modes[md], ds + (size_t)md * npairs + a, stream,
-                      stats ? &st : nullptr, 0, qr, tr);
+      rc = batch_modes_impl(dq, dqo + a, dt, dto + a, b - a, scoring, modes, nmodes, ds + a, npairs, stream,
+                            stats ? &st : nullptr, 0, qr, tr);
       if (!rc && stats) {
         tot.cells += st.cells; tot.pairs += st.pairs; tot.pairs_int16 += st.pairs_int16;
         tot.pairs_int32 += st.pairs_int32; tot.pairs_int32_rerun += st.pairs_int32_rerun;
@@ -1625,6 +1643,14 @@ static int batch_host_impl(const uint8_t *q_codes, const int64_t *q_off, const u
   if (e1) cudaEventDestroy(e1);
   if (cs) cudaStreamDestroy(cs);
   return rc;
+}
+
+int ga_align_batch_modes(const uint8_t *q_codes, const int64_t *q_off, const uint8_t *t_codes,
+                         const int64_t *t_off, int64_t npairs, const ga_scoring *scoring,
+                         const int32_t *modes, int32_t nmodes, int32_t *scores, void *stream,
+                         ga_stats *stats) {
+  return batch_modes_impl(q_codes, q_off, t_codes, t_off, npairs, scoring, modes, nmodes, scores, npairs, stream,
+                          stats, 0);
 }
 
 int ga_align_batch_host(const uint8_t *q_codes, const int64_t *q_off, const uint8_t *t_codes,

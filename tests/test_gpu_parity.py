@@ -250,6 +250,24 @@ def test_host_entry_point_in_chunks():
     assert_same(host[sub], want, "host chunks vs oracle")
 
 
+def test_batch_modes_entry_point():
+    # several modes from one packing of the inputs: every row equals the
+    # single-mode entry point, mixed lengths (inter-sequence bins, long pairs,
+    # empty sequences) included; bad modes are rejected before any work
+    qc, qo, tc, to = _pairs(np.random.default_rng(8), np.random.default_rng(9).integers(0, 700, size=900),
+                            np.random.default_rng(10).integers(0, 700, size=900))
+    b = synth.Batch(qc, qo, tc, to, synth.dna_matrix(2, -3), 5, 2, "modes")
+    q, qo_d, t, to_d = _dev(b)
+    modes = ["semiglobal", "local", "global", "local"]
+    got, st = ga.align_batch_modes(q, qo_d, t, to_d, b.matrix, 5, 2, modes, stats=True)
+    assert tuple(got.shape) == (4, b.npairs) and st["status"] == 0 and st["pairs"] == 4 * b.npairs
+    for k, mode in enumerate(modes):
+        assert_same(got[k].cpu().numpy(), oracle_batch(b, mode), f"modes row {k} {mode}")
+    with pytest.raises(ga.GotohError) as e:
+        ga.align_batch_modes(q, qo_d, t, to_d, b.matrix, 5, 2, [1, 5])
+    assert e.value.code == 1
+
+
 def test_host_modes_entry_point():
     # several modes of the same pairs from one host copy, over several copy
     # chunks; every row equals the device entry point in its mode, and the
