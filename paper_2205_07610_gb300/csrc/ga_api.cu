@@ -880,16 +880,14 @@ int features_impl(const uint8_t *q_codes, const int64_t *q_off, const uint8_t *t
 // stages of 512 columns), flagged pairs recomputed exactly in int32.
 template <int K>
 int launch_kp(Call &c, KPParams &kp, int64_t max_grid) {
-  const size_t smem = (size_t)kKpWarps * (size_t)(c.sc.A + 1) * (size_t)(kKpG * K);
+  const size_t smem = sizeof(uint32_t) * (size_t)kp_prof_words<K>(c.sc.A);
   if (cudaFuncSetAttribute(kp_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
     return GA_ERR_CUDA;
   int occ = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kp_kernel<K>, 32 * kKpWarps, smem) != cudaSuccess)
     return GA_ERR_CUDA;
-  kp.prof_bytes = (c.sc.A + 1) * kKpG * K;
-  const int64_t ntasks = (int64_t)kp.nqb * ((kp.ntv + 3) / 4);
-  const int64_t want = (ntasks + kKpWarps - 1) / kKpWarps;
-  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>({want, (int64_t)c.nsm * std::max(occ, 1), max_grid}));
+  const int64_t ntasks = (int64_t)((kp.nqb + 1) / 2) * ((kp.ntv + kKpGroups - 1) / kKpGroups);
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>({ntasks, (int64_t)c.nsm * std::max(occ, 1), max_grid}));
   c.dp_begin();
   kp_kernel<K><<<grid, 32 * kKpWarps, smem, c.s>>>(kp);
   c.dp_end();
@@ -968,6 +966,12 @@ int cross_protein_local(Call &c, const uint8_t *q_codes, const int64_t *q_off, i
     bins[kp_bin_for(m)].push_back((int32_t)k);
     cells += m;
   }
+  // the kernel packs queries 2i and 2i+1 of a bin into one register; sorted
+  // by length, the two queries of a pair have the same number of stages
+  for (auto &b : bins)
+    std::stable_sort(b.begin(), b.end(), [&](int32_t x, int32_t y) {
+      return hqo[(size_t)x + 1] - hqo[(size_t)x] > hqo[(size_t)y + 1] - hqo[(size_t)y];
+    });
   {
     std::vector<int64_t> hto((size_t)nt + 1);
     std::vector<uint8_t> htb((size_t)nt);
@@ -988,7 +992,7 @@ int cross_protein_local(Call &c, const uint8_t *q_codes, const int64_t *q_off, i
   // per-group stage edges: every group slot of the largest grid
   const int64_t max_grid = (int64_t)c.nsm * 4;
   const int64_t stride = (int64_t)std::max(max_len, 0) + 64;
-  int2 *bnd = c.al.get<int2>((size_t)max_grid * kKpWarps * 2 * (size_t)stride);
+  int2 *bnd = c.al.get<int2>((size_t)max_grid * kKpGroups * (size_t)stride);
   if (c.al.failed) return GA_ERR_OOM;
   KPParams kp{};
   kp.q_codes = q_codes;

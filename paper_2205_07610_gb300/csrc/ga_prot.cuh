@@ -1,29 +1,32 @@
 // ga_prot.cuh -- inter-sequence database search for alphabets of more than
-// four symbols (protein), local mode: one query against many targets.
+// four symbols (protein), local mode: many queries against many targets.
 //
-// The query runs along the columns and its scoring profile
-// P[c][x] = sigma(query residue x, target residue c) lives in shared memory
-// as int8 (Sec. 3.1, "scoring profile"), one copy per warp for the stage of
-// columns it is working on (rebuilt, one 32-bit word per lane and row, from a
-// transposed sigma table whenever the warp's query or stage changes);
-// targets run along the rows.  As in the DNA
-// inter-sequence kernel, a group of 16 lanes computes one wavefront with K
-// columns per lane, and every lane carries two targets in the two int16
-// halves of each register (int16x2).  For each row a lane loads the K
-// profile bytes of its columns for the row residue of each half (16-byte
-// shared loads) and one byte permute per column builds the packed pair of
-// substitution scores.  A warp takes 4 targets of one query per task
-// (targets sorted longest first, tasks query-major so that a warp keeps its
-// profile for many tasks).  Queries longer than 16K columns run in stages
-// of 16K columns; the right edge of a stage (packed H and outgoing F per
-// row) goes to a per-group global buffer, batched through shared memory,
-// that lane 0 of the next stage reads.
+// Queries run along the columns, targets along the rows.  As in the DNA
+// inter-sequence kernel a group of 16 lanes computes one wavefront with K
+// columns per lane, and every register carries two alignments in its two
+// int16 halves; here the halves are two queries of similar length against
+// the same target, so that both halves of a row share the row residue c and
+// the scoring profile (Sec. 3.1, "scoring profile") can hold the packed
+// pair directly:
+//
+//   P[c][x] = sigma(query0[x], c) | sigma(query1[x], c) << 16   (int16x2)
+//
+// One profile per block, in shared memory, for the stage of 16K columns the
+// block is working on: the 4 warps (8 groups) of a block take 8 targets of
+// one query pair per task (targets sorted longest first, tasks
+// query-pair-major), and the block rebuilds the profile from a transposed
+// sigma table only when its query pair or stage changes.  A row then costs
+// K/4 16-byte shared loads per lane and no per-column byte permute.
+// Queries longer than 16K columns run in stages of 16K columns; the right
+// edge of a stage (packed H and outgoing F per row) goes to a per-group
+// global buffer, batched through shared memory, that lane 0 of the next
+// stage reads.
 //
 // Padding: rows past a target's end use the all-zero profile row and
-// columns past the query's end have score 0; in local mode such cells
-// never exceed the largest real cell, so the running maximum is exact.
-// A target whose running maximum reaches 32767 - sigma_max is queued for
-// an exact int32 rerun.
+// columns past a query's end have score 0; in local mode such cells never
+// exceed the largest real cell, so the running maximum is exact.  A pair
+// whose running maximum reaches 32767 - sigma_max is queued for an exact
+// int32 rerun.
 #pragma once
 
 #include "ga_dp.cuh"
@@ -33,6 +36,7 @@ namespace ga {
 
 constexpr int kKpG = 16;
 constexpr int kKpWarps = 4;
+constexpr int kKpGroups = 2 * kKpWarps;  // targets per block task
 constexpr int kKpMaxA = 31;
 
 struct KPParams {
@@ -40,7 +44,7 @@ struct KPParams {
   const int64_t *q_off;
   const uint8_t *t_codes;
   const int64_t *t_off;
-  const int32_t *queries;   // query ids of this launch
+  const int32_t *queries;   // query ids of this launch; entries 2i, 2i+1 form pair i
   int32_t nqb;
   const int32_t *t_sorted;  // valid targets, longest first
   int32_t ntv;
@@ -54,32 +58,20 @@ struct KPParams {
   int32_t rerun_cap;
   int2 *bnd;                // per group slot: bnd_stride entries
   int64_t bnd_stride;
-  int32_t prof_bytes;       // per warp: (A + 1) * 16K
 };
 
-// Profile layout: row c holds the stage's 16K columns.  With K = 8 or 24
-// (8-byte loads) DP lane t reads its K columns at byte t*K; with K = 16 or
-// 32 (16-byte loads) the row is chunk-major: 16-column chunk q of lane t
-// sits at byte q*256 + t*16, so that the 8 lanes of a shared-memory phase
-// read 8 different 16-byte bank groups with compile-time offsets (rows are
-// multiples of 128 bytes, so the row never changes the bank).
+// Profile layout: row c holds the stage's 16K columns as int16x2 words in
+// chunks of 4 columns; chunk q of DP lane t sits at word q*64 + t*4, so the
+// 8 lanes of a shared-memory phase read 8 consecutive 16-byte chunks
+// whatever rows they are on (rows are multiples of 128 bytes).
 template <int K>
-__device__ __forceinline__ int prof_lane_offset(int t) {
-  return (K % 16) == 0 ? t * 16 : t * K;
-}
-// Byte offset in a row of the K/2 columns L*K/2 .. written by lane L of the
-// rebuild (they belong to DP lane L*K/2 / K).
-template <int K>
-__device__ __forceinline__ int prof_offset(int L) {
-  constexpr int CPL = K / 2;
-  const int t = L * CPL / K, c0 = L * CPL - t * K;
-  if constexpr ((K % 16) == 0) return (c0 / 16) * 256 + t * 16 + (c0 % 16);
-  else return L * CPL;
+__host__ __device__ constexpr int kp_prof_words(int A) {
+  return (A + 1) * kKpG * K;
 }
 
 // Resident blocks per SM requested from ptxas: what shared memory allows for
-// BLOSUM-sized alphabets (24 symbols + pad: (A+1) x 16K bytes of profile per
-// warp plus 11.5 KB of static rings per block).
+// BLOSUM-sized alphabets (24 symbols + pad: (A+1) x 16K words of profile per
+// block plus 11.5 KB of static rings).
 template <int K>
 struct KPMinBlocks {
   static constexpr int value = K <= 8 ? 8 : K <= 16 ? 6 : K <= 24 ? 4 : 3;
@@ -89,113 +81,99 @@ template <int K>
 __global__ void __launch_bounds__(32 * kKpWarps, KPMinBlocks<K>::value) kp_kernel(const __grid_constant__ KPParams p) {
   using Cell = CellS16x2;
   using T = uint32_t;
-  constexpr int G = kKpG, W = G * K, kRing = 4 * G;
-  static_assert(K % 8 == 0, "profile loads are 8 columns wide");
-  extern __shared__ __align__(16) uint8_t kp_smem[];
+  constexpr int G = kKpG, W = G * K, kRing = 4 * G, CH = K / 4;  // CH: 4-column chunks per lane
+  static_assert(K % 8 == 0, "profile rows are 16-byte chunks");
+  extern __shared__ __align__(16) uint32_t kp_prof[];
   // sigma transposed: sigT_s[c * 32 + x] = sigma(query code x, target code c);
   // rows c >= A and columns x >= A are 0 (x = 31 is the pad column)
-  __shared__ __align__(16) uint8_t sigT_s[32 * 32];
-  __shared__ uint32_t ring_s[kKpWarps][2][5 * G];  // row codes of both halves, mirrored ring
-  __shared__ uint2 in_ring_s[kKpWarps][2][64];
-  __shared__ uint2 out_ring_s[kKpWarps][2][64];
+  __shared__ __align__(16) int8_t sigT_s[32 * 32];
+  __shared__ uint32_t ring_s[kKpGroups][5 * G];  // row codes, mirrored ring
+  __shared__ uint2 in_ring_s[kKpGroups][64];
+  __shared__ uint2 out_ring_s[kKpGroups][64];
+  __shared__ int task_s;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int g = lane / G, t = lane % G;
+  const int g = lane / G, t = lane % G, grp = warp * 2 + g;
   for (int i = threadIdx.x; i < 32 * 32; i += blockDim.x) {
     const int c = i >> 5, x = i & 31;
-    sigT_s[i] = (uint8_t)((c < p.A && x < p.A) ? p.sigma[x * p.A + c] : 0);
+    sigT_s[i] = (c < p.A && x < p.A) ? p.sigma[x * p.A + c] : (int8_t)0;
   }
-  __syncthreads();
-  uint8_t *prof = kp_smem + (size_t)warp * (size_t)p.prof_bytes;
-  uint32_t *ring = ring_s[warp][g];
-  uint2 *in_ring = in_ring_s[warp][g];
-  uint2 *out_ring = out_ring_s[warp][g];
-  int2 *bnd = p.bnd + (size_t)((blockIdx.x * kKpWarps + warp) * 2 + g) * (size_t)p.bnd_stride;
+  uint32_t *ring = ring_s[grp];
+  uint2 *in_ring = in_ring_s[grp];
+  uint2 *out_ring = out_ring_s[grp];
+  int2 *bnd = p.bnd + (size_t)(blockIdx.x * kKpGroups + grp) * (size_t)p.bnd_stride;
   const int A = p.A, alpha = p.alpha, beta = p.beta;
   const T NB = Cell::splat(-beta), NAc = Cell::splat(-alpha);
-  const int ngroups = (p.ntv + 3) / 4;
-  const int64_t ntasks = (int64_t)p.nqb * ngroups;
-  int cur_q = -1, cur_stage = -1;  // query and stage of the profile in `prof`
+  const int ngroups = (p.ntv + kKpGroups - 1) / kKpGroups;
+  const int nqp = (p.nqb + 1) / 2;
+  const int64_t ntasks = (int64_t)nqp * ngroups;
+  int cur_qp = -1, cur_stage = -1;  // query pair and stage of the profile
 
   for (;;) {
-    int task = 0;
-    if (lane == 0) task = atomicAdd(p.task_counter, 1);
-    task = __shfl_sync(0xffffffffu, task, 0);
+    __syncthreads();  // the previous task is done everywhere (and sigT_s is filled)
+    if (threadIdx.x == 0) task_s = atomicAdd(p.task_counter, 1);
+    __syncthreads();
+    const int task = task_s;
     if ((int64_t)task >= ntasks) break;
-    const int k = p.queries[task / ngroups];
-    const int tg = task % ngroups;
-    const int64_t qs = p.q_off[k];
-    const int m = (int)(p.q_off[k + 1] - qs);
-    // the two targets of this group (halves 0 / 1)
-    int tid[2], len[2];
-    int64_t tstart[2];
+    const int qp = task / ngroups, tg = task % ngroups;
+    int kq[2], m[2];
+    int64_t qs[2];
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
-      const int slot = tg * 4 + g * 2 + h;
-      tid[h] = slot < p.ntv ? p.t_sorted[slot] : -1;
-      tstart[h] = tid[h] >= 0 ? p.t_off[tid[h]] : 0;
-      len[h] = tid[h] >= 0 ? (int)(p.t_off[tid[h] + 1] - tstart[h]) : 0;
+      const int qi = 2 * qp + h;
+      kq[h] = qi < p.nqb ? p.queries[qi] : -1;
+      qs[h] = kq[h] >= 0 ? p.q_off[kq[h]] : 0;
+      m[h] = kq[h] >= 0 ? (int)(p.q_off[kq[h] + 1] - qs[h]) : 0;
     }
-    const int Rtask = __reduce_max_sync(0xffffffffu, (unsigned)::max(len[0], len[1]));
-    const int nstage = (m + W - 1) / W;
+    const int slot = tg * kKpGroups + grp;
+    const int tid = slot < p.ntv ? p.t_sorted[slot] : -1;
+    const int64_t tstart = tid >= 0 ? p.t_off[tid] : 0;
+    const int len = tid >= 0 ? (int)(p.t_off[tid + 1] - tstart) : 0;
+    const int Rw = __reduce_max_sync(0xffffffffu, (unsigned)len);  // rows of this warp
+    const int nstage = (::max(m[0], m[1]) + W - 1) / W;            // the same for the whole block
     T best = Cell::splat(0);
 
     for (int s = 0; s < nstage; ++s) {
-      // ---- profile of this stage's columns (the whole warp) -------------
-      // Lane L writes the K/2 columns L*K/2 .. of every profile row, one
-      // row at a time, from the transposed sigma table (pad columns and the
-      // pad row A are 0).
-      if (k != cur_q || s != cur_stage) {
-        __syncwarp();
-        constexpr int CPL = K / 2;
-        uint32_t qx4[CPL / 4];  // 4 codes per word
-#pragma unroll
-        for (int u = 0; u < CPL / 4; ++u) {
-          uint32_t v = 0;
+      // ---- the block's profile of this stage's columns ------------------
+      if (qp != cur_qp || s != cur_stage) {
+        __syncthreads();  // nobody reads the old profile any more
+        for (int ch = threadIdx.x; ch < W / 4; ch += blockDim.x) {
+          const int dt = ch / CH, q = ch - dt * CH;  // DP lane and its chunk
+          const int col0 = s * W + dt * K + 4 * q;
+          int x0[4], x1[4];
 #pragma unroll
           for (int i = 0; i < 4; ++i) {
-            const int col = s * W + lane * CPL + 4 * u + i;
-            v |= (uint32_t)(col < m ? p.q_codes[qs + col] : 31) << (8 * i);
+            x0[i] = col0 + i < m[0] ? (int)p.q_codes[qs[0] + col0 + i] : 31;
+            x1[i] = col0 + i < m[1] ? (int)p.q_codes[qs[1] + col0 + i] : 31;
           }
-          qx4[u] = v;
-        }
-        const int pofs = prof_offset<K>(lane);
-        for (int c = 0; c <= A; ++c) {
-          const uint8_t *row = sigT_s + c * 32;
-          uint32_t w[CPL / 4];
+          uint4 *dst = reinterpret_cast<uint4 *>(kp_prof + q * 64 + dt * 4);
+          for (int c = 0; c <= A; ++c) {
+            const int8_t *row = sigT_s + c * 32;
+            uint32_t w[4];
 #pragma unroll
-          for (int u = 0; u < CPL / 4; ++u)
-            w[u] = (uint32_t)row[qx4[u] & 0xffu] | ((uint32_t)row[(qx4[u] >> 8) & 0xffu] << 8) |
-                   ((uint32_t)row[(qx4[u] >> 16) & 0xffu] << 16) | ((uint32_t)row[qx4[u] >> 24] << 24);
-          uint8_t *dst = prof + (size_t)c * W + pofs;
-          if constexpr (CPL == 16) {
-            *reinterpret_cast<uint4 *>(dst) = make_uint4(w[0], w[1], w[2], w[3]);
-          } else if constexpr (CPL == 8) {
-            *reinterpret_cast<uint2 *>(dst) = make_uint2(w[0], w[1]);
-          } else {
-#pragma unroll
-            for (int u = 0; u < CPL / 4; ++u) reinterpret_cast<uint32_t *>(dst)[u] = w[u];
+            for (int i = 0; i < 4; ++i)
+              w[i] = (uint32_t)(uint16_t)(int16_t)row[x0[i]] | ((uint32_t)(uint16_t)(int16_t)row[x1[i]] << 16);
+            dst[(size_t)c * (W / 4)] = make_uint4(w[0], w[1], w[2], w[3]);
           }
         }
-        cur_q = k;
+        cur_qp = qp;
         cur_stage = s;
-        __syncwarp();
+        __syncthreads();
       }
-      // ---- row codes of both halves, refilled G rows ahead ---------------
+      if (Rw == 0) continue;  // a warp past the last target
+      // ---- row codes, refilled G rows ahead -----------------------------
       auto fill_batch = [&](int b) {
         const int r = b * G + 1 + t;
-        const uint32_t c0 = r <= len[0] ? p.t_codes[tstart[0] + r - 1] : (uint32_t)A;
-        const uint32_t c1 = r <= len[1] ? p.t_codes[tstart[1] + r - 1] : (uint32_t)A;
+        const uint32_t c = r <= len ? (uint32_t)p.t_codes[tstart + r - 1] : (uint32_t)A;
         const int sl = r & (kRing - 1);
-        const uint32_t v = c0 | (c1 << 16);
-        ring[sl] = v;
-        if (sl < G) ring[sl + kRing] = v;
+        ring[sl] = c;
+        if (sl < G) ring[sl + kRing] = c;
       };
       // left edge of the stage, batched (rows 16b+1 .. 16b+16)
       auto load_edge = [&](int b) {
         if (s > 0) {
           const int r = b * G + 1 + t;
-          if (r <= Rtask) {
+          if (r <= Rw) {
             const int2 v = bnd[r];
             in_ring[(r - 1) & 63] = make_uint2((uint32_t)v.x, (uint32_t)v.y);
           }
@@ -225,8 +203,9 @@ __global__ void __launch_bounds__(32 * kKpWarps, KPMinBlocks<K>::value) kp_kerne
       };
       T Hdiag = Cell::splat(0), Hleft = Cell::splat(0), Fin = Cell::splat(CellInfo<Cell>::kNeg);
       if (t == 0) left(1, Hleft, Fin);
+      const uint32_t *plane = kp_prof + t * 4;
 
-      const int nit = Rtask + G - 1;
+      const int nit = Rw + G - 1;
       for (int it = 0; it < nit; ++it) {
         if ((it % G) == 0) {
           __syncwarp();
@@ -241,32 +220,17 @@ __global__ void __launch_bounds__(32 * kKpWarps, KPMinBlocks<K>::value) kp_kerne
         }
         const int r = it - t + 1;
         T Hout = H[K - 1], Fout = Cell::splat(CellInfo<Cell>::kNeg);
-        if ((unsigned)(r - 1) < (unsigned)Rtask) {
+        if ((unsigned)(r - 1) < (unsigned)Rw) {
           const uint32_t rc = ring[r & (kRing - 1)];
-          const uint8_t *b0 = prof + (size_t)(rc & 0xffffu) * W + prof_lane_offset<K>(t);
-          const uint8_t *b1 = prof + (size_t)(rc >> 16) * W + prof_lane_offset<K>(t);
-          uint32_t w0[K / 4], w1[K / 4];
-          if constexpr ((K % 16) == 0) {  // chunk-major rows, 16-byte loads
+          const uint4 *pr = reinterpret_cast<const uint4 *>(plane + (size_t)rc * W);
+          uint32_t w[K];
 #pragma unroll
-            for (int q = 0; q < K / 16; ++q) {
-              const uint4 a = *reinterpret_cast<const uint4 *>(b0 + q * 256);
-              const uint4 b = *reinterpret_cast<const uint4 *>(b1 + q * 256);
-              w0[4 * q] = a.x; w0[4 * q + 1] = a.y; w0[4 * q + 2] = a.z; w0[4 * q + 3] = a.w;
-              w1[4 * q] = b.x; w1[4 * q + 1] = b.y; w1[4 * q + 2] = b.z; w1[4 * q + 3] = b.w;
-            }
-          } else {  // 8-byte boundaries (K = 8, 24)
-#pragma unroll
-            for (int q = 0; q < K / 8; ++q) {
-              const uint2 a = reinterpret_cast<const uint2 *>(b0)[q];
-              const uint2 b = reinterpret_cast<const uint2 *>(b1)[q];
-              w0[2 * q] = a.x; w0[2 * q + 1] = a.y;
-              w1[2 * q] = b.x; w1[2 * q + 1] = b.y;
-            }
+          for (int q = 0; q < CH; ++q) {
+            const uint4 a = pr[q * 16];
+            w[4 * q] = a.x; w[4 * q + 1] = a.y; w[4 * q + 2] = a.z; w[4 * q + 3] = a.w;
           }
           Fout = dp_row<Cell, kModeLocal, K>(
-              H, E, Hdiag, Fin, NB, best,
-              [&](int j) -> T { return (T)prmt(w0[j >> 2], w1[j >> 2], sext_sel<Cell>(j & 3)); },
-              [&](int) -> T { return NAc; });
+              H, E, Hdiag, Fin, NB, best, [&](int j) -> T { return w[j]; }, [&](int) -> T { return NAc; });
           Hout = H[K - 1];
           if (t == G - 1) out_ring[(r - 1) & 63] = make_uint2(Hout, Fout);
         }
@@ -274,7 +238,7 @@ __global__ void __launch_bounds__(32 * kKpWarps, KPMinBlocks<K>::value) kp_kerne
         Hleft = __shfl_up_sync(0xffffffffu, Hout, 1, G);
         Fin = __shfl_up_sync(0xffffffffu, Fout, 1, G);
         if (t == 0) {
-          if (it + 2 <= Rtask) left(it + 2, Hleft, Fin);
+          if (it + 2 <= Rw) left(it + 2, Hleft, Fin);
           else {
             Hleft = Cell::splat(0);
             Fin = NAc;
@@ -284,7 +248,7 @@ __global__ void __launch_bounds__(32 * kKpWarps, KPMinBlocks<K>::value) kp_kerne
       __syncwarp();
       if (s + 1 < nstage) {  // flush the remaining rows of the edge
         const int first = (nit - 1 >= 2 * G) ? ((nit - 1) / G) * G - 2 * G + 1 + G : 1;
-        for (int r = first + t; r <= Rtask; r += G) {
+        for (int r = first + t; r <= Rw; r += G) {
           const uint2 v = out_ring[(r - 1) & 63];
           bnd[r] = make_int2((int)v.x, (int)v.y);
         }
@@ -296,8 +260,8 @@ __global__ void __launch_bounds__(32 * kKpWarps, KPMinBlocks<K>::value) kp_kerne
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       const int v = group_max<G>(cell_get<Cell>(best, h));
-      if (tid[h] >= 0 && t == 0) {
-        const int64_t pid = (int64_t)k * p.nt + tid[h];
+      if (kq[h] >= 0 && tid >= 0 && t == 0) {
+        const int64_t pid = (int64_t)kq[h] * p.nt + tid;
         if (v >= 32767 - p.sigma_max_pos) {
           const int sl = atomicAdd(p.rerun_count, 1);
           if (sl < p.rerun_cap) p.rerun_list[sl] = (int32_t)pid;
@@ -306,7 +270,6 @@ __global__ void __launch_bounds__(32 * kKpWarps, KPMinBlocks<K>::value) kp_kerne
         }
       }
     }
-    __syncwarp();
   }
 }
 
