@@ -894,21 +894,41 @@ int launch_kp(Call &c, KPParams &kp, int64_t max_grid) {
   return cudaGetLastError() == cudaSuccess ? GA_OK : GA_ERR_CUDA;
 }
 
-// Tile (K = 8, 16, 24, 32) of a query of m columns in the protein search.
+// Tiles of the protein search: columns per lane K (16K columns per group)
+// and the measured relative rate of the kernel per computed cell on GB300
+// (wider tiles amortise the per-row work over more columns); a query of
+// several stages pays for its profile rebuilds and stage edges.
+constexpr int kKpTiles = 6;
+constexpr int kKpTileK[kKpTiles] = {8, 16, 20, 24, 28, 32};
+constexpr double kKpRate[kKpTiles] = {0.68, 0.82, 0.97, 1.0, 1.03, 1.01};
+constexpr double kKpStagedRate = 0.97;
+
+// Tile of a query of m columns: the one that minimises the estimated time
+// ceil(m / 16K) * 16K / rate(K).
 int kp_bin_for(int64_t m) {
-  static const double kRate[4] = {0.71, 0.91, 1.0, 0.96};  // per computed cell, K = 8 .. 32
-  int best = 3;
+  int best = kKpTiles - 1;
   double tbest = 1e300;
-  for (int b = 0; b < 4; ++b) {
-    const int64_t w = (int64_t)kKpG * 8 * (b + 1);
+  for (int b = 0; b < kKpTiles; ++b) {
+    const int64_t w = (int64_t)kKpG * kKpTileK[b];
     const int64_t nst = (m + w - 1) / w;
-    const double t = (double)(nst * w) / (kRate[b] * (nst > 1 ? 0.93 : 1.0));
+    const double t = (double)(nst * w) / (kKpRate[b] * (nst > 1 ? kKpStagedRate : 1.0));
     if (t < tbest) {
       tbest = t;
       best = b;
     }
   }
   return best;
+}
+
+int launch_kp_tile(Call &c, KPParams &kp, int64_t max_grid, int b) {
+  switch (kKpTileK[b]) {
+    case 8: return launch_kp<8>(c, kp, max_grid);
+    case 16: return launch_kp<16>(c, kp, max_grid);
+    case 20: return launch_kp<20>(c, kp, max_grid);
+    case 24: return launch_kp<24>(c, kp, max_grid);
+    case 28: return launch_kp<28>(c, kp, max_grid);
+    default: return launch_kp<32>(c, kp, max_grid);
+  }
 }
 
 int cross_protein_local(Call &c, const uint8_t *q_codes, const int64_t *q_off, int64_t nq,
@@ -953,12 +973,8 @@ int cross_protein_local(Call &c, const uint8_t *q_codes, const int64_t *q_off, i
                         256, 0, c.s>>>(Q.bad, nq, T.bad, nt, scores, &c.small->status);
     ++c.launches;
   }
-  // query bins: tile width 16K (K = 8, 16, 24, 32) per query, chosen to
-  // minimise the estimated time ceil(m / 16K) * 16K / rate(K), with the
-  // measured relative rates of the kernel per computed cell (GB300: wider
-  // tiles amortise the per-row work; a query of several stages pays for
-  // its profile rebuilds and stage edges)
-  std::vector<int32_t> bins[4];
+  // query bins: one tile per query (kp_bin_for)
+  std::vector<int32_t> bins[kKpTiles];
   int64_t cells = 0, tcells = 0;
   for (int64_t k = 0; k < nq; ++k) {
     if (hqb[k]) continue;
@@ -985,7 +1001,7 @@ int cross_protein_local(Call &c, const uint8_t *q_codes, const int64_t *q_off, i
   int32_t *dq = c.al.get<int32_t>((size_t)std::max<int64_t>(nq, 1));
   if (c.al.failed) return GA_ERR_OOM;
   std::vector<int32_t> flat;
-  for (int b = 0; b < 4; ++b) flat.insert(flat.end(), bins[b].begin(), bins[b].end());
+  for (int b = 0; b < kKpTiles; ++b) flat.insert(flat.end(), bins[b].begin(), bins[b].end());
   if (!flat.empty() &&
       cudaMemcpyAsync(dq, flat.data(), sizeof(int32_t) * flat.size(), cudaMemcpyHostToDevice, c.s) != cudaSuccess)
     return GA_ERR_CUDA;
@@ -1014,7 +1030,7 @@ int cross_protein_local(Call &c, const uint8_t *q_codes, const int64_t *q_off, i
   kp.bnd = bnd;
   kp.bnd_stride = stride;
   size_t off = 0;
-  for (int b = 0; b < 4; ++b) {
+  for (int b = 0; b < kKpTiles; ++b) {
     if (bins[b].empty() || ntv == 0) {
       off += bins[b].size();
       continue;
@@ -1023,8 +1039,7 @@ int cross_protein_local(Call &c, const uint8_t *q_codes, const int64_t *q_off, i
     kp.nqb = (int32_t)bins[b].size();
     kp.task_counter = &c.small->counters[b];
     off += bins[b].size();
-    rc = b == 0 ? launch_kp<8>(c, kp, max_grid) : b == 1 ? launch_kp<16>(c, kp, max_grid)
-       : b == 2 ? launch_kp<24>(c, kp, max_grid) : launch_kp<32>(c, kp, max_grid);
+    rc = launch_kp_tile(c, kp, max_grid, b);
     if (rc) return rc;
   }
   // exact int32 rerun of flagged pairs (rare: a local score near 32767)

@@ -17,10 +17,10 @@
 // query-pair-major), and the block rebuilds the profile from a transposed
 // sigma table only when its query pair or stage changes.  A row then costs
 // K/4 16-byte shared loads per lane and no per-column byte permute.
-// Queries longer than 16K columns run in stages of 16K columns; the right
-// edge of a stage (packed H and outgoing F per row) goes to a per-group
-// global buffer, batched through shared memory, that lane 0 of the next
-// stage reads.
+// Queries longer than 16K columns run in stages of 16K columns; lane 15
+// stores the right edge of a stage (packed H and outgoing F per row) to a
+// per-group global buffer, which the next stage reads back in batches of
+// 16 rows through shared memory for its lane 0.
 //
 // Padding: rows past a target's end use the all-zero profile row and
 // columns past a query's end have score 0; in local mode such cells never
@@ -71,10 +71,11 @@ __host__ __device__ constexpr int kp_prof_words(int A) {
 
 // Resident blocks per SM requested from ptxas: what shared memory allows for
 // BLOSUM-sized alphabets (24 symbols + pad: (A+1) x 16K words of profile per
-// block plus 11.5 KB of static rings).
+// block plus 3.7 KB of static tables and rings; 51.2 KB for K = 32, so 4
+// blocks fit in the SM's 228 KB).
 template <int K>
 struct KPMinBlocks {
-  static constexpr int value = K <= 8 ? 8 : K <= 16 ? 6 : K <= 24 ? 4 : 3;
+  static constexpr int value = K <= 8 ? 8 : K <= 16 ? 6 : K <= 20 ? 5 : 4;
 };
 
 template <int K>
@@ -82,14 +83,13 @@ __global__ void __launch_bounds__(32 * kKpWarps, KPMinBlocks<K>::value) kp_kerne
   using Cell = CellS16x2;
   using T = uint32_t;
   constexpr int G = kKpG, W = G * K, kRing = 4 * G, CH = K / 4;  // CH: 4-column chunks per lane
-  static_assert(K % 8 == 0, "profile rows are 16-byte chunks");
+  static_assert(K % 4 == 0, "profile rows are 16-byte chunks of 4 columns");
   extern __shared__ __align__(16) uint32_t kp_prof[];
   // sigma transposed: sigT_s[c * 32 + x] = sigma(query code x, target code c);
   // rows c >= A and columns x >= A are 0 (x = 31 is the pad column)
   __shared__ __align__(16) int8_t sigT_s[32 * 32];
-  __shared__ uint32_t ring_s[kKpGroups][5 * G];  // row codes, mirrored ring
-  __shared__ uint2 in_ring_s[kKpGroups][64];
-  __shared__ uint2 out_ring_s[kKpGroups][64];
+  __shared__ uint8_t ring_s[kKpGroups][5 * G];  // row codes, mirrored ring
+  __shared__ uint2 in_ring_s[kKpGroups][2 * G];  // left edge: the current and the next batch
   __shared__ int task_s;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -98,9 +98,8 @@ __global__ void __launch_bounds__(32 * kKpWarps, KPMinBlocks<K>::value) kp_kerne
     const int c = i >> 5, x = i & 31;
     sigT_s[i] = (c < p.A && x < p.A) ? p.sigma[x * p.A + c] : (int8_t)0;
   }
-  uint32_t *ring = ring_s[grp];
+  uint8_t *ring = ring_s[grp];
   uint2 *in_ring = in_ring_s[grp];
-  uint2 *out_ring = out_ring_s[grp];
   int2 *bnd = p.bnd + (size_t)(blockIdx.x * kKpGroups + grp) * (size_t)p.bnd_stride;
   const int A = p.A, alpha = p.alpha, beta = p.beta;
   const T NB = Cell::splat(-beta), NAc = Cell::splat(-alpha);
@@ -164,21 +163,24 @@ __global__ void __launch_bounds__(32 * kKpWarps, KPMinBlocks<K>::value) kp_kerne
       // ---- row codes, refilled G rows ahead -----------------------------
       auto fill_batch = [&](int b) {
         const int r = b * G + 1 + t;
-        const uint32_t c = r <= len ? (uint32_t)p.t_codes[tstart + r - 1] : (uint32_t)A;
+        const uint8_t c = r <= len ? p.t_codes[tstart + r - 1] : (uint8_t)A;
         const int sl = r & (kRing - 1);
         ring[sl] = c;
         if (sl < G) ring[sl + kRing] = c;
       };
-      // left edge of the stage, batched (rows 16b+1 .. 16b+16)
+      // left edge of the stage, batched (rows 16b+1 .. 16b+16); batch b is
+      // loaded while lane 0 still reads batch b-1, and before lane 15
+      // overwrites those rows with this stage's right edge (15 rows later)
       auto load_edge = [&](int b) {
         if (s > 0) {
           const int r = b * G + 1 + t;
           if (r <= Rw) {
             const int2 v = bnd[r];
-            in_ring[(r - 1) & 63] = make_uint2((uint32_t)v.x, (uint32_t)v.y);
+            in_ring[(r - 1) & (2 * G - 1)] = make_uint2((uint32_t)v.x, (uint32_t)v.y);
           }
         }
       };
+      const bool edge_out = s + 1 < nstage;
       __syncwarp();
       fill_batch(0);
       fill_batch(1);
@@ -196,7 +198,7 @@ __global__ void __launch_bounds__(32 * kKpWarps, KPMinBlocks<K>::value) kp_kerne
           hl = Cell::splat(0);
           fl = NAc;
         } else {
-          const uint2 v = in_ring[(r - 1) & 63];
+          const uint2 v = in_ring[(r - 1) & (2 * G - 1)];
           hl = v.x;
           fl = v.y;
         }
@@ -211,11 +213,6 @@ __global__ void __launch_bounds__(32 * kKpWarps, KPMinBlocks<K>::value) kp_kerne
           __syncwarp();
           fill_batch(it / G + 2);
           load_edge(it / G + 1);
-          if (it >= 2 * G) {  // flush lane 15's rows it-31 .. it-16
-            const int r = it - 2 * G + 1 + t;
-            const uint2 v = out_ring[(r - 1) & 63];
-            bnd[r] = make_int2((int)v.x, (int)v.y);
-          }
           __syncwarp();
         }
         const int r = it - t + 1;
@@ -232,7 +229,7 @@ __global__ void __launch_bounds__(32 * kKpWarps, KPMinBlocks<K>::value) kp_kerne
           Fout = dp_row<Cell, kModeLocal, K>(
               H, E, Hdiag, Fin, NB, best, [&](int j) -> T { return w[j]; }, [&](int) -> T { return NAc; });
           Hout = H[K - 1];
-          if (t == G - 1) out_ring[(r - 1) & 63] = make_uint2(Hout, Fout);
+          if (t == G - 1 && edge_out) bnd[r] = make_int2((int)Hout, (int)Fout);
         }
         Hdiag = Hleft;
         Hleft = __shfl_up_sync(0xffffffffu, Hout, 1, G);
@@ -245,15 +242,7 @@ __global__ void __launch_bounds__(32 * kKpWarps, KPMinBlocks<K>::value) kp_kerne
           }
         }
       }
-      __syncwarp();
-      if (s + 1 < nstage) {  // flush the remaining rows of the edge
-        const int first = (nit - 1 >= 2 * G) ? ((nit - 1) / G) * G - 2 * G + 1 + G : 1;
-        for (int r = first + t; r <= Rw; r += G) {
-          const uint2 v = out_ring[(r - 1) & 63];
-          bnd[r] = make_int2((int)v.x, (int)v.y);
-        }
-      }
-      __syncwarp();
+      __syncwarp();  // the edge stores are ordered before the next stage's loads
     }
 
     // ---- scores ----------------------------------------------------------

@@ -300,11 +300,13 @@ def _subset(b, idx):
 
 def test_protein_cross_local_bins_and_stages():
     # queries in every column bin of the packed protein kernel (<= 128, 256,
-    # 384, 512 columns) and longer ones that run in stages of 512 columns;
+    # 320, 384, 448, 512 columns), both sides of each bin edge, and longer
+    # ones that run in stages; queries of a bin are paired by length, so some
+    # pairs mix stage counts and odd bins leave a half without a query;
     # targets from empty to long, one with an invalid residue
     rng = np.random.default_rng(12)
     bg = np.concatenate([synth.PROTEIN_BACKGROUND, np.zeros(4)])
-    qlens = [0, 1, 50, 128, 129, 256, 300, 384, 385, 512, 513, 700, 1100]
+    qlens = [0, 1, 50, 128, 129, 256, 257, 300, 320, 321, 384, 385, 448, 449, 512, 513, 700, 1100]
     tlens = list(rng.integers(1, 900, size=150)) + [0, 1, 2, 2000]
     qs = [rng.choice(24, size=n, p=bg).astype(np.uint8) for n in qlens]
     ts = [rng.choice(24, size=int(n), p=bg).astype(np.uint8) for n in tlens]
