@@ -383,214 +383,302 @@ struct DpFork {
   }
 };
 
-// Plan, sort and run one chunk of pairs.  nt == 0: pair p = (q_p, t_p);
-// nt > 0: pair p = (query q0 + p / nt, target p % nt).
-int run_chunk(Call &c, const SetView &Q, const SetView &T, int64_t npairs, int64_t nt, int64_t q0,
-              int32_t *scores, int force_long, uint32_t *keys, int4 *info, int32_t *sorted,
-              int32_t *rerun_list) {
-  if (npairs == 0) return GA_OK;
-  if (cudaMemsetAsync(c.hist, 0, sizeof(int32_t) * kNumKeys, c.s) != cudaSuccess) return GA_ERR_CUDA;
-  if (cudaMemsetAsync(&c.small->counters, 0, sizeof(c.small->counters) + sizeof(c.small->rerun_range),
-                      c.s) != cudaSuccess)
+// One plan of a chunk of pairs in one mode.  nt == 0: pair p = (q_p, t_p);
+// nt > 0: pair p = (query q0 + p / nt, target p % nt).  Its device state (the
+// (class, bin) ranges, task counters and rerun range in `sm`, the sort
+// buffers) is its own, so several plans can be enqueued, read back with one
+// synchronisation and launched together; the status word and the cell count
+// are the call's.
+struct ChunkPlan {
+  int mode = 0;
+  int64_t npairs = 0, nt = 0, q0 = 0;
+  int32_t *scores = nullptr;
+  int force_long = 0;
+  Small *sm = nullptr;
+  int32_t *hist = nullptr, *cursor = nullptr;
+  uint32_t *keys = nullptr;
+  int4 *info = nullptr;
+  int32_t *sorted = nullptr, *rerun = nullptr;
+  Readback r{};
+  int nlaunch = 0, counter = 0;
+  // the long class (warp-per-pair stages)
+  int long_cnt = 0, long_grid = 0;
+  int64_t long_stride = 0;
+  size_t long_smem = 0;
+  int2 *long_bnd = nullptr;
+};
+
+// Plan and sort kernels of one plan, on the call's stream.
+int plan_enqueue(Call &c, const SetView &Q, const SetView &T, ChunkPlan &p) {
+  if (p.npairs == 0) return GA_OK;
+  if (cudaMemsetAsync(p.hist, 0, sizeof(int32_t) * kNumKeys, c.s) != cudaSuccess) return GA_ERR_CUDA;
+  if (cudaMemsetAsync(&p.sm->counters, 0, sizeof(p.sm->counters) + sizeof(p.sm->rerun_range), c.s) !=
+      cudaSuccess)
     return GA_ERR_CUDA;
-  if (cudaMemsetAsync(&c.small->rmax_long, 0, sizeof(int32_t), c.s) != cudaSuccess) return GA_ERR_CUDA;
+  if (cudaMemsetAsync(&p.sm->rmax_long, 0, sizeof(int32_t), c.s) != cudaSuccess) return GA_ERR_CUDA;
 
   PlanParams pp{};
   pp.q_off = Q.off;
   pp.t_off = T.off;
-  pp.npairs = npairs;
-  pp.nt = nt;
-  pp.q0 = q0;
+  pp.npairs = p.npairs;
+  pp.nt = p.nt;
+  pp.q0 = p.q0;
   pp.qbad = Q.bad;
   pp.tbad = T.bad;
   pp.A = c.sc.A;
-  pp.mode = c.mode;
+  pp.mode = p.mode;
   pp.alpha = c.sc.alpha;
   pp.beta = c.sc.beta;
   pp.sigma_max = c.sc.smax;
   pp.sigma_min = c.sc.smin;
-  pp.dna = c.dna && !force_long;
+  pp.dna = c.dna && !p.force_long;
   pp.bins = make_bins();
-  pp.scores = scores;
-  pp.keys = keys;
-  pp.info = info;
+  pp.scores = p.scores;
+  pp.keys = p.keys;
+  pp.info = p.info;
   pp.status = &c.small->status;
   pp.cells = &c.small->cells;
-  pp.rmax_long = &c.small->rmax_long;
+  pp.rmax_long = &p.sm->rmax_long;
   const unsigned tb = 256;
-  const unsigned nb = (unsigned)((npairs + tb - 1) / tb);
+  const unsigned nb = (unsigned)((p.npairs + tb - 1) / tb);
   plan_kernel<<<nb, tb, 0, c.s>>>(pp);
-  hist_kernel<<<nb, tb, 0, c.s>>>(keys, npairs, c.hist);
-  scan_partials_kernel<<<kScanTiles, kScanTile, 0, c.s>>>(c.hist, c.small->scan_partials);
-  scan_apply_kernel<<<kScanTiles, kScanTile, 0, c.s>>>(c.hist, c.small->scan_partials, c.cursor,
-                                                       c.small->ranges);
-  scatter_kernel<<<nb, tb, 0, c.s>>>(keys, npairs, c.cursor, sorted);
+  hist_kernel<<<nb, tb, 0, c.s>>>(p.keys, p.npairs, p.hist);
+  scan_partials_kernel<<<kScanTiles, kScanTile, 0, c.s>>>(p.hist, p.sm->scan_partials);
+  scan_apply_kernel<<<kScanTiles, kScanTile, 0, c.s>>>(p.hist, p.sm->scan_partials, p.cursor, p.sm->ranges);
+  scatter_kernel<<<nb, tb, 0, c.s>>>(p.keys, p.npairs, p.cursor, p.sorted);
   c.launches += 5;
-  if (cudaGetLastError() != cudaSuccess) return GA_ERR_CUDA;
+  return cudaGetLastError() == cudaSuccess ? GA_OK : GA_ERR_CUDA;
+}
 
+// Bin populations and longest long-class pair of n plans: one copy each,
+// one synchronisation.
+int plan_readback(Call &c, ChunkPlan *ps, int n) {
+  static_assert(8 * sizeof(Readback) <= 4096, "pinned scratch holds the readbacks of 8 plans");
   Readback *rb = (Readback *)pinned_scratch();
-  if (cudaMemcpyAsync(rb, c.small, sizeof(Readback), cudaMemcpyDeviceToHost, c.s) != cudaSuccess ||
-      cudaStreamSynchronize(c.s) != cudaSuccess)
-    return GA_ERR_CUDA;
-  Readback r = *rb;
+  bool any = false;
+  for (int k = 0; k < n; ++k) {
+    if (ps[k].npairs == 0) continue;
+    if (cudaMemcpyAsync(rb + k, ps[k].sm, sizeof(Readback), cudaMemcpyDeviceToHost, c.s) != cudaSuccess)
+      return GA_ERR_CUDA;
+    any = true;
+  }
+  if (any && cudaStreamSynchronize(c.s) != cudaSuccess) return GA_ERR_CUDA;
+  for (int k = 0; k < n; ++k)
+    if (ps[k].npairs > 0) ps[k].r = rb[k];
+  return GA_OK;
+}
 
+int plan_bin_count(const ChunkPlan &p, int cls, int bin) {
+  const int key = cls * kBins + bin;
+  return p.r.ranges[2 * key + 1] - p.r.ranges[2 * key];
+}
+
+// Launch count, long-class grid and edge buffer of a read-back plan.  The
+// buffer is allocated here, before the fork: the side streams start after it.
+int launch_prepare(Call &c, ChunkPlan &p) {
+  p.nlaunch = 0;
+  p.counter = 0;
+  if (p.npairs == 0) return GA_OK;
+  p.long_cnt = plan_bin_count(p, kClassLong, 0);
+  p.nlaunch = p.long_cnt > 0;
+  for (int cls = 0; cls < 2; ++cls)
+    for (int bin = 0; bin < kKaNumBins; ++bin) p.nlaunch += plan_bin_count(p, cls, bin) > 0;
+  const bool profile = !c.dna;
+  p.long_smem = profile ? (size_t)kKbWarps * (size_t)(c.sc.A + 1) * (32 * kKbK) : 0;
+  if (p.long_cnt > 0) {
+    int occ = 0;
+    if (profile)
+      occ = p.mode == GA_LOCAL ? blocks_per_sm_kb_local_prof(p.long_smem)
+          : p.mode == GA_GLOBAL ? blocks_per_sm_kb_global_prof(p.long_smem)
+                                : blocks_per_sm_kb_semi_prof(p.long_smem);
+    else
+      occ = p.mode == GA_LOCAL ? blocks_per_sm_kb_local_sel(p.long_smem)
+          : p.mode == GA_GLOBAL ? blocks_per_sm_kb_global_sel(p.long_smem)
+                                : blocks_per_sm_kb_semi_sel(p.long_smem);
+    const int64_t want = (p.long_cnt + kKbWarps - 1) / kKbWarps;
+    p.long_grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)c.nsm * std::max(occ, 1)));
+    p.long_stride = (int64_t)p.r.rmax_long + 128;
+    p.long_bnd = c.al.get<int2>((size_t)p.long_grid * kKbWarps * (size_t)p.long_stride);
+    if (c.al.failed) return GA_ERR_OOM;
+  }
+  return GA_OK;
+}
+
+KAParams make_ka(Call &c, const SetView &Q, const SetView &T, const ChunkPlan &p) {
   KAParams ka{};
   ka.packed_q = Q.packed;
   ka.packed_t = T.packed;
   ka.q_off = Q.off;
   ka.t_off = T.off;
-  ka.info = info;
-  ka.sorted = sorted;
+  ka.info = p.info;
+  ka.sorted = p.sorted;
   std::memcpy(ka.tables, c.sc.tables, sizeof(ka.tables));
   ka.alpha = c.sc.alpha;
   ka.beta = c.sc.beta;
   ka.sigma_max_pos = std::max(c.sc.smax, 0);
-  ka.scores = scores;
-  ka.rerun_list = rerun_list;
-  ka.rerun_count = &c.small->rerun_range[1];
-  ka.nt = nt;
-  ka.q0 = q0;
+  ka.scores = p.scores;
+  ka.rerun_list = p.rerun;
+  ka.rerun_count = &p.sm->rerun_range[1];
+  ka.nt = p.nt;
+  ka.q0 = p.q0;
+  return ka;
+}
 
-  // launches of this chunk: the non-empty bins and the long class
-  const int long_key = kClassLong * kBins;
-  const int long_cnt = r.ranges[2 * long_key + 1] - r.ranges[2 * long_key];
-  int nlaunch = long_cnt > 0;
-  for (int cls = 0; cls < 2; ++cls)
-    for (int bin = 0; bin < kKaNumBins; ++bin)
-      nlaunch += r.ranges[2 * (cls * kBins + bin) + 1] > r.ranges[2 * (cls * kBins + bin)];
-  const bool profile = !c.dna;
-  const size_t long_smem = profile ? (size_t)kKbWarps * (size_t)(c.sc.A + 1) * (32 * kKbK) : 0;
-  int long_grid = 0;
-  int64_t long_stride = 0;
-  int2 *long_bnd = nullptr;
-  if (long_cnt > 0) {  // allocated before the fork: the side streams start after it
-    int occ = 0;
-    if (profile)
-      occ = c.mode == GA_LOCAL ? blocks_per_sm_kb_local_prof(long_smem)
-          : c.mode == GA_GLOBAL ? blocks_per_sm_kb_global_prof(long_smem)
-                                : blocks_per_sm_kb_semi_prof(long_smem);
-    else
-      occ = c.mode == GA_LOCAL ? blocks_per_sm_kb_local_sel(long_smem)
-          : c.mode == GA_GLOBAL ? blocks_per_sm_kb_global_sel(long_smem)
-                                : blocks_per_sm_kb_semi_sel(long_smem);
-    const int64_t want = (long_cnt + kKbWarps - 1) / kKbWarps;
-    long_grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)c.nsm * std::max(occ, 1)));
-    long_stride = (int64_t)r.rmax_long + 128;
-    long_bnd = c.al.get<int2>((size_t)long_grid * kKbWarps * (size_t)long_stride);
-    if (c.al.failed) return GA_ERR_OOM;
+// The inter-sequence launch of one (class, bin) of a plan, if it is populated.
+int launch_bin(Call &c, const SetView &Q, const SetView &T, ChunkPlan &p, int cls, int bin, DpFork &fk) {
+  if (p.npairs == 0) return GA_OK;
+  const int cnt = plan_bin_count(p, cls, bin);
+  if (cnt <= 0) return GA_OK;
+  (cls == 0 ? c.pairs16 : c.pairs32) += cnt;
+  KAParams ka = make_ka(c, Q, T, p);
+  ka.range = &p.sm->ranges[2 * (cls * kBins + bin)];
+  ka.task_counter = &p.sm->counters[p.counter++];
+  const int ppt = (cls == 0 ? 2 : 1) * (32 / kKaG);
+  const int64_t ntasks = (cnt + ppt - 1) / ppt;
+  int occ;
+  if (cls == 0) {
+    occ = p.mode == GA_LOCAL ? blocks_per_sm_ka16_local(bin)
+        : p.mode == GA_GLOBAL ? blocks_per_sm_ka16_global(bin)
+                              : blocks_per_sm_ka16_semi(bin);
+  } else {
+    occ = p.mode == GA_LOCAL ? blocks_per_sm_ka32_local(bin)
+        : p.mode == GA_GLOBAL ? blocks_per_sm_ka32_global(bin)
+                              : blocks_per_sm_ka32_semi(bin);
   }
+  const int64_t want = (ntasks + (kKaThreads / 32) - 1) / (kKaThreads / 32);
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)c.nsm * std::max(occ, 1)));
+  cudaError_t e;
+  const cudaStream_t ls = fk.launch_begin();
+  if (cls == 0) {
+    e = p.mode == GA_LOCAL ? launch_ka16_local(bin, ka, grid, ls)
+      : p.mode == GA_GLOBAL ? launch_ka16_global(bin, ka, grid, ls)
+                            : launch_ka16_semi(bin, ka, grid, ls);
+  } else {
+    e = p.mode == GA_LOCAL ? launch_ka32_local(bin, ka, grid, ls)
+      : p.mode == GA_GLOBAL ? launch_ka32_global(bin, ka, grid, ls)
+                            : launch_ka32_semi(bin, ka, grid, ls);
+  }
+  fk.launch_end();
+  return e == cudaSuccess ? GA_OK : GA_ERR_CUDA;
+}
+
+// Long pairs (and every pair of an alphabet of more than 4 symbols) of a plan.
+int launch_long(Call &c, const SetView &Q, const SetView &T, ChunkPlan &p, DpFork &fk) {
+  if (p.npairs == 0 || p.long_cnt <= 0) return GA_OK;
+  const bool profile = !c.dna;
+  c.pairs32 += p.long_cnt;
+  KBParams kb{};
+  kb.packed_q = Q.packed;
+  kb.packed_t = T.packed;
+  kb.q_codes = Q.codes;
+  kb.t_codes = T.codes;
+  kb.q_off = Q.off;
+  kb.t_off = T.off;
+  kb.info = p.info;
+  kb.sorted = p.sorted;
+  kb.range = &p.sm->ranges[2 * (kClassLong * kBins)];
+  kb.task_counter = &p.sm->counters[p.counter++];
+  std::memcpy(kb.tables, c.sc.tables, sizeof(kb.tables));
+  std::memcpy(kb.sigma, c.sc.mat, sizeof(kb.sigma));
+  kb.A = c.sc.A;
+  kb.alpha = c.sc.alpha;
+  kb.beta = c.sc.beta;
+  kb.scores = p.scores;
+  kb.bnd = p.long_bnd;
+  kb.bnd_stride = p.long_stride;
+  kb.nt = p.nt;
+  kb.q0 = p.q0;
+  cudaError_t e;
+  const cudaStream_t ls = fk.launch_begin();
+  if (profile)
+    e = p.mode == GA_LOCAL ? launch_kb_local_prof(kb, p.long_grid, p.long_smem, ls)
+      : p.mode == GA_GLOBAL ? launch_kb_global_prof(kb, p.long_grid, p.long_smem, ls)
+                            : launch_kb_semi_prof(kb, p.long_grid, p.long_smem, ls);
+  else
+    e = p.mode == GA_LOCAL ? launch_kb_local_sel(kb, p.long_grid, p.long_smem, ls)
+      : p.mode == GA_GLOBAL ? launch_kb_global_sel(kb, p.long_grid, p.long_smem, ls)
+                            : launch_kb_semi_sel(kb, p.long_grid, p.long_smem, ls);
+  fk.launch_end();
+  return e == cudaSuccess ? GA_OK : GA_ERR_CUDA;
+}
+
+// DP launches of n read-back plans in one fork / join: the inter-sequence
+// bins widest tile first (the plans' bins of one width together), so the
+// narrow tiles of every plan fill the tail, then the long classes.
+int launch_plans(Call &c, const SetView &Q, const SetView &T, ChunkPlan *ps, int n) {
+  int nlaunch = 0;
+  for (int k = 0; k < n; ++k) nlaunch += ps[k].nlaunch;
   DpFork fk(c);
   if (int rc = fk.begin(nlaunch)) return rc;
+  for (int cls = 1; cls >= 0; --cls)
+    for (int bin = kKaNumBins - 1; bin >= 0; --bin)
+      for (int k = 0; k < n; ++k)
+        if (int rc = launch_bin(c, Q, T, ps[k], cls, bin, fk)) return rc;
+  for (int k = 0; k < n; ++k)
+    if (int rc = launch_long(c, Q, T, ps[k], fk)) return rc;
+  return fk.end();
+}
 
-  int counter = 0;
-  for (int cls = 1; cls >= 0; --cls) {  // widest tiles first
-    for (int bin = kKaNumBins - 1; bin >= 0; --bin) {
-      const int key = cls * kBins + bin;
-      const int cnt = r.ranges[2 * key + 1] - r.ranges[2 * key];
-      if (cnt <= 0) continue;
-      (cls == 0 ? c.pairs16 : c.pairs32) += cnt;
-      ka.range = &c.small->ranges[2 * key];
-      ka.task_counter = &c.small->counters[counter++];
-      const int ppt = (cls == 0 ? 2 : 1) * (32 / kKaG);
-      const int64_t ntasks = (cnt + ppt - 1) / ppt;
-      int occ;
-      if (cls == 0) {
-        occ = c.mode == GA_LOCAL ? blocks_per_sm_ka16_local(bin)
-            : c.mode == GA_GLOBAL ? blocks_per_sm_ka16_global(bin)
-                                  : blocks_per_sm_ka16_semi(bin);
-      } else {
-        occ = c.mode == GA_LOCAL ? blocks_per_sm_ka32_local(bin)
-            : c.mode == GA_GLOBAL ? blocks_per_sm_ka32_global(bin)
-                                  : blocks_per_sm_ka32_semi(bin);
-      }
-      const int64_t want = (ntasks + (kKaThreads / 32) - 1) / (kKaThreads / 32);
-      const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)c.nsm * std::max(occ, 1)));
-      cudaError_t e;
-      const cudaStream_t ls = fk.launch_begin();
-      if (cls == 0) {
-        e = c.mode == GA_LOCAL ? launch_ka16_local(bin, ka, grid, ls)
-          : c.mode == GA_GLOBAL ? launch_ka16_global(bin, ka, grid, ls)
-                                : launch_ka16_semi(bin, ka, grid, ls);
-      } else {
-        e = c.mode == GA_LOCAL ? launch_ka32_local(bin, ka, grid, ls)
-          : c.mode == GA_GLOBAL ? launch_ka32_global(bin, ka, grid, ls)
-                                : launch_ka32_semi(bin, ka, grid, ls);
-      }
-      fk.launch_end();
-      if (e != cudaSuccess) return GA_ERR_CUDA;
-    }
-  }
+// Exact int32 rerun of local int16 pairs whose running max reached the
+// int16 limit (queued by the int16x2 kernels on the device); after the join.
+int rerun_enqueue(Call &c, const SetView &Q, const SetView &T, ChunkPlan &p) {
+  if (p.npairs == 0 || p.mode != GA_LOCAL || !c.dna) return GA_OK;
+  int any16 = 0;
+  for (int bin = 0; bin < kKaNumBins; ++bin) any16 |= plan_bin_count(p, 0, bin) > 0;
+  if (!any16) return GA_OK;
+  range_from_count_kernel<<<1, 1, 0, c.s>>>(&p.sm->rerun_range[1], p.sm->rerun_range);
+  count_reruns_kernel<<<1, 1, 0, c.s>>>(p.sm->rerun_range, &c.small->rerun_total);
+  KAParams ka = make_ka(c, Q, T, p);
+  ka.sorted = p.rerun;
+  ka.range = p.sm->rerun_range;
+  ka.rerun_list = nullptr;
+  ka.rerun_count = nullptr;
+  ka.task_counter = &p.sm->counters[p.counter++];
+  const int bin = kKaNumBins - 1;
+  const int occ = blocks_per_sm_ka32_local(bin);
+  c.launches += 2;
+  c.dp_begin();
+  const cudaError_t e = launch_ka32_local(bin, ka, c.nsm * std::max(occ, 1), c.s);
+  c.dp_end();
+  return e == cudaSuccess ? GA_OK : GA_ERR_CUDA;
+}
 
-  // Long pairs (and every pair of an alphabet of more than 4 symbols).
-  {
-    const int key = long_key;
-    const int cnt = long_cnt;
-    if (cnt > 0) {
-      c.pairs32 += cnt;
-      const size_t smem = long_smem;
-      const int grid = long_grid;
-      const int64_t stride = long_stride;
-      int2 *bnd = long_bnd;
-      KBParams kb{};
-      kb.packed_q = Q.packed;
-      kb.packed_t = T.packed;
-      kb.q_codes = Q.codes;
-      kb.t_codes = T.codes;
-      kb.q_off = Q.off;
-      kb.t_off = T.off;
-      kb.info = info;
-      kb.sorted = sorted;
-      kb.range = &c.small->ranges[2 * key];
-      kb.task_counter = &c.small->counters[counter++];
-      std::memcpy(kb.tables, c.sc.tables, sizeof(kb.tables));
-      std::memcpy(kb.sigma, c.sc.mat, sizeof(kb.sigma));
-      kb.A = c.sc.A;
-      kb.alpha = c.sc.alpha;
-      kb.beta = c.sc.beta;
-      kb.scores = scores;
-      kb.bnd = bnd;
-      kb.bnd_stride = stride;
-      kb.nt = nt;
-      kb.q0 = q0;
-      cudaError_t e;
-      const cudaStream_t ls = fk.launch_begin();
-      if (profile)
-        e = c.mode == GA_LOCAL ? launch_kb_local_prof(kb, grid, smem, ls)
-          : c.mode == GA_GLOBAL ? launch_kb_global_prof(kb, grid, smem, ls)
-                                : launch_kb_semi_prof(kb, grid, smem, ls);
-      else
-        e = c.mode == GA_LOCAL ? launch_kb_local_sel(kb, grid, smem, ls)
-          : c.mode == GA_GLOBAL ? launch_kb_global_sel(kb, grid, smem, ls)
-                                : launch_kb_semi_sel(kb, grid, smem, ls);
-      fk.launch_end();
-      if (e != cudaSuccess) return GA_ERR_CUDA;
-    }
-  }
-  if (int rc = fk.end()) return rc;
-
-  // Exact int32 rerun of local int16 pairs whose running max reached the
-  // int16 limit (queued by the int16x2 kernels on the device).
-  if (c.mode == GA_LOCAL && c.dna) {
-    int any16 = 0;
-    for (int bin = 0; bin < kKaNumBins; ++bin) any16 |= r.ranges[2 * bin + 1] > r.ranges[2 * bin];
-    if (any16) {
-      range_from_count_kernel<<<1, 1, 0, c.s>>>(&c.small->rerun_range[1], c.small->rerun_range);
-      count_reruns_kernel<<<1, 1, 0, c.s>>>(c.small->rerun_range, &c.small->rerun_total);
-      ka.sorted = rerun_list;
-      ka.range = c.small->rerun_range;
-      ka.rerun_list = nullptr;
-      ka.rerun_count = nullptr;
-      ka.task_counter = &c.small->counters[counter++];
-      const int bin = kKaNumBins - 1;
-      const int occ = blocks_per_sm_ka32_local(bin);
-      c.launches += 2;
-      c.dp_begin();
-      const cudaError_t e = launch_ka32_local(bin, ka, c.nsm * std::max(occ, 1), c.s);
-      c.dp_end();
-      if (e != cudaSuccess) return GA_ERR_CUDA;
-    }
-  }
+// Plan, read back, launch and rerun several plans of the same pairs (one per
+// mode) as one unit: nothing waits for the host between them.
+int run_plans(Call &c, const SetView &Q, const SetView &T, ChunkPlan *ps, int n) {
+  int rc;
+  for (int k = 0; k < n; ++k)
+    if ((rc = plan_enqueue(c, Q, T, ps[k]))) return rc;
+  if ((rc = plan_readback(c, ps, n))) return rc;
+  for (int k = 0; k < n; ++k)
+    if ((rc = launch_prepare(c, ps[k]))) return rc;
+  if ((rc = launch_plans(c, Q, T, ps, n))) return rc;
+  for (int k = 0; k < n; ++k)
+    if ((rc = rerun_enqueue(c, Q, T, ps[k]))) return rc;
   return GA_OK;
+}
+
+// Plan, sort and run one chunk of pairs in the call's mode, with the call's
+// own plan state.
+int run_chunk(Call &c, const SetView &Q, const SetView &T, int64_t npairs, int64_t nt, int64_t q0,
+              int32_t *scores, int force_long, uint32_t *keys, int4 *info, int32_t *sorted,
+              int32_t *rerun_list) {
+  if (npairs == 0) return GA_OK;
+  ChunkPlan p;
+  p.mode = c.mode;
+  p.npairs = npairs;
+  p.nt = nt;
+  p.q0 = q0;
+  p.scores = scores;
+  p.force_long = force_long;
+  p.sm = c.small;
+  p.hist = c.hist;
+  p.cursor = c.cursor;
+  p.keys = keys;
+  p.info = info;
+  p.sorted = sorted;
+  p.rerun = rerun_list;
+  return run_plans(c, Q, T, &p, 1);
 }
 
 int finish(Call &c, ga_stats *st, cudaEvent_t e0, cudaEvent_t e1, int64_t pairs) {
@@ -654,17 +742,26 @@ int batch_modes_impl(const uint8_t *q_codes, const int64_t *q_off, const uint8_t
   SetView Q{q_codes, q_off, nullptr, nullptr}, T{t_codes, t_off, nullptr, nullptr};
   if ((rc = prepare_set(c, q_codes, q_off, npairs, &Q.packed, &Q.bad, &c.small->invalid_q, qr))) return rc;
   if ((rc = prepare_set(c, t_codes, t_off, npairs, &T.packed, &T.bad, &c.small->invalid_t, tr))) return rc;
-  uint32_t *keys = c.al.get<uint32_t>((size_t)npairs);
-  int4 *info = c.al.get<int4>((size_t)npairs);
-  int32_t *sorted = c.al.get<int32_t>((size_t)npairs);
-  int32_t *rerun = c.al.get<int32_t>((size_t)npairs);
-  if (c.al.failed) return GA_ERR_OOM;
+  // one plan per mode (own sort buffers and plan state), all read back with
+  // one synchronisation and launched in one fork / join
+  ChunkPlan ps[8];
   for (int k = 0; k < nmodes; ++k) {
-    c.mode = modes[k];
-    if ((rc = run_chunk(c, Q, T, npairs, 0, 0, scores + (size_t)k * (size_t)score_stride, force_long, keys, info,
-                        sorted, rerun)))
-      return rc;
+    ChunkPlan &p = ps[k];
+    p.mode = modes[k];
+    p.npairs = npairs;
+    p.scores = scores + (size_t)k * (size_t)score_stride;
+    p.force_long = force_long;
+    p.sm = k == 0 ? c.small : c.al.get<Small>(1);
+    p.hist = k == 0 ? c.hist : c.al.get<int32_t>(kNumKeys);
+    p.cursor = k == 0 ? c.cursor : c.al.get<int32_t>(kNumKeys);
+    p.keys = c.al.get<uint32_t>((size_t)npairs);
+    p.info = c.al.get<int4>((size_t)npairs);
+    p.sorted = c.al.get<int32_t>((size_t)npairs);
+    p.rerun = c.al.get<int32_t>((size_t)npairs);
+    if (c.al.failed) return GA_ERR_OOM;
+    if (k > 0 && cudaMemsetAsync(p.sm, 0, sizeof(Small), c.s) != cudaSuccess) return GA_ERR_CUDA;
   }
+  if ((rc = run_plans(c, Q, T, ps, nmodes))) return rc;
   return finish(c, stats, ev.e0, ev.e1, npairs * nmodes);
 }
 
