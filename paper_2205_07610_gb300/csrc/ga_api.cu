@@ -1646,8 +1646,11 @@ static int batch_host_impl(const uint8_t *q_codes, const int64_t *q_off, const u
   const int64_t qn = q_off[npairs], tn = t_off[npairs];
   if (qn < 0 || tn < 0 || q_off[0] < 0 || t_off[0] < 0 || q_off[0] > qn || t_off[0] > tn) return GA_ERR_ARG;
   // Chunks of pairs: the copies of every chunk go in order on a copy stream,
-  // the alignment of chunk k on `stream` waits only for chunk k's copy, and
-  // its scores go back as soon as it is done, so copies and alignment overlap.
+  // the alignment of chunk k waits only for chunk k's copy, and its scores go
+  // back as soon as it is done, so copies and alignment overlap.  Chunk k
+  // runs on plan stream k % 2: the readback of its bin populations then waits
+  // for chunk k-2 only, so the host enqueues chunk k's kernels while chunk
+  // k-1's still run, and the device never drains between chunks.
   const int64_t kChunkPairs = 1 << 18;
   const int nchunk = (int)std::min<int64_t>(8, std::max<int64_t>(1, (npairs + kChunkPairs - 1) / kChunkPairs));
   // geometric chunk sizes (1, 2, 4, ... parts): the first alignment starts
@@ -1660,14 +1663,16 @@ static int batch_host_impl(const uint8_t *q_codes, const int64_t *q_off, const u
   uint8_t *dq = nullptr, *dt = nullptr;
   int64_t *dqo = nullptr, *dto = nullptr;
   int32_t *ds = nullptr;
-  cudaStream_t cs = nullptr;
+  cudaStream_t cs = nullptr, pst[2] = {nullptr, nullptr};
   std::vector<cudaEvent_t> ev_in((size_t)nchunk, nullptr), ev_done((size_t)nchunk, nullptr);
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   auto cleanup = [&]() {
     cudaFreeAsync(dq, s); cudaFreeAsync(dt, s); cudaFreeAsync(dqo, s);
     cudaFreeAsync(dto, s); cudaFreeAsync(ds, s);
   };
-  bool ok = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) == cudaSuccess;
+  bool ok = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) == cudaSuccess &&
+            cudaStreamCreateWithFlags(&pst[0], cudaStreamNonBlocking) == cudaSuccess &&
+            cudaStreamCreateWithFlags(&pst[1], cudaStreamNonBlocking) == cudaSuccess;
   for (int k = 0; ok && k < nchunk; ++k)
     ok = cudaEventCreateWithFlags(&ev_in[k], cudaEventDisableTiming) == cudaSuccess &&
          cudaEventCreateWithFlags(&ev_done[k], cudaEventDisableTiming) == cudaSuccess;
@@ -1680,7 +1685,9 @@ static int batch_host_impl(const uint8_t *q_codes, const int64_t *q_off, const u
     rc = GA_ERR_OOM;
   cudaEvent_t ready = nullptr;  // the allocations above are ordered on `s`
   if (!rc && (cudaEventCreateWithFlags(&ready, cudaEventDisableTiming) != cudaSuccess ||
-              cudaEventRecord(ready, s) != cudaSuccess || cudaStreamWaitEvent(cs, ready, 0) != cudaSuccess))
+              cudaEventRecord(ready, s) != cudaSuccess || cudaStreamWaitEvent(cs, ready, 0) != cudaSuccess ||
+              cudaStreamWaitEvent(pst[0], ready, 0) != cudaSuccess ||
+              cudaStreamWaitEvent(pst[1], ready, 0) != cudaSuccess))
     rc = GA_ERR_CUDA;
   if (!rc && stats) {
     cudaEventCreate(&e0);
@@ -1706,7 +1713,8 @@ static int batch_host_impl(const uint8_t *q_codes, const int64_t *q_off, const u
   ga_stats tot{};
   for (int k = 0; !rc && k < nchunk; ++k) {
     const int64_t a = cut[k], b = cut[k + 1];
-    if (cudaStreamWaitEvent(s, ev_in[k], 0) != cudaSuccess) {
+    cudaStream_t pk = pst[k & 1];
+    if (cudaStreamWaitEvent(pk, ev_in[k], 0) != cudaSuccess) {
       rc = GA_ERR_CUDA;
       break;
     }
@@ -1718,7 +1726,7 @@ static int batch_host_impl(const uint8_t *q_codes, const int64_t *q_off, const u
     tr.total = t_off[b];
     {  // every mode on the chunk copied once (packed once)
       ga_stats st{};
-      rc = batch_modes_impl(dq, dqo + a, dt, dto + a, b - a, scoring, modes, nmodes, ds + a, npairs, stream,
+      rc = batch_modes_impl(dq, dqo + a, dt, dto + a, b - a, scoring, modes, nmodes, ds + a, npairs, pk,
                             stats ? &st : nullptr, 0, qr, tr);
       if (!rc && stats) {
         tot.cells += st.cells; tot.pairs += st.pairs; tot.pairs_int16 += st.pairs_int16;
@@ -1728,19 +1736,25 @@ static int batch_host_impl(const uint8_t *q_codes, const int64_t *q_off, const u
       }
     }
     if (rc) break;
-    if (cudaEventRecord(ev_done[k], s) != cudaSuccess || cudaStreamWaitEvent(cs, ev_done[k], 0) != cudaSuccess)
+    if (cudaEventRecord(ev_done[k], pk) != cudaSuccess || cudaStreamWaitEvent(cs, ev_done[k], 0) != cudaSuccess)
       rc = GA_ERR_CUDA;
     for (int md = 0; !rc && md < nmodes; ++md)
       if (cudaMemcpyAsync(scores + (size_t)md * npairs + a, ds + (size_t)md * npairs + a,
                           sizeof(int32_t) * (size_t)(b - a), cudaMemcpyDeviceToHost, cs) != cudaSuccess)
         rc = GA_ERR_CUDA;
   }
-  // the frees are ordered after the last score copy
-  cudaEvent_t copied = nullptr;
+  // the frees are ordered after the last score copy and everything on the
+  // plan streams (also on an error path)
+  cudaEvent_t copied = nullptr, tail[2] = {nullptr, nullptr};
   if (cudaEventCreateWithFlags(&copied, cudaEventDisableTiming) == cudaSuccess) {
     cudaEventRecord(copied, cs);
     cudaStreamWaitEvent(s, copied, 0);
   }
+  for (int i = 0; i < 2; ++i)
+    if (pst[i] && cudaEventCreateWithFlags(&tail[i], cudaEventDisableTiming) == cudaSuccess) {
+      cudaEventRecord(tail[i], pst[i]);
+      cudaStreamWaitEvent(s, tail[i], 0);
+    }
   if (e1) cudaEventRecord(e1, s);
   cleanup();
   if (cudaStreamSynchronize(s) != cudaSuccess && !rc) rc = GA_ERR_CUDA;
@@ -1755,9 +1769,11 @@ static int batch_host_impl(const uint8_t *q_codes, const int64_t *q_off, const u
   for (cudaEvent_t e : ev_done) if (e) cudaEventDestroy(e);
   if (ready) cudaEventDestroy(ready);
   if (copied) cudaEventDestroy(copied);
+  for (cudaEvent_t e : tail) if (e) cudaEventDestroy(e);
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
   if (cs) cudaStreamDestroy(cs);
+  for (cudaStream_t p : pst) if (p) cudaStreamDestroy(p);
   return rc;
 }
 
