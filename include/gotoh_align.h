@@ -39,7 +39,8 @@
  * been synchronised.  If `stats` is non-NULL the call synchronises the
  * stream before returning and fills it.  The batch and cross entry points
  * read the bin populations back once per call (a short synchronisation of
- * `stream` between planning and the DP kernels) and run the bins as
+ * `stream` between planning and the DP kernels; ga_align_batch_modes plans
+ * every mode first and reads all of them back at once) and run the bins as
  * concurrent kernels on four side streams of the library (created once per
  * device, forked from and joined back to `stream` with events).  Calls from
  * different host threads on different streams are safe; their DP kernels
@@ -153,10 +154,12 @@ int ga_align_batch_modes(const uint8_t *q_codes, const int64_t *q_off, const uin
  * (pinned memory gives the fastest copies).  The pairs are cut into up to 8
  * chunks of geometrically growing size (one chunk per 2^18 pairs, the
  * first the smallest); all inputs are copied in, chunk by chunk,
- * on a stream of the call's own while the chunks are aligned on `stream`,
- * each as soon as its inputs have arrived, and its scores copied back
- * behind it.  The call synchronises before returning; the host buffers may
- * be reused afterwards.  stats (nullable) sums the chunks' statistics;
+ * on a stream of the call's own while the chunks are aligned, each as soon
+ * as its inputs have arrived, on two planning streams of the call's own in
+ * turn (so that reading back one chunk's bin populations does not wait for
+ * the previous chunk's kernels), and its scores copied back behind it;
+ * `stream` waits for all of it.  The call synchronises before returning;
+ * the host buffers may be reused afterwards.  stats (nullable) sums the chunks' statistics;
  * kernel_ms is the device time of the whole call.
  */
 int ga_align_batch_host(const uint8_t *q_codes, const int64_t *q_off, const uint8_t *t_codes,
