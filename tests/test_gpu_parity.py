@@ -268,6 +268,51 @@ def test_batch_modes_entry_point():
     assert e.value.code == 1
 
 
+def test_batch_modes_overflow_errors_and_empty():
+    # one multi-mode call whose two local plans both queue int16 overflows
+    # for the int32 rerun, with empty sequences, long-class pairs and one
+    # invalid residue: every row equals the single-mode entry point
+    # (INT32_MIN for the invalid pair, status GA_ERR_RESIDUE), the valid
+    # pairs equal the oracle, and the host entry point gives the same rows
+    rng = np.random.default_rng(15)
+    lq = list(rng.integers(0, 520, size=300)) + [0, 5, 0, 513, 600]
+    lt = list(rng.integers(0, 520, size=300)) + [7, 0, 0, 600, 513]
+    qs = [rng.integers(0, 4, size=int(n)).astype(np.uint8) for n in lq]
+    ts = [rng.integers(0, 4, size=int(n)).astype(np.uint8) for n in lt]
+    for i, L in enumerate((330, 400, 480, 510)):  # identical: local score 100 L > 32767
+        qs[10 + i] = rng.integers(0, 4, size=L).astype(np.uint8)
+        ts[10 + i] = qs[10 + i].copy()
+    qs[40] = qs[40].copy()
+    qs[40][len(qs[40]) // 2] = 7  # outside the 4-symbol alphabet
+    assert len(qs[40]) > 0
+    qc, qo = synth.pack_csr(qs)
+    tc, to = synth.pack_csr(ts)
+    b = synth.Batch(qc, qo, tc, to, synth.dna_matrix(100, -90), 120, 60, "modes-errors")
+    q, qo_d, t, to_d = _dev(b)
+    modes = ["local", "global", "local", "semiglobal"]
+    got, st = ga.align_batch_modes(q, qo_d, t, to_d, b.matrix, 120, 60, modes, stats=True)
+    got = got.cpu().numpy()
+    assert st["status"] == 5 and st["pairs_int32_rerun"] >= 8
+    valid = np.ones(b.npairs, dtype=bool)
+    valid[40] = False
+    for k, mode in enumerate(modes):
+        assert_same(got[k], gpu_batch(b, mode), f"modes row {k} {mode} vs single mode")
+        assert got[k][40] == INT32_MIN
+        want, errs = oracle.batch(*_subset(b, np.nonzero(valid)[0]), b.matrix, 120, 60, mode, nthreads=NTHREADS)
+        assert not errs.any()
+        assert_same(got[k][valid], want, f"modes row {k} {mode} vs oracle")
+    assert oracle_batch_local_max(b, valid) > 32767
+    host, hst = ga.align_batch_host_modes(qc, qo, tc, to, b.matrix, 120, 60, modes, stats=True)
+    assert hst["status"] == 5
+    assert_same(host.ravel(), got.ravel(), "host modes vs device modes")
+
+
+def oracle_batch_local_max(b, valid):
+    want, _ = oracle.batch(*_subset(b, np.nonzero(valid)[0]), b.matrix, b.alpha, b.beta, "local",
+                           nthreads=NTHREADS)
+    return int(want.max())
+
+
 def test_host_modes_entry_point():
     # several modes of the same pairs from one host copy, over several copy
     # chunks; every row equals the device entry point in its mode, and the
