@@ -109,6 +109,31 @@ def global_scores(q, s, sigma, alpha, beta) -> np.ndarray:
     return np.einsum("kij,ij->k", match, sig) - gap_cost
 
 
+def global_table(Q: np.ndarray, S: np.ndarray, sigma, alpha, beta, chunk: int = 32) -> np.ndarray:
+    """Brute-force global scores of every pair of rows of Q (Nq x a codes)
+    and S (Ns x b codes), all of one length pair (a, b): the same explicit
+    alignment list as global_scores, scored for many pairs at once.
+    Returns an (Nq, Ns) int64 table."""
+    Q = np.asarray(Q, dtype=np.int64).reshape(len(Q), -1)
+    S = np.asarray(S, dtype=np.int64).reshape(len(S), -1)
+    a, b = Q.shape[1], S.shape[1]
+    match, runs, gaps = _tables(a, b)
+    gap_cost = alpha * runs + beta * (gaps - runs)
+    out = np.empty((len(Q), len(S)), dtype=np.int64)
+    if a == 0 or b == 0:
+        out[:] = -int(gap_cost.min())  # one alignment: every column a gap
+        return out
+    sig = np.asarray(sigma, dtype=np.int64)
+    mflat = match.reshape(len(match), a * b).T  # (a*b, K)
+    for c0 in range(0, len(Q), chunk):
+        qc = Q[c0:c0 + chunk]
+        # sigma(q_i, s_j) for every pair of the chunk: (nq, Ns, a, b)
+        pair_sig = sig[qc[:, None, :, None], S[None, :, None, :]]
+        scores = pair_sig.reshape(len(qc) * len(S), a * b) @ mflat - gap_cost[None, :]
+        out[c0:c0 + chunk] = scores.max(axis=1).reshape(len(qc), len(S))
+    return out
+
+
 def brute_global(q, s, sigma, alpha, beta) -> int:
     return int(global_scores(q, s, sigma, alpha, beta).max())
 

@@ -1,8 +1,8 @@
 """Pins of the CPU oracle against things other than itself (no GPU).
 
 * brute force: every alignment enumerated and scored from the definitions
-  (oracle/brute.py), exhaustively for tiny DNA inputs and on random DNA and
-  protein inputs up to length 6;
+  (oracle/brute.py), exhaustively for every pair of DNA strings of length
+  0..4 and on random DNA and protein inputs up to length 6;
 * closed forms: identical sequences, one empty sequence, AAAA vs CCCC;
 * an independent linear-gap DP (the paper's linear scheme) equals the affine
   oracle at alpha == beta;
@@ -56,6 +56,64 @@ def test_exhaustive_short_dna(mode, scheme):
         for s in seqs:
             assert oracle.score(q, s, sig, alpha, beta, mode) == \
                 brute.brute(q, s, sig, alpha, beta, mode), (q, s, mode)
+
+
+@pytest.mark.parametrize("scheme", SCHEMES[:2])
+def test_exhaustive_dna_up_to_4(scheme):
+    """Every pair of DNA strings of length 0..4 (341 strings, 116,281 pairs),
+    all three modes: the C oracle against brute force.  Global scores of
+    every pair of strings come from the explicit alignment enumeration
+    (vectorised over pairs); local and semi-global follow from them by their
+    definitions over substrings (Sec. 2.1): local = max(0, max over substring
+    pairs), semi-global = max over substrings that start on row or column 0
+    and end on row m or column n."""
+    (ma, mi), alpha, beta = scheme
+    sig = synth.dna_matrix(ma, mi)
+    by_len = [np.array(list(itertools.product(range(4), repeat=L)), dtype=np.uint8).reshape(4 ** L, L)
+              for L in range(5)]
+    base = np.cumsum([0] + [len(x) for x in by_len])  # id of string k of length L: base[L] + k
+    nstr = int(base[-1])
+    G = np.empty((nstr, nstr), dtype=np.int64)
+    for a in range(5):
+        for b in range(5):
+            G[base[a]:base[a + 1], base[b]:base[b + 1]] = brute.global_table(by_len[a], by_len[b], sig, alpha,
+                                                                           beta)
+
+    def sid(x):  # id of a code string
+        k = 0
+        for c in x:
+            k = 4 * k + int(c)
+        return int(base[len(x)]) + k
+
+    want = {m: np.empty((nstr, nstr), dtype=np.int64) for m in MODES}
+    for a in range(5):
+        for b in range(5):
+            qa, sb = by_len[a], by_len[b]
+            # substring ids of every string of the two lengths
+            subq = [(i0, i1) for i0 in range(a + 1) for i1 in range(i0, a + 1)]
+            subs = [(j0, j1) for j0 in range(b + 1) for j1 in range(j0, b + 1)]
+            Iq = np.array([[sid(x[i0:i1]) for (i0, i1) in subq] for x in qa])  # (Nq, nsubq)
+            Is = np.array([[sid(y[j0:j1]) for (j0, j1) in subs] for y in sb])  # (Ns, nsubs)
+            loc = np.zeros((len(qa), len(sb)), dtype=np.int64)
+            semi = np.full((len(qa), len(sb)), np.iinfo(np.int64).min, dtype=np.int64)
+            for u, (i0, i1) in enumerate(subq):
+                for v, (j0, j1) in enumerate(subs):
+                    g = G[Iq[:, u][:, None], Is[:, v][None, :]]
+                    loc = np.maximum(loc, g)
+                    if (i0 == 0 or j0 == 0) and (i1 == a or j1 == b):
+                        semi = np.maximum(semi, g)
+            sl = (slice(base[a], base[a + 1]), slice(base[b], base[b + 1]))
+            want["global"][sl] = G[sl]
+            want["local"][sl] = loc
+            want["semiglobal"][sl] = semi
+    strings = [x for L in range(5) for x in by_len[L]]
+    qc, qo = synth.pack_csr([x for x in strings for _ in strings])
+    tc, to = synth.pack_csr([y for _ in strings for y in strings])
+    for mode in MODES:
+        got, errs = oracle.batch(qc, qo, tc, to, sig, alpha, beta, mode, nthreads=4)
+        assert not errs.any()
+        bad = np.nonzero(got != want[mode].ravel())[0]
+        assert len(bad) == 0, (mode, bad[:5])
 
 
 @pytest.mark.parametrize("mode", MODES)
