@@ -1640,6 +1640,10 @@ static int batch_host_impl(const uint8_t *q_codes, const int64_t *q_off, const u
   for (int k = 0; k < nmodes; ++k)
     if (modes[k] < 0 || modes[k] > 2) return GA_ERR_ARG;
   if (npairs > 0 && (!q_codes || !q_off || !t_codes || !t_off || !scores)) return GA_ERR_ARG;
+  {  // the scoring is checked before any stream, copy or allocation is made
+    Scoring sc;
+    if (int rc0 = check_scoring(scoring, &sc)) return rc0;
+  }
   if (npairs == 0) return batch_impl(nullptr, nullptr, nullptr, nullptr, 0, scoring, modes[0], nullptr, stream,
                                      stats, 0);
   cudaStream_t s = (cudaStream_t)stream;

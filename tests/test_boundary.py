@@ -107,3 +107,65 @@ def test_plan_arguments_rejected_before_any_cuda_call(libpath):
         assert getattr(lib, fn)(*args) == 1, fn
     assert ctypes.sizeof(ga.Tuning) == 16
     assert ga.Tuning((1 << 16) | 0b101, 0, 1, 0).as_dict() == {"tiles16": [6, 8, 32], "tiles32": [], "concurrent": 1}
+
+
+def test_multi_mode_arguments_rejected_before_any_cuda_call(libpath):
+    """ga_align_batch_modes / ga_align_batch_host_modes check the mode list
+    (1..8 entries, each local, global or semi-global) and the buffers before
+    anything touches the device."""
+    import numpy as np
+    import paper_2205_07610_gb300 as ga
+    lib = ga.load()
+    sc, keep = ga.make_scoring(np.zeros((4, 4), dtype=np.int8), 5, 2)
+    for fn in ("ga_align_batch_modes", "ga_align_batch_host_modes"):
+        f = getattr(lib, fn)
+        for modes in ([], [0] * 9, [1, 3], [-1], [2, 0, 7]):
+            md = np.asarray(modes if modes else [0], dtype=np.int32)
+            rc = f(None, None, None, None, 4, ctypes.byref(sc), md.ctypes.data, len(modes), None, None, None)
+            assert rc == 1, (fn, modes)
+        md = np.asarray([0, 1], dtype=np.int32)
+        assert f(None, None, None, None, 4, ctypes.byref(sc), None, 2, None, None, None) == 1, fn  # no mode list
+        assert f(None, None, None, None, 4, ctypes.byref(sc), md.ctypes.data, 2, None, None, None) == 1, fn  # no buffers
+        assert f(None, None, None, None, -1, ctypes.byref(sc), md.ctypes.data, 2, None, None, None) == 1, fn
+        bad, keep2 = ga.make_scoring(np.zeros((4, 4), dtype=np.int8), 2, 3)  # gap_extend > gap_open
+        qo = np.zeros(2, dtype=np.int64)
+        codes = np.zeros(1, dtype=np.uint8)
+        sco = np.zeros(4, dtype=np.int32)
+        if fn == "ga_align_batch_host_modes":
+            # host buffers: the scoring is checked before any copy is made
+            rc = f(codes.ctypes.data, qo.ctypes.data, codes.ctypes.data, qo.ctypes.data, 1, ctypes.byref(bad),
+                   md.ctypes.data, 2, sco.ctypes.data, None, None)
+            assert rc == 1, fn
+
+
+def test_bad_scoring_rejected_before_any_cuda_call(libpath):
+    """Every entry point that takes a scoring returns GA_ERR_ARG for an
+    invalid one (gap_extend > gap_open, gap_open <= 0) synchronously, with
+    non-null buffers, before any stream, copy, allocation or launch (on a
+    machine without a GPU a CUDA call made first would answer GA_ERR_CUDA)."""
+    import numpy as np
+    import paper_2205_07610_gb300 as ga
+    lib = ga.load()
+    m = np.zeros((4, 4), dtype=np.int8)
+    codes = np.zeros(8, dtype=np.uint8)
+    off = np.array([0, 4], dtype=np.int64)
+    out = np.zeros(8, dtype=np.int32)
+    md = np.array([0, 1], dtype=np.int32)
+    c, o, s = codes.ctypes.data, off.ctypes.data, out.ctypes.data
+    for go, ge in ((2, 3), (0, 1), (5, 0)):
+        sc, keep = ga.make_scoring(m, go, ge)
+        r = ctypes.byref(sc)
+        calls = {
+            "ga_align_batch": lambda: lib.ga_align_batch(c, o, c, o, 1, r, 1, s, None, None),
+            "ga_align_batch_modes": lambda: lib.ga_align_batch_modes(c, o, c, o, 1, r, md.ctypes.data, 2, s, None,
+                                                                     None),
+            "ga_align_batch_host": lambda: lib.ga_align_batch_host(c, o, c, o, 1, r, 1, s, None, None),
+            "ga_align_batch_host_modes": lambda: lib.ga_align_batch_host_modes(c, o, c, o, 1, r, md.ctypes.data, 2,
+                                                                               s, None, None),
+            "ga_align_cross": lambda: lib.ga_align_cross(c, o, 1, c, o, 1, r, 0, s, None, None),
+            "ga_align_long": lambda: lib.ga_align_long(c, 4, c, 4, r, 1, s, None, None),
+            "ga_align_long_noalloc": lambda: lib.ga_align_long_noalloc(c, 4, c, 4, r, 1, s, None),
+            "ga_align_banded": lambda: lib.ga_align_banded(c, o, c, o, 1, r, None, 16, s, None, None, None),
+        }
+        for name, call in calls.items():
+            assert call() == 1, (name, go, ge)
