@@ -169,3 +169,40 @@ def test_bad_scoring_rejected_before_any_cuda_call(libpath):
         }
         for name, call in calls.items():
             assert call() == 1, (name, go, ge)
+
+
+def test_band_mlp_and_server_arguments_rejected_before_any_cuda_call(libpath):
+    """The band-predictor, network and server entry points return GA_ERR_ARG
+    for null buffers, negative sizes or an invalid scoring before anything
+    touches the device."""
+    import numpy as np
+    import paper_2205_07610_gb300 as ga
+    lib = ga.load()
+    c = np.zeros(8, np.uint8)
+    o = np.array([0, 4], np.int64)
+    f = np.zeros(64, np.float32)
+    i = np.zeros(8, np.int32)
+    u = np.zeros(8, np.uint16)
+    C, O, F, I, U = c.ctypes.data, o.ctypes.data, f.ctypes.data, i.ctypes.data, u.ctypes.data
+    bad, keep = ga.make_scoring(np.zeros((4, 4), np.int8), 2, 3)
+    fl = ctypes.c_float
+    adam = (fl(1e-3), fl(0.9), fl(0.999), fl(1e-8))
+    calls = {
+        "features npairs < 0": lambda: lib.ga_band_features(C, O, C, O, -1, F, None, None),
+        "features null codes": lambda: lib.ga_band_features(None, O, C, O, 1, F, None, None),
+        "min_w bad scoring": lambda: lib.ga_band_min_w(C, O, C, O, 1, ctypes.byref(bad), I, I, None, None),
+        "predict null params": lambda: lib.ga_band_predict(C, O, C, O, 1, None, fl(0.25), I, None, None, None),
+        "predict npairs < 0": lambda: lib.ga_band_predict(C, O, C, O, -1, U, fl(0.25), I, None, None, None),
+        "forward n < 0": lambda: lib.ga_mlp_forward(U, F, -1, F, None),
+        "forward null params": lambda: lib.ga_mlp_forward(None, F, 1, F, None),
+        "loss_grad n = 0": lambda: lib.ga_mlp_loss_grad(U, F, F, 0, F, None, None),
+        "loss_grad null x": lambda: lib.ga_mlp_loss_grad(U, None, F, 1, F, None, None),
+        "train steps < 0": lambda: lib.ga_mlp_train(F, U, F, F, F, F, 4, I, -1, 1, 0, *adam, None, None),
+        "train batch = 0": lambda: lib.ga_mlp_train(F, U, F, F, F, F, 4, I, 1, 0, 0, *adam, None, None),
+        "train null master": lambda: lib.ga_mlp_train(None, U, F, F, F, F, 4, I, 1, 1, 0, *adam, None, None),
+        "cast null master": lambda: lib.ga_mlp_cast(None, U, None),
+        "server_create null": lambda: lib.ga_server_create(None, None),
+        "server_drain null": lambda: lib.ga_server_drain(None, 10),
+    }
+    for name, call in calls.items():
+        assert call() == 1, name
