@@ -103,6 +103,21 @@ int64_t ga_server_clock_ns(ga_server *s);
 
 int ga_server_stats_get(ga_server *s, ga_server_stats *st);
 
+/*
+ * ga_probe_bounded_wait -- the strip kernel's bounded wait, run alone: one
+ * GPU thread waits (acquire loads, __nanosleep back-off, limit measured on
+ * the GPU's globaltimer) until a device flag holding flag_value reaches
+ * need.  Nothing writes the flag, so with flag_value < need the wait runs
+ * out: *status = GA_ERR_TIMEOUT after about limit_ns; with flag_value >=
+ * need, *status = GA_OK at once.  *waited_ns: the time the wait took on the
+ * GPU clock.  limit_ns in [0, 1e9], else GA_ERR_ARG; GA_ERR_OOM / GA_ERR_CUDA
+ * for allocation or launch failures.  Synchronous (legacy default stream).
+ * This is how failure detection of the strip schedule is tested: the wait
+ * gives up and reports, and the GPU context stays usable.
+ */
+int ga_probe_bounded_wait(int32_t flag_value, int32_t need, int64_t limit_ns, int32_t *status,
+                          int64_t *waited_ns);
+
 /* Stop the scheduler and the kernel and free everything.  Requests not yet
  * completed are dropped. */
 int ga_server_destroy(ga_server *s);

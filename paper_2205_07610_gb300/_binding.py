@@ -36,7 +36,7 @@ EXPORTED = ("ga_align_batch", "ga_align_batch_modes", "ga_align_batch_host", "ga
             "ga_server_poll", "ga_server_drain", "ga_server_clock_ns", "ga_server_stats_get",
             "ga_server_destroy", "ga_plan_create", "ga_plan_run", "ga_plan_capture",
             "ga_plan_launch", "ga_plan_stats", "ga_plan_autotune", "ga_plan_get_tuning",
-            "ga_plan_set_tuning", "ga_plan_destroy")
+            "ga_plan_set_tuning", "ga_plan_destroy", "ga_probe_bounded_wait")
 TILE_K = (6, 7, 8, 9, 10, 11, 12, 13, 14, 15, 16, 17, 18, 19, 20, 24, 32)  # columns per lane of tile 0..16
 SERVE_MAX_LEN = 65536
 BAND_NFEAT = 32
@@ -151,8 +151,10 @@ def load(build_if_missing: bool = False):
     lib.ga_server_clock_ns.restype = i64
     lib.ga_server_stats_get.argtypes = [P, ctypes.POINTER(ServerStats)]
     lib.ga_server_destroy.argtypes = [P]
+    lib.ga_probe_bounded_wait.argtypes = [i32, i32, i64, ctypes.POINTER(i32), ctypes.POINTER(i64)]
     for f in ("ga_server_create", "ga_server_add_scoring", "ga_server_submit_batch",
-              "ga_server_poll", "ga_server_drain", "ga_server_stats_get", "ga_server_destroy"):
+              "ga_server_poll", "ga_server_drain", "ga_server_stats_get", "ga_server_destroy",
+              "ga_probe_bounded_wait"):
         getattr(lib, f).restype = i32
     tp = ctypes.POINTER(Tuning)
     lib.ga_plan_create.argtypes = [sp, i32, i64, i64, i32, vp]
@@ -197,6 +199,18 @@ def probe_issue_rate(op: str, iters: int = 1024, blocks: int = 0, threads: int =
     if rc:
         raise RuntimeError(f"ga_probe_issue_rate({op}) failed: {rc}")
     return float(ms.value), float(ops.value)
+
+
+def probe_bounded_wait(flag_value: int, need: int, limit_ns: int):
+    """(status, waited_ns) of the strip kernel's bounded wait run alone on a
+    device flag that nothing writes (gotoh_serve.h)."""
+    st = ctypes.c_int32(-1)
+    waited = ctypes.c_int64(-1)
+    rc = load().ga_probe_bounded_wait(int(flag_value), int(need), int(limit_ns), ctypes.byref(st),
+                                      ctypes.byref(waited))
+    if rc:
+        raise GotohError(rc, "ga_probe_bounded_wait")
+    return int(st.value), int(waited.value)
 
 
 def strerror(code: int) -> str:

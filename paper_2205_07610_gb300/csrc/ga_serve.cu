@@ -543,11 +543,47 @@ void sched_main(ga_server *S) {
 }
 
 }  // namespace
+
+// One thread waits, with the strip kernel's bounded wait, until *flag >= need.
+__global__ void wait_probe_kernel(const int32_t *flag, int32_t need, int64_t limit_ns, int32_t *status,
+                                  int64_t *waited_ns) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const uint64_t t0 = sv_now();
+  const bool ok = sv_wait_at_least(flag, need, (uint64_t)limit_ns);
+  *waited_ns = (int64_t)(sv_now() - t0);
+  *status = ok ? GA_OK : GA_ERR_TIMEOUT;
+}
+
 }  // namespace ga
 
 using namespace ga;
 
 extern "C" {
+
+int ga_probe_bounded_wait(int32_t flag_value, int32_t need, int64_t limit_ns, int32_t *status,
+                          int64_t *waited_ns) {
+  if (!status || !waited_ns || limit_ns < 0 || limit_ns > 1000000000ll) return GA_ERR_ARG;
+  struct Buf {
+    int32_t flag, status;
+    int64_t waited;
+  };
+  Buf *d = nullptr;
+  if (cudaMalloc(&d, sizeof(Buf)) != cudaSuccess) return GA_ERR_OOM;
+  Buf h{flag_value, -1, -1};
+  int rc = GA_OK;
+  if (cudaMemcpy(d, &h, sizeof(Buf), cudaMemcpyHostToDevice) != cudaSuccess) rc = GA_ERR_CUDA;
+  if (!rc) {
+    wait_probe_kernel<<<1, 32>>>(&d->flag, need, limit_ns, &d->status, &d->waited);
+    if (cudaGetLastError() != cudaSuccess || cudaMemcpy(&h, d, sizeof(Buf), cudaMemcpyDeviceToHost) != cudaSuccess)
+      rc = GA_ERR_CUDA;
+  }
+  cudaFree(d);
+  if (!rc) {
+    *status = h.status;
+    *waited_ns = h.waited;
+  }
+  return rc;
+}
 
 int ga_server_create(const ga_server_config *cfg, ga_server **out) {
   if (!cfg || !out) return GA_ERR_ARG;

@@ -128,6 +128,21 @@ __device__ __forceinline__ int sv_ld_sys(const int32_t *p) {
   return v;
 }
 
+// Bounded wait until *flag >= need (acquire): true once it is, false when
+// limit_ns of globaltimer time pass first.  The poll backs off from 32 ns to
+// 2 us of __nanosleep.
+__device__ __forceinline__ bool sv_wait_at_least(const int32_t *flag, int need, uint64_t limit_ns) {
+  if (sv_ld_acquire(flag) >= need) return true;
+  const uint64_t t0 = sv_now();
+  unsigned ns = 32;
+  while (sv_ld_acquire(flag) < need) {
+    if (sv_now() - t0 > limit_ns) return false;
+    __nanosleep(ns);
+    if (ns < 2048) ns *= 2;
+  }
+  return true;
+}
+
 struct SvView {
   const uint8_t *rowraw, *colraw;
   int2 *edges;
@@ -205,18 +220,7 @@ __device__ int sv_strip(const SvParams &p, SvRequest *rq, int slot, const SvView
     const int need = ::min(R, 32 * b + 32);
     if (32 * b + 1 > R) return;
     const int32_t *pp = &rq->progress[s - 1];
-    if (t == 0 && sv_ld_acquire(pp) < need) {
-      const uint64_t t0 = sv_now();
-      unsigned ns = 32;
-      while (sv_ld_acquire(pp) < need) {
-        if (sv_now() - t0 > (uint64_t)p.wait_ns) {
-          atomicCAS(&rq->status, 0, GA_ERR_TIMEOUT);
-          break;
-        }
-        __nanosleep(ns);
-        if (ns < 2048) ns *= 2;
-      }
-    }
+    if (t == 0 && !sv_wait_at_least(pp, need, (uint64_t)p.wait_ns)) atomicCAS(&rq->status, 0, GA_ERR_TIMEOUT);
     __syncwarp();
     (void)sv_ld_acquire(pp);  // every lane orders its edge loads after the flag
     const int r = 32 * b + 1 + t;

@@ -187,6 +187,7 @@ def test_band_mlp_and_server_arguments_rejected_before_any_cuda_call(libpath):
     bad, keep = ga.make_scoring(np.zeros((4, 4), np.int8), 2, 3)
     fl = ctypes.c_float
     adam = (fl(1e-3), fl(0.9), fl(0.999), fl(1e-8))
+    st, w = ctypes.c_int32(0), ctypes.c_int64(0)
     calls = {
         "features npairs < 0": lambda: lib.ga_band_features(C, O, C, O, -1, F, None, None),
         "features null codes": lambda: lib.ga_band_features(None, O, C, O, 1, F, None, None),
@@ -203,6 +204,10 @@ def test_band_mlp_and_server_arguments_rejected_before_any_cuda_call(libpath):
         "cast null master": lambda: lib.ga_mlp_cast(None, U, None),
         "server_create null": lambda: lib.ga_server_create(None, None),
         "server_drain null": lambda: lib.ga_server_drain(None, 10),
+        "bounded wait limit < 0": lambda: lib.ga_probe_bounded_wait(0, 1, -1, ctypes.byref(st), ctypes.byref(w)),
+        "bounded wait limit > 1 s": lambda: lib.ga_probe_bounded_wait(0, 1, 2_000_000_000, ctypes.byref(st),
+                                                                      ctypes.byref(w)),
+        "bounded wait null out": lambda: lib.ga_probe_bounded_wait(0, 1, 1000, None, ctypes.byref(w)),
     }
     for name, call in calls.items():
         assert call() == 1, name

@@ -172,3 +172,21 @@ def test_server_rejects_bad_requests():
         srv.drain(30_000)
         r = srv.poll()
         assert len(r) == 1 and r["status"][0] == 5  # GA_ERR_RESIDUE
+
+
+def test_bounded_wait_runs_out_and_reports():
+    # failure detection without a GPU fault: the strip kernel's edge wait,
+    # run alone on a device flag that nothing writes, gives up after its
+    # limit and reports GA_ERR_TIMEOUT; a satisfied flag returns at once, and
+    # the context stays usable (an alignment afterwards is exact)
+    status, waited = ga.probe_bounded_wait(0, 1, 2_000_000)
+    assert status == 6  # GA_ERR_TIMEOUT
+    assert 2_000_000 <= waited < 500_000_000
+    status, waited = ga.probe_bounded_wait(7, 7, 2_000_000)
+    assert status == 0 and waited < 2_000_000
+    rng = np.random.default_rng(77)
+    q = rng.integers(0, 4, size=900).astype(np.uint8)
+    t = rng.integers(0, 4, size=1100).astype(np.uint8)
+    mat = synth.dna_matrix(2, -3)
+    got = ga.align_long(torch.from_numpy(q).cuda(), torch.from_numpy(t).cuda(), mat, 5, 2, "global")
+    assert int(got.item()) == oracle.score(q, t, mat, 5, 2, "global")
