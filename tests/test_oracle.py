@@ -58,7 +58,10 @@ def test_exhaustive_short_dna(mode, scheme):
                 brute.brute(q, s, sig, alpha, beta, mode), (q, s, mode)
 
 
-@pytest.mark.parametrize("scheme", SCHEMES[:2])
+ASYM = np.array([[3, -2, -4, 1], [-1, 2, -3, -2], [0, -4, 4, -1], [-3, 1, -2, 2]], dtype=np.int8)
+
+
+@pytest.mark.parametrize("scheme", SCHEMES[:2] + [(ASYM, 3, 1)])
 def test_exhaustive_dna_up_to_4(scheme):
     """Every pair of DNA strings of length 0..4 (341 strings, 116,281 pairs),
     all three modes: the C oracle against brute force.  Global scores of
@@ -67,8 +70,8 @@ def test_exhaustive_dna_up_to_4(scheme):
     definitions over substrings (Sec. 2.1): local = max(0, max over substring
     pairs), semi-global = max over substrings that start on row or column 0
     and end on row m or column n."""
-    (ma, mi), alpha, beta = scheme
-    sig = synth.dna_matrix(ma, mi)
+    mat, alpha, beta = scheme  # (match, mismatch) or an asymmetric 4 x 4 matrix (sigma(q, s) != sigma(s, q))
+    sig = mat if isinstance(mat, np.ndarray) else synth.dna_matrix(*mat)
     by_len = [np.array(list(itertools.product(range(4), repeat=L)), dtype=np.uint8).reshape(4 ** L, L)
               for L in range(5)]
     base = np.cumsum([0] + [len(x) for x in by_len])  # id of string k of length L: base[L] + k
