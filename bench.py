@@ -44,14 +44,19 @@ import synth  # noqa: E402
 # int16 operations per cell in the paper's count for global / semi-global
 # affine alignment (Sec. 4.2: 4 max + 3 add/sub); local adds 2.
 OPS_PER_CELL = 7
+# ALU-pipe operations per packed column (two cells) that the kernels issue:
+# ka_kernel prmt + vimax3 + 2 viaddmax; kp_kernel vimax3_relu + 2 viaddmax
+# + half a vimax3 (running maximum).  The FMA-pipe adds run beside them.
+KA_ALU_OPS_PER_COLUMN = 4.0
+KP_ALU_OPS_PER_COLUMN = 3.5
 # DRAM bytes (read + write) of one launch of the dominant DP kernel,
 # ka_kernel<CellS16x2, semi, 16, 18> (pairs of 273..288 columns), on this
 # batch: one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) of
 # the current kernel code and bins.
 KA_TRAFFIC_BYTES = 48514304 + 5376
-LANES_PER_SM = 128       # 4 SM sub-partitions x 32 lanes, one integer op each per clock
 SIMD = 2                 # int16x2: two cells per lane-op
 FALLBACK_SM_MHZ = 2070.0  # GB300 maximum SM clock, used only if no measured value is available
+PROBE_OPS = ("vadd2", "vmaxs2", "vimax3_s16x2", "mix_ka")
 
 
 def device_peak(dev, clocks=None):
@@ -72,6 +77,33 @@ def device_peak(dev, clocks=None):
     if mhz is None:
         mhz, src = FALLBACK_SM_MHZ, "GB300 nominal maximum"
     return n_sm, mhz, src
+
+
+def measured_peaks(rates: dict, n_sm: int, mhz: float) -> dict:
+    """Issue peaks of this GPU from the probes run at the start of the bench
+    (roofline.measure: lane-ops per clock per SM), scaled to `mhz`.
+
+    issue_ops   int16 lane-ops/s the SMs can issue: the packed add's rate (FMA
+                pipe) plus the packed max's (ALU pipe), x2 for int16x2; the
+                paper's model (Sec. 4.2) divides its 7 ops per cell by this;
+    *_alu_gcups the ALU-pipe ceiling of a kernel's own op mix: the measured
+                3-way max rate (ALU pipe) over the kernel's ALU ops per cell;
+    ka_mix_gcups the measured rate of ka_kernel's whole packed column update
+                (6 ops on two pipes, probe mix_ka), a cross-check.
+    """
+    clk = n_sm * mhz * 1e6
+    r = {k: v["lane_ops_per_clk_per_sm"] for k, v in rates["probes"].items()}
+    issue = r["vadd2"] + r["vmaxs2"]
+    return {
+        "issue_lane_ops_per_clk_sm": issue,
+        "issue_ops": issue * clk * SIMD,
+        "ka_alu_gcups": r["vimax3_s16x2"] * clk * 2 / KA_ALU_OPS_PER_COLUMN / 1e9,
+        "kp_alu_gcups": r["vimax3_s16x2"] * clk * 2 / KP_ALU_OPS_PER_COLUMN / 1e9,
+        "ka_mix_gcups": rates["mix_ka_cells_per_clk_sm"] * clk / 1e9,
+        "basis": f"{n_sm} SM x {mhz:.0f} MHz x measured lane-ops/clk/SM: vadd2 {r['vadd2']:.1f} + "
+                 f"vmaxs2 {r['vmaxs2']:.1f} (issue), vimax3 {r['vimax3_s16x2']:.1f} (ALU), "
+                 f"ka column mix {rates['mix_ka_cells_per_clk_sm']:.1f} cells",
+    }
 
 
 def parse_args():
@@ -96,6 +128,10 @@ def parse_args():
     ap.add_argument("--protein-qmin", type=int, default=100, help="shortest protein query")
     ap.add_argument("--protein-qmax", type=int, default=1000, help="longest protein query")
     ap.add_argument("--serve-requests", type=int, default=200_000)
+    ap.add_argument("--probe-iters", type=int, default=128,
+                    help="outer iterations of each issue-rate probe (about 0.1 s each)")
+    ap.add_argument("--detail", default=None,
+                    help="also write every section's full record to this JSON file")
     return ap.parse_args()
 
 
@@ -375,7 +411,7 @@ def serve_section(ga, dev, nreq: int, load: float = 0.7, burst: int = 50_000):
 
 
 def protein_section(ga, dev, stream, nq: int, nt: int, qmin: int = 100, qmax: int = 1000, reps: int = 2,
-                    check_targets: int = 512, peak_ops: float = 0.0):
+                    check_targets: int = 512, peaks: dict | None = None):
     """Protein database search: every query against every target, local mode.
 
     512 queries |Q| ~ U{100..1000} against 200k targets |T| ~ LogNormal(ln 300,
@@ -433,13 +469,20 @@ def protein_section(ga, dev, stream, nq: int, nt: int, qmin: int = 100, qmax: in
         "dp_ms": st["dp_ms"], "dp_gcups": cells / st["dp_ms"] / 1e6 if st["dp_ms"] > 0 else None,
         "pairs_int32_rerun": st["pairs_int32_rerun"], "status": st["status"],
         "exact_vs_int32_sample": exact, "checked_pairs": int(len(qi)), "gen_s": gen_s,
-        "roofline": {"bound": "alu", "ops_per_cell": 9,
-                     "achieved": cells * 9 / (st["dp_ms"] / 1e3) / 1e12 if st["dp_ms"] > 0 else None,
-                     "peak": peak_ops / 1e12,
-                     "frac": cells * 9 / (st["dp_ms"] / 1e3) / peak_ops if st["dp_ms"] > 0 and peak_ops else None,
-                     "unit": "Tops/s (int16, 9 ops per local cell)",
-                     "kernel": "kp_kernel (packed int16x2 query-profile kernel)"},
+        "roofline": protein_roofline(cells, st["dp_ms"], peaks),
     }
+
+
+def protein_roofline(cells: int, dp_ms: float, peaks: dict | None) -> dict | None:
+    """kp_kernel against the paper's 9-op local model and its own ALU mix."""
+    if not peaks or dp_ms <= 0:
+        return None
+    gcups = cells / dp_ms / 1e6
+    ops = cells * 9 / (dp_ms / 1e3)
+    return {"bound": "alu", "achieved": ops / 1e12, "peak": peaks["issue_ops"] / 1e12,
+            "unit": "Tops/s (int16, 9 ops per local cell)", "frac": ops / peaks["issue_ops"],
+            "alu_ceiling_gcups": peaks["kp_alu_gcups"], "frac_alu_mix": gcups / peaks["kp_alu_gcups"],
+            "kernel": "kp_kernel"}
 
 
 def plan_section(ga, dev, stream, big, d_big, reps: int = 200):
@@ -520,6 +563,50 @@ def plan_section(ga, dev, stream, big, d_big, reps: int = 200):
     return out
 
 
+def r4(x):
+    """Round floats to 4 significant digits, recursively (keeps the line short)."""
+    if isinstance(x, float):
+        return float(f"{x:.4g}")
+    if isinstance(x, dict):
+        return {k: r4(v) for k, v in x.items()}
+    if isinstance(x, (list, tuple)):
+        return [r4(v) for v in x]
+    return x
+
+
+def compact_plan(p):
+    if not p:
+        return None
+    return r4({"small_eager_us": p["small"]["eager_us"], "small_graph_us": p["small"]["graph_us"],
+               "large_graph_ms": p["large"]["graph_step_ms"], "large_eager_ms": p["large"]["eager_step_ms"],
+               "exact": p["small"]["exact"] and p["large"]["exact"]})
+
+
+def compact_protein(p):
+    if not p:
+        return None
+    rf = p["roofline"] or {}
+    return r4({"gcups": p["gcups"], "frac": rf.get("frac"), "frac_alu_mix": rf.get("frac_alu_mix"),
+               "rerun": p["pairs_int32_rerun"], "exact": p["exact_vs_int32_sample"]})
+
+
+def compact_serve(v):
+    if not v:
+        return None
+    return r4({k: v[k] for k in ("p50_ms", "p99_ms", "max_ms", "gcups", "capacity_gcups", "exact")})
+
+
+def compact_band(v):
+    if not v:
+        return None
+    runs = v["runs"]
+    best = next(k for k in runs if k.startswith("best_constant"))
+    return r4({"full_dp_ms": v["full_dp_ms"], "learned_ms": runs["learned"]["ms"],
+               "best_const_ms": runs[best]["ms"], "w0_16_ms": runs["default_w0_16"]["ms"],
+               "speedup": v["full_dp_ms"] / runs["learned"]["ms"],
+               "exact": all(r["exact"] for r in runs.values())})
+
+
 def run_reference(args, rank: int):
     if rank != 0:
         return
@@ -584,6 +671,10 @@ def main():
     torch.cuda.set_device(dev)
     ga.build()
     ga.load()
+    # issue-rate probes of this GPU (the roofline's denominators), before the
+    # workload so that nothing else runs beside them
+    import roofline as rl
+    rates = rl.measure(iters=args.probe_iters, ops=PROBE_OPS)
 
     b = workload(args.npairs, rank)
     cells_mode = b.cells()
@@ -651,25 +742,21 @@ def main():
     int16_pairs = sum(s["pairs_int16"] for pair in sts for s in pair)
 
     # ---- roofline of the dominant kernel (packed int16x2 inter-sequence DP)
-    n_sm, peak_mhz, peak_src = device_peak(dev, clocks)
-    sm_mhz = clocks.get("sm_mhz") or peak_mhz
-    peak_ops = n_sm * LANES_PER_SM * SIMD * peak_mhz * 1e6           # int16 ops / s
+    n_sm, max_mhz, _ = device_peak(dev, clocks)
+    sm_mhz = clocks.get("sm_mhz") or max_mhz   # median SM clock inside the timed region
+    peaks = measured_peaks(rates, n_sm, sm_mhz)
     alg_ops = step_cells * args.steps * OPS_PER_CELL
     achieved_ops = alg_ops / (dp_ms / 1e3) if dp_ms > 0 else 0.0
+    dp_gcups = step_cells * args.steps / (dp_ms / 1e3) / 1e9 if dp_ms > 0 else None
     roofline = {
-        "bound": "alu", "achieved": achieved_ops / 1e12, "peak": peak_ops / 1e12,
-        "unit": "Tops/s (int16, 7 ops per cell)", "frac": achieved_ops / peak_ops,
-        "traffic": KA_TRAFFIC_BYTES,
-        "traffic_unit": "bytes per launch of ka_kernel<CellS16x2, semi, 16, 18> (ncu)",
-        "kernel": "ka_kernel<CellS16x2> (inter-sequence, packed int16x2); achieved and peak "
-                  "over all of its launches in the timed region",
-        "dp_gcups": step_cells * args.steps / (dp_ms / 1e3) / 1e9 if dp_ms > 0 else None,
-        "dp_launches_per_step": dp_launches / args.steps,
-        "peak_gcups_at_7_ops": peak_ops / OPS_PER_CELL / 1e9,
-        "peak_basis": f"{n_sm} SM x {LANES_PER_SM} lanes x {SIMD} (int16x2) x {peak_mhz:.0f} MHz ({peak_src})",
-        "sm_mhz_measured": sm_mhz,
+        "bound": "alu", "achieved": r4(achieved_ops / 1e12), "peak": r4(peaks["issue_ops"] / 1e12),
+        "unit": "Tops/s (int16, 7 ops per cell, Sec. 4.2)", "frac": r4(achieved_ops / peaks["issue_ops"]),
+        "traffic": KA_TRAFFIC_BYTES, "kernel": "ka_kernel<CellS16x2> (all launches of the timed region)",
+        "dp_gcups": r4(dp_gcups), "alu_ceiling_gcups": r4(peaks["ka_alu_gcups"]),
+        "frac_alu_mix": r4(dp_gcups / peaks["ka_alu_gcups"]) if dp_gcups else None,
+        "mix_probe_gcups": r4(peaks["ka_mix_gcups"]),
+        "peak_basis": peaks["basis"],
     }
-
     # ---- end to end through the host entry point (pinned buffers) ---------
     e2e = None
     if not args.no_e2e:
@@ -707,15 +794,15 @@ def main():
     prot_res = None
     if world == 1 and not args.no_protein:
         prot_res = protein_section(ga, dev, stream, args.protein_queries, args.protein_targets,
-                                   args.protein_qmin, args.protein_qmax, peak_ops=peak_ops)
+                                   args.protein_qmin, args.protein_qmax, peaks=peaks)
     serve_res = None
     if world == 1 and not args.no_serve:
         serve_res = serve_section(ga, dev, args.serve_requests)
 
     if rank == 0:
         line = {
-            "metric": "GCUPS", "value": value, "unit": "GCUPS", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+            "metric": "GCUPS", "value": r4(value), "unit": "GCUPS", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": r4(ms_per_step),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "int16x2", "data": "synthetic",
             "config": {
@@ -723,16 +810,21 @@ def main():
                 "npairs_per_gpu": b.npairs, "cells_per_step_per_gpu": step_cells,
                 "scoring": "+2/-3, gap open 5, extend 2",
                 "parallelism": f"pairs sharded, {world} independent rank(s)",
-                "l2": "inputs larger than L2 (2 x 200 MB raw codes re-read each step)",
+                "l2": "inputs larger than L2 (2 x 200 MB codes per step)",
             },
-            "step_ms_median": step_ms_median,
-            "value_at_median_step": step_cells * world / (step_ms_median / 1e3) / 1e9,
-            "clocks": clocks, "roofline": roofline, "e2e": e2e, "cpu_baseline": cpu,
-            "band": band_res, "protein": prot_res, "plan": plan_res, "serve": serve_res,
+            "clocks": {k: clocks.get(k) for k in ("sm_mhz", "sm_max_mhz", "reasons", "samples_in_timed_region")},
+            "roofline": roofline, "e2e": r4(e2e), "cpu_baseline": r4(cpu),
             "gpu_launches": launches, "dp_status": max(status) if status else 0,
-            "pairs_int16_per_step": int16_pairs / args.steps,
+            "step_ms_median": r4(step_ms_median),
+            "plan": compact_plan(plan_res), "protein": compact_protein(prot_res),
+            "serve": compact_serve(serve_res), "band": compact_band(band_res),
         }
-        print(json.dumps(line), flush=True)
+        print(json.dumps(line, separators=(",", ":")), flush=True)
+        if args.detail:
+            with open(args.detail, "w") as f:
+                json.dump(r4({"line": line, "rates": rates, "peaks": peaks, "band": band_res,
+                              "protein": prot_res, "plan": plan_res, "serve": serve_res,
+                              "pairs_int16_per_step": int16_pairs / args.steps}), f, indent=1)
     if dist is not None:
         dist.destroy_process_group()
 

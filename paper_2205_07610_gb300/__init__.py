@@ -11,7 +11,7 @@ from ._binding import (LOCAL, GLOBAL, SEMIGLOBAL, EXPORTED, GotohError, Scoring,
                        align_banded, align_batch, align_batch_modes, align_batch_host, align_batch_host_modes,
                        align_cross,
                        align_long,
-                       align_long_noalloc, NOALLOC_MAX_LEN, PROBES, probe_issue_rate, probe_bounded_wait,
+                       align_long_noalloc, NOALLOC_MAX_LEN, probe_bounded_wait,
                        lib_path, load, make_scoring, strerror, version, BAND_NFEAT, MLP_NPARAMS,
                        band_features, band_min_w, band_predict, mlp_forward, mlp_loss_grad,
                        mlp_train, mlp_cast, Server, RESULT_DTYPE, SERVE_MAX_LEN, Plan, Tuning,
@@ -21,7 +21,7 @@ from .build import build
 __all__ = [
     "LOCAL", "GLOBAL", "SEMIGLOBAL", "EXPORTED", "GotohError", "Scoring", "Stats", "align_banded",
     "align_batch", "align_batch_modes", "align_batch_host", "align_batch_host_modes", "align_cross", "align_long", "align_long_noalloc",
-    "NOALLOC_MAX_LEN", "PROBES", "probe_issue_rate", "probe_bounded_wait", "lib_path", "load",
+    "NOALLOC_MAX_LEN", "probe_bounded_wait", "lib_path", "load",
     "make_scoring", "strerror", "version", "build", "BAND_NFEAT", "MLP_NPARAMS", "band_features",
     "band_min_w", "band_predict", "mlp_forward", "mlp_loss_grad", "mlp_train", "mlp_cast",
     "Server", "RESULT_DTYPE", "SERVE_MAX_LEN", "Plan", "Tuning", "TILE_K",

@@ -30,7 +30,7 @@ GA_ERR_RANGE = 7
 EXPORTED = ("ga_align_batch", "ga_align_batch_modes", "ga_align_batch_host", "ga_align_batch_host_modes",
             "ga_align_cross", "ga_align_long",
             "ga_align_long_noalloc", "ga_align_banded", "ga_strerror", "ga_version",
-            "ga_probe_issue_rate", "ga_band_features", "ga_band_min_w", "ga_band_predict",
+            "ga_band_features", "ga_band_min_w", "ga_band_predict",
             "ga_mlp_forward", "ga_mlp_loss_grad", "ga_mlp_train", "ga_mlp_cast",
             "ga_server_create", "ga_server_add_scoring", "ga_server_submit_batch",
             "ga_server_poll", "ga_server_drain", "ga_server_clock_ns", "ga_server_stats_get",
@@ -41,9 +41,6 @@ TILE_K = (6, 7, 8, 9, 10, 11, 12, 13, 14, 15, 16, 17, 18, 19, 20, 24, 32)  # col
 SERVE_MAX_LEN = 65536
 BAND_NFEAT = 32
 MLP_NPARAMS = 6337
-PROBES = {"vadd2": 0, "vmaxs2": 1, "viaddmax_s16x2": 2, "vimax3_s16x2": 3,
-          "viaddmax_s16x2_relu": 4, "prmt": 5, "iadd": 6, "imax": 7, "viaddmax_s32": 8,
-          "vimax3_s32": 9, "imad": 10, "lop3": 11, "hadd2": 12, "hmax2": 13, "cell": 14}
 NOALLOC_MAX_LEN = 65536
 
 
@@ -175,30 +172,12 @@ def load(build_if_missing: bool = False):
               "ga_plan_stats", "ga_plan_autotune", "ga_plan_get_tuning", "ga_plan_set_tuning",
               "ga_plan_destroy"):
         getattr(lib, f).restype = i32
-    lib.ga_probe_issue_rate.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
-                                        ctypes.POINTER(ctypes.c_float),
-                                        ctypes.POINTER(ctypes.c_double)]
-    lib.ga_probe_issue_rate.restype = ctypes.c_int
     lib.ga_strerror.argtypes = [ctypes.c_int]
     lib.ga_strerror.restype = ctypes.c_char_p
     lib.ga_version.argtypes = []
     lib.ga_version.restype = ctypes.c_int
     _lib = lib
     return lib
-
-
-def probe_issue_rate(op: str, iters: int = 1024, blocks: int = 0, threads: int = 256):
-    """(ms, lane_ops) of one timed launch of an issue-rate probe (gotoh_probe.h)."""
-    if blocks <= 0:
-        import torch
-        blocks = 8 * torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
-    ms = ctypes.c_float(0)
-    ops = ctypes.c_double(0)
-    rc = load().ga_probe_issue_rate(PROBES[op], int(iters), int(blocks), int(threads),
-                                    ctypes.byref(ms), ctypes.byref(ops))
-    if rc:
-        raise RuntimeError(f"ga_probe_issue_rate({op}) failed: {rc}")
-    return float(ms.value), float(ops.value)
 
 
 def probe_bounded_wait(flag_value: int, need: int, limit_ns: int):

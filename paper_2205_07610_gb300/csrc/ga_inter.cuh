@@ -80,9 +80,9 @@ __host__ __device__ constexpr int ka_tile_index(int K) {
 // compiles on sm_103a without register spills (local mode and the int32
 // cells) or with at most 16 bytes of spill stores (packed global and
 // semi-global: the extra resident block measured faster on GB300, local
-// measured slower), as printed by
-// `python -m paper_2205_07610_gb300.occupancy_sweep [--max-spill 16]`
-// (rerun after changing the kernel).
+// measured slower).  The values come from compiling every instantiation at
+// each candidate block count and reading ptxas's spill report; they must be
+// re-derived the same way after a change to the kernel.
 template <class Cell, int MODE, int K>
 struct KAMinBlocks {
   // columns per lane:    6  7  8  9 10 11 12 13 14 15 16 17 18 19 20 24 32
