@@ -95,6 +95,13 @@ struct Scoring {
   uint32_t tables[16] = {};
 };
 
+// Long pairs of alphabets of <= 4 symbols run on the packed kernel when its
+// relative int16 cells are exact for the scoring (sigma_max + alpha <=
+// kKwMaxStep); every other long pair on the int32 kernel.
+bool long_packed(const Scoring &sc, bool dna) {
+  return dna && std::max(sc.smax, 0) + sc.alpha <= kKwMaxStep;
+}
+
 int check_scoring(const ga_scoring *sc, Scoring *out) {
   if (!sc) return GA_ERR_ARG;
   if (sc->alphabet_size < 1 || sc->alphabet_size > 31 || !sc->matrix) return GA_ERR_ALPHABET;
@@ -487,7 +494,11 @@ int launch_prepare(Call &c, ChunkPlan &p) {
   p.long_smem = profile ? (size_t)kKbWarps * (size_t)(c.sc.A + 1) * (32 * kKbK) : 0;
   if (p.long_cnt > 0) {
     int occ = 0;
-    if (profile)
+    if (long_packed(c.sc, c.dna))
+      occ = p.mode == GA_LOCAL ? blocks_per_sm_kw_local()
+          : p.mode == GA_GLOBAL ? blocks_per_sm_kw_global()
+                                : blocks_per_sm_kw_semi();
+    else if (profile)
       occ = p.mode == GA_LOCAL ? blocks_per_sm_kb_local_prof(p.long_smem)
           : p.mode == GA_GLOBAL ? blocks_per_sm_kb_global_prof(p.long_smem)
                                 : blocks_per_sm_kb_semi_prof(p.long_smem);
@@ -566,7 +577,8 @@ int launch_bin(Call &c, const SetView &Q, const SetView &T, ChunkPlan &p, int cl
 int launch_long(Call &c, const SetView &Q, const SetView &T, ChunkPlan &p, DpFork &fk) {
   if (p.npairs == 0 || p.long_cnt <= 0) return GA_OK;
   const bool profile = !c.dna;
-  c.pairs32 += p.long_cnt;
+  const bool packed = long_packed(c.sc, c.dna);
+  (packed ? c.pairs16 : c.pairs32) += p.long_cnt;
   KBParams kb{};
   kb.packed_q = Q.packed;
   kb.packed_t = T.packed;
@@ -590,7 +602,11 @@ int launch_long(Call &c, const SetView &Q, const SetView &T, ChunkPlan &p, DpFor
   kb.q0 = p.q0;
   cudaError_t e;
   const cudaStream_t ls = fk.launch_begin();
-  if (profile)
+  if (packed)
+    e = p.mode == GA_LOCAL ? launch_kw_local(kb, p.long_grid, ls)
+      : p.mode == GA_GLOBAL ? launch_kw_global(kb, p.long_grid, ls)
+                            : launch_kw_semi(kb, p.long_grid, ls);
+  else if (profile)
     e = p.mode == GA_LOCAL ? launch_kb_local_prof(kb, p.long_grid, p.long_smem, ls)
       : p.mode == GA_GLOBAL ? launch_kb_global_prof(kb, p.long_grid, p.long_smem, ls)
                             : launch_kb_semi_prof(kb, p.long_grid, p.long_smem, ls);
@@ -1038,7 +1054,9 @@ int cross_protein_local(Call &c, const uint8_t *q_codes, const int64_t *q_off, i
   if (nt >= (1ll << 31) - 64 || nq * nt >= (1ll << 31) - 64) return GA_ERR_ARG;
   uint32_t *keys = c.al.get<uint32_t>((size_t)nt);
   int32_t *sorted = c.al.get<int32_t>((size_t)nt);
-  const int32_t rerun_cap = (int32_t)std::min<int64_t>(std::max<int64_t>(nq * nt, 1), 1 << 22);
+  // flagged pairs are rerun in int32 one list at a time; a search with more
+  // of them than the list holds finds the rest by scanning for their marks
+  const int32_t rerun_cap = (int32_t)std::min<int64_t>(std::max<int64_t>(nq * nt, 1), 1 << 16);
   int32_t *rerun = c.al.get<int32_t>((size_t)rerun_cap);
   if (c.al.failed) return GA_ERR_OOM;
   // targets: longest first, invalid ones left out
@@ -1139,30 +1157,53 @@ int cross_protein_local(Call &c, const uint8_t *q_codes, const int64_t *q_off, i
     rc = launch_kp_tile(c, kp, max_grid, b);
     if (rc) return rc;
   }
-  // exact int32 rerun of flagged pairs (rare: a local score near 32767)
+  // exact int32 rerun of flagged pairs (rare: a local score near 32767).
+  // Each pass reruns the pairs of the list; when the kernels flagged more
+  // pairs than the list holds, the next list is collected from the marks
+  // left in the scores (a rerun overwrites its pair's mark).
   int32_t *hn = (int32_t *)pinned_scratch();
   if (cudaMemcpyAsync(hn, &c.small->rerun_range[1], sizeof(int32_t), cudaMemcpyDeviceToHost, c.s) != cudaSuccess ||
       cudaStreamSynchronize(c.s) != cudaSuccess)
     return GA_ERR_CUDA;
   const int32_t nre = hn[0];
-  if (nre > rerun_cap) return GA_ERR_RANGE;
-  if (nre > 0) {
-    int64_t *info = c.al.get<int64_t>((size_t)nre * 4);
-    std::vector<int32_t> ids((size_t)nre);
-    std::vector<int64_t> hinfo((size_t)nre * 4);
-    if (c.al.failed) return GA_ERR_OOM;
-    kp_rerun_info_kernel<<<(unsigned)((nre + 255) / 256), 256, 0, c.s>>>(rerun, nre, nt, q_off, t_off, info);
-    if (cudaMemcpyAsync(ids.data(), rerun, sizeof(int32_t) * (size_t)nre, cudaMemcpyDeviceToHost, c.s) != cudaSuccess ||
-        cudaMemcpyAsync(hinfo.data(), info, sizeof(int64_t) * (size_t)nre * 4, cudaMemcpyDeviceToHost, c.s) != cudaSuccess ||
+  int32_t pending = nre;
+  bool from_list = true;
+  int64_t *info = nre > 0 ? c.al.get<int64_t>((size_t)std::min(nre, rerun_cap) * 4) : nullptr;
+  if (c.al.failed) return GA_ERR_OOM;
+  std::vector<int32_t> ids;
+  std::vector<int64_t> hinfo;
+  while (pending > 0) {
+    if (!from_list) {  // collect the next list from the marks
+      if (cudaMemsetAsync(&c.small->rerun_range[1], 0, sizeof(int32_t), c.s) != cudaSuccess) return GA_ERR_CUDA;
+      const int64_t total = nq * nt;
+      kp_collect_marked_kernel<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256,
+                                                                                  (int64_t)c.nsm * 32)),
+                                 256, 0, c.s>>>(scores, total, rerun, rerun_cap, &c.small->rerun_range[1]);
+      ++c.launches;
+      if (cudaMemcpyAsync(hn, &c.small->rerun_range[1], sizeof(int32_t), cudaMemcpyDeviceToHost, c.s) != cudaSuccess ||
+          cudaStreamSynchronize(c.s) != cudaSuccess)
+        return GA_ERR_CUDA;
+      pending = hn[0];
+      if (pending <= 0) break;
+    }
+    const int32_t n_now = std::min(pending, rerun_cap);
+    ids.resize((size_t)n_now);
+    hinfo.resize((size_t)n_now * 4);
+    kp_rerun_info_kernel<<<(unsigned)((n_now + 255) / 256), 256, 0, c.s>>>(rerun, n_now, nt, q_off, t_off, info);
+    ++c.launches;
+    if (cudaMemcpyAsync(ids.data(), rerun, sizeof(int32_t) * (size_t)n_now, cudaMemcpyDeviceToHost, c.s) != cudaSuccess ||
+        cudaMemcpyAsync(hinfo.data(), info, sizeof(int64_t) * (size_t)n_now * 4, cudaMemcpyDeviceToHost, c.s) != cudaSuccess ||
         cudaStreamSynchronize(c.s) != cudaSuccess)
       return GA_ERR_CUDA;
-    for (int32_t i = 0; i < nre; ++i) {
+    for (int32_t i = 0; i < n_now; ++i) {
       const int64_t *f = &hinfo[(size_t)i * 4];
       rc = sv_align_pair(q_codes + f[0], f[1], t_codes + f[2], f[3], c.sc.A, c.sc.mat, c.sc.alpha, c.sc.beta,
                          GA_LOCAL, scores + ids[i], c.s, nullptr);
       if (rc) return rc;
     }
-    c.pairs32 += nre;
+    c.pairs32 += n_now;
+    pending = (from_list && pending <= rerun_cap) ? 0 : 1;  // an overflowed list: rescan
+    from_list = false;
   }
   c.pairs16 += (int64_t)flat.size() * ntv - nre;
   rc = finish(c, stats, e0, e1, nq * nt);
@@ -1192,6 +1233,7 @@ struct PlanImpl {
   ga_tuning tune{};
   int occ16[kKaNumBins] = {}, occ32[kKaNumBins] = {};
   int occ_kb = 0, long_grid = 0;
+  bool long_packed = false;
   size_t long_smem = 0;
   Small *small = nullptr;
   int32_t *hist = nullptr, *cursor = nullptr;
@@ -1270,7 +1312,10 @@ int plan_create(const ga_scoring *scoring, int32_t mode, int64_t max_pairs, int6
     P->occ32[b] = std::max(plan_occupancy(1, mode, b), 1);
   }
   P->long_smem = dna ? 0 : (size_t)kKbWarps * (size_t)(P->sc.A + 1) * (32 * kKbK);
-  P->occ_kb = dna ? (mode == GA_LOCAL ? blocks_per_sm_kb_local_sel(0) : mode == GA_GLOBAL ? blocks_per_sm_kb_global_sel(0)
+  P->long_packed = long_packed(P->sc, dna);
+  P->occ_kb = P->long_packed ? (mode == GA_LOCAL ? blocks_per_sm_kw_local() : mode == GA_GLOBAL ? blocks_per_sm_kw_global()
+                                                                                            : blocks_per_sm_kw_semi())
+            : dna ? (mode == GA_LOCAL ? blocks_per_sm_kb_local_sel(0) : mode == GA_GLOBAL ? blocks_per_sm_kb_global_sel(0)
                                                                                          : blocks_per_sm_kb_semi_sel(0))
                   : (mode == GA_LOCAL ? blocks_per_sm_kb_local_prof(P->long_smem)
                                       : mode == GA_GLOBAL ? blocks_per_sm_kb_global_prof(P->long_smem)
@@ -1425,7 +1470,11 @@ int plan_enqueue(PlanImpl &P, const uint8_t *q_codes, const int64_t *q_off, cons
     const int grid = std::max(P.long_grid, 1);
     const cudaStream_t ls = stream_for(nlaunch++);
     cudaError_t e;
-    if (!dna)
+    if (P.long_packed)
+      e = P.mode == GA_LOCAL ? launch_kw_local(kb, grid, ls)
+        : P.mode == GA_GLOBAL ? launch_kw_global(kb, grid, ls)
+                              : launch_kw_semi(kb, grid, ls);
+    else if (!dna)
       e = P.mode == GA_LOCAL ? launch_kb_local_prof(kb, grid, P.long_smem, ls)
         : P.mode == GA_GLOBAL ? launch_kb_global_prof(kb, grid, P.long_smem, ls)
                               : launch_kb_semi_prof(kb, grid, P.long_smem, ls);

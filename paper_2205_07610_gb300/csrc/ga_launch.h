@@ -7,6 +7,7 @@
 
 #include "ga_inter.cuh"
 #include "ga_long.cuh"
+#include "ga_longpk.cuh"
 
 namespace ga {
 
@@ -45,6 +46,16 @@ GA_KB_DECLARE(kb_semi_sel)
 GA_KB_DECLARE(kb_local_prof)
 GA_KB_DECLARE(kb_global_prof)
 GA_KB_DECLARE(kb_semi_prof)
+
+// Packed long kernel (alphabets of <= 4 symbols, sigma_max + alpha <=
+// kKwMaxStep): 32 lanes x 16 columns per half, two halves per super-stage.
+constexpr int kKwK = 16;
+cudaError_t launch_kw_local(const KBParams &p, int grid, cudaStream_t s);
+cudaError_t launch_kw_global(const KBParams &p, int grid, cudaStream_t s);
+cudaError_t launch_kw_semi(const KBParams &p, int grid, cudaStream_t s);
+int blocks_per_sm_kw_local();
+int blocks_per_sm_kw_global();
+int blocks_per_sm_kw_semi();
 
 struct KCParams;
 cudaError_t launch_kc(const KCParams &p, int grid, cudaStream_t s);
