@@ -51,7 +51,7 @@
  *   GA_ERR_ARG       null pointer where data is required, gap_open <= 0,
  *                    gap_extend <= 0, gap_extend > gap_open, gap costs
  *                    > 4096, a bad mode, negative counts;
- *   GA_ERR_ALPHABET  alphabet_size outside 1..32 or a matrix entry
+ *   GA_ERR_ALPHABET  alphabet_size outside 1..31 or a matrix entry
  *                    outside [-127, 127];
  *   GA_ERR_OOM       workspace allocation failed;
  *   GA_ERR_CUDA      a CUDA call failed while enqueueing.
@@ -190,7 +190,11 @@ int ga_align_batch_host_modes(const uint8_t *q_codes, const int64_t *q_off, cons
  * every target l = 0..nt-1; scores[k*nt + l] (row-major, device,
  * int32[nq*nt]).  Offsets as in ga_align_batch.  The query's scoring
  * profile is staged once in shared memory and the targets stream through
- * it (Sec. 3.1, "scoring profile").
+ * it (Sec. 3.1, "scoring profile").  Local searches over alphabets of more
+ * than 4 symbols run in packed int16x2; every pair whose int16 running
+ * maximum reaches 32767 - sigma_max is recomputed exactly in int32, one
+ * pair at a time (a search with many such pairs, e.g. near-identical
+ * database hits longer than a few thousand residues, is exact but slow).
  */
 int ga_align_cross(const uint8_t *q_codes, const int64_t *q_off, int64_t nq,
                    const uint8_t *t_codes, const int64_t *t_off, int64_t nt,
@@ -255,7 +259,12 @@ int ga_align_banded(const uint8_t *q_codes, const int64_t *q_off, const uint8_t 
  *     enqueued); other argument errors as for ga_align_batch.
  *   - The first call on a device looks up the array's device address
  *     (cudaGetSymbolAddress) once for that device; make that first call
- *     before any stream capture.
+ *     before any stream capture.  With CUDA's default lazy module loading,
+ *     that first call may also be what loads the library's device code and
+ *     reserves the array itself (device memory), so make it (a warm-up call
+ *     with tiny inputs will do) before a pooling allocator takes the
+ *     device's memory, or load modules eagerly (CUDA_MODULE_LOADING=EAGER).
+ *     Later calls allocate nothing.
  *   - Every call shares the array and leaves its contents behind; each call
  *     rewrites what must start fresh.  Calls whose GPU work overlaps (other
  *     streams, unordered host threads) race on the array: serialise them.

@@ -2,8 +2,8 @@
 // more than four symbols (int32 cells).
 //
 // The columns (shorter sequence) are cut into stages of W = 32*K columns
-// (Sec. 3.1: "we partition the workload into l non-overlapping submatrices
-// ... computed by a thread group in l stages from left to right").  A warp
+// that one warp computes one after another from left to right, the
+// multi-stage partitioning of a long alignment in Sec. 3.1.  A warp
 // runs one pair: within a stage lane t owns K columns and works on row
 // it - t + 1 as in the inter-sequence kernel; the right edge of a stage
 // (H and the outgoing F of lane 31, one int2 per row) goes to a per-warp

@@ -26,7 +26,10 @@
 // columns past a query's end have score 0; in local mode such cells never
 // exceed the largest real cell, so the running maximum is exact.  A pair
 // whose running maximum reaches 32767 - sigma_max is queued for an exact
-// int32 rerun.
+// int32 rerun: its score entry is set to kRerunMark (no real score comes
+// near it: every admitted score is below 2^30) and its id is appended to the
+// rerun list while the list has room, so the caller can always find every
+// flagged pair by scanning the scores when the list overflowed.
 #pragma once
 
 #include "ga_dp.cuh"
@@ -38,6 +41,7 @@ constexpr int kKpG = 16;
 constexpr int kKpWarps = 4;
 constexpr int kKpGroups = 2 * kKpWarps;  // targets per block task
 constexpr int kKpMaxA = 31;
+constexpr int32_t kRerunMark = 0x7fffffff;
 
 struct KPParams {
   const uint8_t *q_codes;
@@ -54,7 +58,7 @@ struct KPParams {
   int8_t sigma[32 * 32];    // sigma(query code, target code), A x A
   int32_t *scores;          // [nq][nt]
   int32_t *rerun_list;      // pair ids k * nt + l, rerun_cap entries
-  int32_t *rerun_count;     // may exceed rerun_cap: the caller reports an error
+  int32_t *rerun_count;     // may exceed rerun_cap: the caller then scans for kRerunMark
   int32_t rerun_cap;
   int2 *bnd;                // per group slot: bnd_stride entries
   int64_t bnd_stride;
@@ -252,6 +256,7 @@ __global__ void __launch_bounds__(32 * kKpWarps, KPMinBlocks<K>::value) kp_kerne
       if (kq[h] >= 0 && tid >= 0 && t == 0) {
         const int64_t pid = (int64_t)kq[h] * p.nt + tid;
         if (v >= 32767 - p.sigma_max_pos) {
+          p.scores[pid] = kRerunMark;
           const int sl = atomicAdd(p.rerun_count, 1);
           if (sl < p.rerun_cap) p.rerun_list[sl] = (int32_t)pid;
         } else {
@@ -294,6 +299,20 @@ __global__ void kp_invalid_kernel(const uint8_t *qbad, int64_t nq, const uint8_t
     if (qbad[k] || tbad[l]) {
       scores[i] = INT32_MIN;
       set_status(status, (qbad[k] == 2 || tbad[l] == 2) ? GA_ERR_ARG : GA_ERR_RESIDUE);
+    }
+  }
+}
+
+// Ids of up to `cap` score entries that still hold kRerunMark (pairs flagged
+// for the int32 rerun after the rerun list overflowed); *count receives the
+// number of marked entries found, which may exceed cap.
+__global__ void kp_collect_marked_kernel(const int32_t *scores, int64_t total, int32_t *list, int32_t cap,
+                                         int32_t *count) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    if (scores[i] == kRerunMark) {
+      const int sl = atomicAdd(count, 1);
+      if (sl < cap) list[sl] = (int32_t)i;
     }
   }
 }

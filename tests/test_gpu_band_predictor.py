@@ -196,6 +196,11 @@ def test_min_w_labels_match_oracle():
         for p in range(len(qs)):
             ref = oracle.min_certified_w_blocks(qs[p], ts[p], mat, al, be, 16)
             assert w[p] == ref, (p, len(qs[p]), len(ts[p]), int(w[p]), ref)
+            # the block-rounded region contains the strict band of the same w
+            # and faces the same outside bound, so it certifies at the strict
+            # minimal width or earlier
+            strict = oracle.min_certified_w(qs[p], ts[p], mat, al, be)
+            assert w[p] <= strict, (p, int(w[p]), strict)
 
 
 def test_trained_predictor_beats_best_constant():

@@ -395,6 +395,29 @@ def test_protein_cross_int16_rerun():
     assert st["pairs_int32_rerun"] >= 1
 
 
+def test_protein_cross_rerun_list_overflow():
+    # more flagged pairs than one rerun list holds (65,536): 260 identical
+    # queries against 260 identical targets (sigma = 127 on the diagonal, so
+    # every such local score is 300 x 127 = 38,100 > 32,767) plus 40 random
+    # targets; the flagged pairs beyond the list are found again from their
+    # marks and recomputed in int32, the others keep their int16 scores
+    rng = np.random.default_rng(17)
+    mat = rng.integers(-4, 5, size=(24, 24)).astype(np.int8)
+    np.fill_diagonal(mat, 127)
+    same = rng.integers(0, 24, size=300).astype(np.uint8)
+    qc, qo = synth.pack_csr([same] * 260)
+    tc, to = synth.pack_csr([same] * 260 + [rng.integers(0, 24, size=300).astype(np.uint8) for _ in range(40)])
+    dev = [torch.from_numpy(a).cuda() for a in (qc, qo, tc, to)]
+    got, st = ga.align_cross(*dev, mat, 11, 1, "local", stats=True)
+    got = got.cpu().numpy().astype(np.int64)
+    assert st["status"] == 0 and st["pairs_int32_rerun"] == 260 * 260
+    assert oracle.score(same, same, mat, 11, 1, "local") == 38100
+    assert np.all(got[:, :260] == 38100)
+    rc, ro = synth.pack_csr([tc[to[k]:to[k + 1]] for k in range(260, 300)])
+    want, _ = oracle.cross(qc[:300], qo[:2], rc, ro, mat, 11, 1, "local", nthreads=NTHREADS)
+    assert_same(got[:, 260:].ravel(), np.tile(want, (260, 1)).ravel(), "non-flagged pairs")
+
+
 @pytest.mark.parametrize("mode", MODES)
 def test_cross_small(mode):
     cr = synth.protein_database(nq=6, qmin=20, qmax=300, nt=80, median=120, seed=31)
