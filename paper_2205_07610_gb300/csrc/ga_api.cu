@@ -835,6 +835,7 @@ struct BandRun {
   uint32_t *keys = nullptr;
   int32_t *sorted = nullptr;
   int max_rows = 0, grid = 0, launches = 0;
+  bool packed = false;  // packed int16x2 kernel (sigma_max + alpha <= kKdMaxStep)
   int64_t stride = 0;
   int2 *bnd = nullptr;
   BandRun(Call &cc, const uint8_t *qc, const int64_t *qo, const uint8_t *tc, const int64_t *to, int64_t np)
@@ -883,7 +884,8 @@ struct BandRun {
       return GA_ERR_CUDA;
     max_rows = h[0];
     if (max_rows > 0) {
-      const int occ = std::max(blocks_per_sm_kc(), 1);
+      packed = std::max(c.sc.smax, 0) + c.sc.alpha <= kKdMaxStep;
+      const int occ = std::max(packed ? blocks_per_sm_kd() : blocks_per_sm_kc(), 1);
       const int64_t want = (npairs + kKcWarps - 1) / kKcWarps;
       grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)c.nsm * occ));
       stride = (int64_t)max_rows + 128;
@@ -923,7 +925,7 @@ struct BandRun {
     kc.bis_lo = bis_lo;
     kc.bis_hi = bis_hi;
     c.dp_begin();
-    const cudaError_t e = launch_kc(kc, grid, c.s);
+    const cudaError_t e = packed ? launch_kd(kc, grid, c.s) : launch_kc(kc, grid, c.s);
     c.dp_end();
     return e == cudaSuccess ? GA_OK : GA_ERR_CUDA;
   }

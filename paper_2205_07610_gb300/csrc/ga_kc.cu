@@ -1,4 +1,5 @@
-// Banded (band-doubling) kernel instantiation.
+// Banded (band-doubling) kernel instantiations: int32 and packed int16x2.
+#include "ga_bandpk.cuh"
 #include "ga_banded.cuh"
 #include "ga_launch.h"
 
@@ -12,6 +13,17 @@ cudaError_t launch_kc(const KCParams &p, int grid, cudaStream_t s) {
 int blocks_per_sm_kc() {
   int n = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kc_kernel<kKcK>, kKcThreads, 0);
+  return n;
+}
+
+cudaError_t launch_kd(const KCParams &p, int grid, cudaStream_t s) {
+  kd_kernel<kKcK><<<grid, kKcThreads, 0, s>>>(p);
+  return cudaGetLastError();
+}
+
+int blocks_per_sm_kd() {
+  int n = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kd_kernel<kKcK>, kKcThreads, 0);
   return n;
 }
 

@@ -8,6 +8,7 @@
 #include "ga_inter.cuh"
 #include "ga_long.cuh"
 #include "ga_longpk.cuh"
+#include "ga_bandpk.cuh"
 
 namespace ga {
 
@@ -60,6 +61,9 @@ int blocks_per_sm_kw_semi();
 struct KCParams;
 cudaError_t launch_kc(const KCParams &p, int grid, cudaStream_t s);
 int blocks_per_sm_kc();
+// Packed banded kernel (sigma_max + alpha <= kKdMaxStep, ga_bandpk.cuh).
+cudaError_t launch_kd(const KCParams &p, int grid, cudaStream_t s);
+int blocks_per_sm_kd();
 
 // Launch / occupancy of tile `bin` (compile-time recursion over the tiles).
 template <class CELL, int MODE, int I = 0>

@@ -100,3 +100,29 @@ def test_banded_protein_falls_back_to_full_dp():
     full, _ = oracle.batch(qc, qo, tc, to, cr.matrix, 11, 1, "global", nthreads=NTHREADS)
     assert np.array_equal(got, full)
     assert (wu == -1).all()
+
+
+def test_banded_packed_and_int32_kernels():
+    # sigma_max + alpha <= 24 runs on the packed int16x2 kernel, larger on the
+    # int32 kernel; both must accept at the oracle's width with its score
+    b = synth.long_dna_pairs(npairs=40, lmin=300, lmax=3000, seed=57)
+    w0s = np.random.default_rng(12).choice([0, 4, 32, 256], size=b.npairs)
+    for al, be in ((5, 2), (22, 2), (23, 2), (40, 3)):
+        _check(synth.Batch(b.q_codes, b.q_off, b.t_codes, b.t_off, synth.dna_matrix(2, -3), al, be, "k"), w0s)
+
+
+def test_banded_single_diagonal_and_super_stage_edges():
+    # equal lengths with w0 = 0 (a band of one diagonal), widths around the
+    # 512 / 1,024 columns of one packed super-stage, and several super-stages
+    rng = np.random.default_rng(13)
+    lens = [100, 511, 512, 513, 1023, 1024, 1025, 2600]
+    qs, ts = [], []
+    for L in lens:
+        q = rng.integers(0, 4, size=L).astype(np.uint8)
+        qs += [q, q]
+        ts += [q.copy(), rng.integers(0, 4, size=L).astype(np.uint8)]
+    qc, qo = synth.pack_csr(qs)
+    tc, to = synth.pack_csr(ts)
+    b = synth.Batch(qc, qo, tc, to, synth.dna_matrix(2, -3), 5, 2, "diag")
+    st = _check(b, np.zeros(b.npairs, dtype=np.int64))
+    assert st["band_retries"] > 0
