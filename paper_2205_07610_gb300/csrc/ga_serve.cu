@@ -67,6 +67,14 @@ __global__ void sv_oneshot_init_kernel(SvRequest *rq, SvScoring *sc_out, const S
 
 inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+// Packed strips keep relative int16 cells exact while sigma_max + alpha <=
+// kSvPkMaxStep.
+int sv_packed_ok(int A, const int8_t *matrix, int alpha) {
+  int smax = 0;
+  for (int i = 0; i < A * A; ++i) smax = std::max(smax, (int)matrix[i]);
+  return smax + alpha <= kSvPkMaxStep ? 1 : 0;
+}
+
 }  // namespace
 
 int sv_strips_for(int64_t m, int64_t n) {
@@ -83,6 +91,7 @@ int sv_align_pair(const uint8_t *q, int64_t m, const uint8_t *t, int64_t n, int 
   sc.alpha = alpha;
   sc.beta = beta;
   std::memcpy(sc.sigma, matrix, (size_t)(A * A));
+  sc.packed = sv_packed_ok(A, matrix, alpha);
   const int nstrips = sv_strips_for(m, n);
   const int64_t R = m < n ? m : n;
   const size_t o_sc = 0, o_rq = align256(o_sc + sizeof(SvScoring));
@@ -103,7 +112,7 @@ int sv_align_pair(const uint8_t *q, int64_t m, const uint8_t *t, int64_t n, int 
   unsigned long long *cseq = (unsigned long long *)(base + o_cseq);
   int2 *cont = (int2 *)(base + o_cont);
 
-  const size_t smem = (size_t)kSvWarps * (size_t)sc.A * kSvW;
+  const size_t smem = (size_t)kSvWarps * (size_t)(sc.A + 2) * kSvW;
   int occ = 0, dev = 0, nsm = 0;
   if (sv_prepare_launch(smem, &occ) != cudaSuccess || cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
@@ -138,7 +147,7 @@ int sv_align_pair(const uint8_t *q, int64_t m, const uint8_t *t, int64_t n, int 
   p.completed = ht + 4;
   p.idle_ns = 0;
   p.wait_ns = 10ll * 1000 * 1000 * 1000;
-  p.prof_bytes = sc.A * kSvW;
+  p.prof_bytes = (sc.A + 2) * kSvW;
   const int grid = std::max(1, std::min((nstrips + kSvWarps - 1) / kSvWarps, nsm * std::max(occ, 1)));
   ks_kernel<<<grid, 32 * kSvWarps, smem, s>>>(p);
   int rc = cudaGetLastError() == cudaSuccess ? GA_OK : GA_ERR_CUDA;
@@ -468,7 +477,7 @@ bool sched_tick(ga_server *S) {
     p.stop = stop_d;
     p.idle_ns = S->idle_ns;
     p.wait_ns = 10ll * 1000 * 1000 * 1000;
-    p.prof_bytes = S->max_A * kSvW;
+    p.prof_bytes = (S->max_A + 2) * kSvW;
     p.cont = S->cont;
     p.cont_seq = S->cont_seq;
     p.cont_cap = S->req_cap;
@@ -627,7 +636,7 @@ int ga_server_create(const ga_server_config *cfg, ga_server **out) {
   }
   S->slots.resize((size_t)S->req_cap);
   S->alloc.reset(new ArenaAlloc(S->arena_bytes));
-  S->smem = (size_t)kSvWarps * (size_t)S->max_A * kSvW;
+  S->smem = (size_t)kSvWarps * (size_t)(S->max_A + 2) * kSvW;
   int occ = 0, nsm = 0;
   if (sv_prepare_launch(S->smem, &occ) != cudaSuccess ||
       cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, S->device) != cudaSuccess) {
@@ -654,6 +663,7 @@ int ga_server_add_scoring(ga_server *S, const ga_scoring *sc, int32_t *scoring_i
     if (sc->matrix[i] < -127) return GA_ERR_ALPHABET;
     h.sigma[i] = sc->matrix[i];
   }
+  h.packed = sv_packed_ok(h.A, h.sigma, h.alpha);
   std::lock_guard<std::mutex> lk(S->mu);
   if ((int)S->sc_host.size() >= GA_SERVE_MAX_SCORINGS) return GA_ERR_ARG;
   if (S->st.submitted > 0 && h.A > S->max_A) return GA_ERR_ARG;  // profile size is fixed once serving
@@ -661,7 +671,7 @@ int ga_server_add_scoring(ga_server *S, const ga_scoring *sc, int32_t *scoring_i
   S->sc_host.push_back(h);
   if (h.A > S->max_A) {
     S->max_A = h.A;
-    S->smem = (size_t)kSvWarps * (size_t)S->max_A * kSvW;
+    S->smem = (size_t)kSvWarps * (size_t)(S->max_A + 2) * kSvW;
     int occ = 0, nsm = 0;
     if (sv_prepare_launch(S->smem, &occ) != cudaSuccess ||
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, S->device) != cudaSuccess)

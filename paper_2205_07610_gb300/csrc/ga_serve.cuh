@@ -31,14 +31,28 @@
 //
 // Substitution scores come from a per-warp int8 profile of the strip in
 // shared memory, P[c][x] = sigma(row residue c, column x), for any alphabet
-// of <= 31 symbols (Sec. 3.1, "scoring profile").  Cells are int32.
+// of <= 31 symbols (Sec. 3.1, "scoring profile").
+//
+// Cells.  A request whose scoring has sigma_max + alpha <= kSvPkMaxStep runs
+// its strips packed (sv_strip_pk): the two 256-column halves of a strip sit
+// in the low and high int16 halves of every register, the high half 32 rows
+// behind the low one, each value stored relative to a per-lane, per-half
+// int32 base that is renormalised every kKwRenorm rows, exactly as in the
+// packed long-pair kernel (ga_longpk.cuh: one rotating shuffle, lane 0
+// joining the strip's left edge and lane 31's low half, virtual rows before
+// the high half's first row, local mode's zero folded into E).  Other
+// scorings run the int32 strip (sv_strip).  Strip edges are absolute int32
+// in both, so the two strip kinds share the edge and progress protocol.
 #pragma once
 
 #include "ga_dp.cuh"
+#include "ga_longpk.cuh"
 
 namespace ga {
 
 constexpr int kSvK = 16;
+constexpr int kSvKp = 8;          // packed strips: 8 packed columns per lane and half
+constexpr int kSvPkMaxStep = 128; // largest sigma_max + alpha of a packed strip
 constexpr int kSvW = 32 * kSvK;  // columns per strip
 constexpr int kSvWarps = 4;      // warps per block
 constexpr int kSvMaxStrips = 128;
@@ -46,7 +60,8 @@ constexpr int kSvMaxLen = kSvMaxStrips * kSvW;  // longer sequence <= 65536
 constexpr int kSvContRows = 96;  // edge rows published before the next strip is queued
 
 struct SvScoring {
-  int32_t A, alpha, beta, pad;
+  int32_t A, alpha, beta;
+  int32_t packed;         // 1: strips run sv_strip_pk (sigma_max + alpha <= kSvPkMaxStep)
   int8_t sigma[32 * 32];  // sigma(query code, target code), A x A row-major
 };
 
@@ -98,7 +113,7 @@ struct SvParams {
   unsigned long long *completed;
   int64_t idle_ns;
   int64_t wait_ns;
-  int32_t prof_bytes;  // per warp: max A * kSvW (rows of real residues only)
+  int32_t prof_bytes;  // per warp: (max A + 2) * kSvW (real residues, pad row, virtual row)
 };
 
 __device__ __forceinline__ uint64_t sv_now() {
@@ -146,7 +161,7 @@ __device__ __forceinline__ bool sv_wait_at_least(const int32_t *flag, int need, 
 struct SvView {
   const uint8_t *rowraw, *colraw;
   int2 *edges;
-  int R, C, sw, A, alpha, beta, nstrips;
+  int R, C, sw, A, alpha, beta, nstrips, packed;
   const int8_t *sigma;
 };
 
@@ -337,11 +352,257 @@ __device__ int sv_strip(const SvParams &p, SvRequest *rq, int slot, const SvView
   else return __reduce_max_sync(0xffffffffu, gscore);
 }
 
+// One strip of one request in packed int16x2 cells (see the file comment):
+// returns what sv_strip returns.
+template <int MODE>
+__device__ int sv_strip_pk(const SvParams &p, SvRequest *rq, int slot, const SvView &v, int s, int t,
+                           uint8_t *prof, uint8_t *colc, int2 *in_ring, int2 *out_ring,
+                           uint32_t *row_ring /* [256] */) {
+  constexpr int K = kSvKp, WH = 32 * kSvKp, W = kSvW;
+  static_assert(2 * WH == W, "a packed strip is two halves of the strip");
+  constexpr int kRing = 256;
+  const int R = v.R, C = v.C, A = v.A, alpha = v.alpha, beta = v.beta;
+  const int col0 = s * W;
+  const int2 *edge_in = (s > 0) ? v.edges + (size_t)(s - 1) * (size_t)(R + 1) : nullptr;
+  int2 *edge_out = (s + 1 < v.nstrips) ? v.edges + (size_t)s * (size_t)(R + 1) : nullptr;
+  const uint32_t NB = pk16(-beta, -beta);
+  const uint32_t NAc = pk16(-alpha, -alpha);
+  const uint32_t NEGV = pk16(kNeg16, kNeg16);
+  auto h0 = [&](int c) -> int { return (MODE == kModeGlobal && c > 0) ? -alpha - beta * (c - 1) : 0; };
+
+  // ---- column codes and the strip's profile: rows 0..A-1, pad row A
+  // (sigma = 0) and virtual row A+1 (leaves row 0 unchanged) --------------
+  for (int x = t; x < W; x += 32) {
+    const int col = col0 + x;
+    int c = A;  // pad
+    if (col < C) {
+      c = __ldcg(v.colraw + col);
+      if (c >= A) {
+        atomicCAS(&rq->status, 0, GA_ERR_RESIDUE);
+        c = A;
+      }
+    }
+    colc[x] = (uint8_t)c;
+  }
+  __syncwarp();
+  for (int e = t; e < (A + 2) * W; e += 32) {
+    const int c = e / W, x = e - c * W;
+    const int cc = colc[x];
+    int val = 0;
+    if (c < A && cc < A) val = v.sw ? v.sigma[cc * A + c] : v.sigma[c * A + cc];
+    else if (c == A + 1 && MODE == kModeGlobal) val = -beta;
+    prof[e] = (uint8_t)(int8_t)val;
+  }
+
+  int b[2];
+  b[0] = h0(col0 + t * K + 1);
+  b[1] = h0(col0 + WH + t * K + 1);
+  uint32_t na[MODE == kModeSemi ? K : 1];
+  uint32_t H[K], E[K];
+#pragma unroll
+  for (int j = 0; j < K; ++j) {
+    if constexpr (MODE == kModeSemi) {
+      const int c0 = col0 + t * K + j, c1 = c0 + WH;
+      na[j] = pk16(c0 == C - 1 ? 0 : -alpha, c1 == C - 1 ? 0 : -alpha);
+    }
+    const int hv = (MODE == kModeGlobal) ? -beta * j : 0;
+    H[j] = pk16(hv, hv);
+    const int ev = (MODE == kModeLocal) ? 0 : hv - alpha;
+    E[j] = pk16(ev, ev);
+  }
+  uint32_t Z = 0;
+  uint32_t D = pk16(t == 0 ? 0 : h0(col0 + t * K + 1 - K) - b[0], h0(col0 + WH + t * K + 1 - K) - b[1]);
+  const int ocol = C - 1 - col0;
+  const int ohalf = ocol >= WH ? 1 : 0;
+  const bool owner = ocol >= 0 && ocol < W && t == (ocol - ohalf * WH) / K;
+  const int oj = (ocol - ohalf * WH) % K;
+  uint32_t best = 0;
+  int best_abs = 0, rowmax = 0, gscore = INT_MIN;
+
+  auto left_row = [&](int r) -> int2 {  // (H(r, col0), F(r, col0 + 1)), absolute
+    int2 lv;
+    if (s == 0) {
+      lv.x = (MODE == kModeGlobal) ? ((r == 0) ? 0 : -alpha - beta * (r - 1)) : 0;
+      lv.y = lv.x - alpha;
+    } else {
+      lv = in_ring[(r - 1) & 63];
+    }
+    return lv;
+  };
+  auto load_batch = [&](int bb) {  // left edge rows 32bb+1 .. 32bb+32, after waiting for them
+    if (s == 0) return;
+    const int need = ::min(R, 32 * bb + 32);
+    if (32 * bb + 1 > R) return;
+    const int32_t *pp = &rq->progress[s - 1];
+    if (t == 0 && !sv_wait_at_least(pp, need, (uint64_t)p.wait_ns)) atomicCAS(&rq->status, 0, GA_ERR_TIMEOUT);
+    __syncwarp();
+    (void)sv_ld_acquire(pp);
+    const int r = 32 * bb + 1 + t;
+    if (r <= R) in_ring[(r - 1) & 63] = __ldcg(edge_in + r);
+  };
+  auto fill_rows = [&](int bb) {  // row codes; pad code A past the last row
+    const int r = 32 * bb + 1 + t;
+    uint32_t c = (uint32_t)A;
+    if (r <= R) {
+      c = __ldcg(v.rowraw + r - 1);
+      if (c >= (uint32_t)A) {
+        atomicCAS(&rq->status, 0, GA_ERR_RESIDUE);
+        c = 0;
+      }
+    }
+    row_ring[r & (kRing - 1)] = c;
+  };
+  bool queued = false;
+  auto publish = [&](int rows) {
+    __threadfence();
+    __syncwarp();
+    if (t == 0) {
+      sv_st_release(&rq->progress[s], rows);
+      if (!queued && rows >= ::min(R, kSvContRows)) {
+        const unsigned long long idx = atomicAdd(p.cont_tail, 1ull);
+        const int64_t e = (int64_t)(idx % (unsigned long long)p.cont_cap);
+        p.cont[e] = make_int2(slot, s + 1);
+        __threadfence();
+        sv_st_release64(p.cont_seq + e, idx + 1);
+      }
+    }
+    queued = queued || rows >= ::min(R, kSvContRows);
+  };
+
+  row_ring[(-t) & (kRing - 1)] = (uint32_t)(A + 1);  // rows 0 .. -31: virtual
+  load_batch(0);
+  fill_rows(0);
+  fill_rows(1);
+  __syncwarp();
+
+  const int hd0 = h0(col0 + t * K) - b[0], hd1 = h0(col0 + WH + t * K) - b[1];
+  uint32_t Hdiag = pk16(hd0, hd1);
+  uint32_t Hleft = Hdiag;
+  uint32_t Fin = NEGV;
+  if (t == 0) {
+    const int2 l1 = left_row(1);
+    Hleft = pk16(l1.x - b[0], hd1);
+    Fin = pk16(l1.y - b[0], kNeg16);
+  }
+
+  const int nit = R + 63;
+  for (int it = 0; it < nit; ++it) {
+    if ((it & 31) == 0) {
+      __syncwarp();
+      load_batch(it / 32 + 1);
+      fill_rows(it / 32 + 2);
+      if (it >= 96 && edge_out) {  // lane 31's high-half rows it-95 .. it-64
+        const int r = it - 95 + t;
+        edge_out[r] = out_ring[(r - 1) & 63];
+        publish(it - 64);
+      }
+      if ((it & (kKwRenorm - 1)) == 0 && it > 0) {
+        const int d0 = lo16(H[0]), d1 = hi16(H[0]);
+        if constexpr (MODE == kModeLocal) {
+          best_abs = ::max(best_abs, ::max(lo16(best) + b[0], hi16(best) + b[1]));
+          best = NEGV;
+        }
+        b[0] += d0;
+        b[1] += d1;
+        const uint32_t dl = pk16(-d0, -d1);
+#pragma unroll
+        for (int j = 0; j < K; ++j) {
+          H[j] = __vadd2(H[j], dl);
+          E[j] = __vadd2(E[j], dl);
+        }
+        Hdiag = __vadd2(Hdiag, dl);
+        Hleft = __vadd2(Hleft, dl);
+        Fin = __vadd2(Fin, dl);
+        if constexpr (MODE == kModeLocal) {
+          Z = pk16(::max(-b[0], kNeg16), ::max(-b[1], kNeg16));
+#pragma unroll
+          for (int j = 0; j < K; ++j) E[j] = __vmaxs2(E[j], Z);
+        }
+        const int nb0 = __shfl_sync(0xffffffffu, b[0], (t + 31) & 31);
+        const int nb1 = __shfl_sync(0xffffffffu, b[1], (t + 31) & 31);
+        D = (t == 0) ? pk16(0, nb0 - b[1]) : pk16(nb0 - b[0], nb1 - b[1]);
+      }
+      __syncwarp();
+    }
+    const int rlo = it - t + 1, rhi = rlo - 32;
+    uint32_t Hout, Fout;
+    if (rlo >= 1) {
+      const uint32_t cl = row_ring[rlo & (kRing - 1)], ch = row_ring[rhi & (kRing - 1)];
+      const uint2 wl = *reinterpret_cast<const uint2 *>(prof + (size_t)cl * W + t * K);
+      const uint2 wh = *reinterpret_cast<const uint2 *>(prof + (size_t)ch * W + WH + t * K);
+      Fout = pk_row<MODE, K>(
+          H, E, Hdiag, Fin, NB, Z, best,
+          [&](int j) -> uint32_t {
+            return prmt(j < 4 ? wl.x : wl.y, j < 4 ? wh.x : wh.y, sext_sel<CellS16x2>(j & 3));
+          },
+          [&](int j) -> uint32_t {
+            if constexpr (MODE == kModeSemi) return na[j];
+            else return NAc;
+          });
+      Hout = H[K - 1];
+      if constexpr (MODE != kModeLocal) {
+        if (rlo == R || rhi == R) {
+          const int h = (rhi == R) ? 1 : 0;
+          if constexpr (MODE == kModeGlobal) {
+            if (owner && h == ohalf) {
+              uint32_t g = H[0];
+#pragma unroll
+              for (int j = 1; j < K; ++j)
+                if (j == oj) g = H[j];
+              gscore = h ? hi16(g) + b[1] : lo16(g) + b[0];
+            }
+          } else {
+            uint32_t mx = H[0];
+#pragma unroll
+            for (int j = 1; j < K; ++j) mx = __vmaxs2(mx, H[j]);
+            rowmax = ::max(rowmax, h ? hi16(mx) + b[1] : lo16(mx) + b[0]);
+          }
+        }
+      }
+    } else {
+      Hout = H[K - 1];
+      Fout = NEGV;
+    }
+    if (t == 31 && rhi >= 1 && rhi <= R) out_ring[(rhi - 1) & 63] = make_int2(hi16(Hout) + b[1], hi16(Fout) + b[1]);
+    Hdiag = Hleft;
+    uint32_t hs = __shfl_sync(0xffffffffu, Hout, (t + 31) & 31);
+    uint32_t fs = __shfl_sync(0xffffffffu, Fout, (t + 31) & 31);
+    if (t == 0) {
+      int lx = kNeg16, ly = kNeg16;
+      if (it + 2 <= R) {
+        const int2 lv = left_row(it + 2);
+        lx = lv.x - b[0];
+        ly = lv.y - b[0];
+      }
+      hs = prmt((uint32_t)lx, hs, 0x5410u);
+      fs = prmt((uint32_t)ly, fs, 0x5410u);
+    }
+    Hleft = __vadd2(hs, D);
+    Fin = __vadd2(fs, D);
+  }
+  __syncwarp();
+  if (edge_out) {
+    const int last = ((nit - 1) / 32) * 32;
+    const int first = (last >= 96) ? last - 63 : 1;
+    for (int r = first + t; r <= R; r += 32) edge_out[r] = out_ring[(r - 1) & 63];
+    publish(R);
+  }
+  __syncwarp();
+  if constexpr (MODE == kModeLocal) {
+    best_abs = ::max(best_abs, ::max(lo16(best) + b[0], hi16(best) + b[1]));
+    return group_max<32>(best_abs);
+  } else if constexpr (MODE == kModeSemi) {
+    return group_max<32>(rowmax);
+  } else {
+    return __reduce_max_sync(0xffffffffu, gscore);
+  }
+}
+
 __global__ void __launch_bounds__(32 * kSvWarps) ks_kernel(const __grid_constant__ SvParams p) {
   extern __shared__ __align__(16) uint8_t sv_smem[];
   __shared__ int2 in_ring_s[kSvWarps][64];
   __shared__ int2 out_ring_s[kSvWarps][64];
-  __shared__ uint32_t row_ring_s[kSvWarps][128];
+  __shared__ uint32_t row_ring_s[kSvWarps][256];
   __shared__ __align__(16) uint8_t colc_s[kSvWarps][kSvW];
   const int warp = threadIdx.x >> 5, t = threadIdx.x & 31;
   uint8_t *prof = sv_smem + (size_t)warp * (size_t)p.prof_bytes;
@@ -420,11 +681,22 @@ __global__ void __launch_bounds__(32 * kSvWarps) ks_kernel(const __grid_constant
     v.alpha = __ldcg(&p.scorings[sc].alpha);
     v.beta = __ldcg(&p.scorings[sc].beta);
     v.sigma = p.scorings[sc].sigma;
+    v.packed = __ldcg(&p.scorings[sc].packed);
 
     int val;
     if (v.R == 0 || v.C == 0) {  // closed forms, any mode
       const int len = v.R + v.C;
       val = (mode == kModeGlobal && len) ? -(v.alpha + v.beta * (len - 1)) : 0;
+    } else if (v.packed) {
+      if (mode == kModeLocal)
+        val = sv_strip_pk<kModeLocal>(p, rq, slot, v, strip, t, prof, colc_s[warp], in_ring_s[warp],
+                                      out_ring_s[warp], row_ring_s[warp]);
+      else if (mode == kModeGlobal)
+        val = sv_strip_pk<kModeGlobal>(p, rq, slot, v, strip, t, prof, colc_s[warp], in_ring_s[warp],
+                                       out_ring_s[warp], row_ring_s[warp]);
+      else
+        val = sv_strip_pk<kModeSemi>(p, rq, slot, v, strip, t, prof, colc_s[warp], in_ring_s[warp],
+                                     out_ring_s[warp], row_ring_s[warp]);
     } else if (mode == kModeLocal) {
       val = sv_strip<kModeLocal>(p, rq, slot, v, strip, t, prof, colc_s[warp], in_ring_s[warp],
                                  out_ring_s[warp], row_ring_s[warp]);
