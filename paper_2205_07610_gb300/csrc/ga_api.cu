@@ -296,9 +296,10 @@ struct KnownRange {
 };
 
 int prepare_set(Call &c, const uint8_t *codes, const int64_t *off, int64_t nseq, uint32_t **packed,
-                uint8_t **bad, int32_t *invalid, KnownRange kr = KnownRange()) {
+                uint8_t **bad, int32_t *invalid, KnownRange kr = KnownRange(), uint32_t **packed5 = nullptr) {
   *bad = c.al.get<uint8_t>((size_t)nseq + 1);
   *packed = nullptr;
+  if (packed5) *packed5 = nullptr;
   if (c.al.failed) return GA_ERR_OOM;
   if (nseq == 0) return GA_OK;
   // the set's residues are codes[off[0] .. off[nseq]) (off[0] > 0 when the
@@ -321,7 +322,16 @@ int prepare_set(Call &c, const uint8_t *codes, const int64_t *off, int64_t nseq,
   }
   const int64_t nwords = (total + 15) / 16 - start / 16;
   const int64_t pblocks = std::min<int64_t>((nwords + 255) / 256, (int64_t)c.nsm * 16);
-  if (nwords > 0) {
+  if (packed5 && !c.dna && total > start) {
+    // 5-bit words (the packing also validates the codes)
+    *packed5 = c.al.get<uint32_t>((size_t)((total + 5) / 6 + 16));
+    if (c.al.failed) return GA_ERR_OOM;
+    const int64_t chunks = ((total + 5) / 6 - start / 6 / 8 * 8 + 7) / 8;
+    const int64_t b5 = std::min<int64_t>((chunks + 255) / 256, (int64_t)c.nsm * 16);
+    flat_pack5_kernel<<<(unsigned)std::max<int64_t>(b5, 1), 256, 0, c.s>>>(codes, start, total, c.sc.A,
+                                                                           *packed5, invalid);
+    ++c.launches;
+  } else if (nwords > 0) {
     flat_pack_kernel<<<(unsigned)std::max<int64_t>(pblocks, 1), 256, 0, c.s>>>(codes, start, total,
                                                                                c.sc.A, *packed, invalid);
     ++c.launches;
@@ -1052,7 +1062,9 @@ int cross_protein_local(Call &c, const uint8_t *q_codes, const int64_t *q_off, i
   int rc;
   SetView Q{q_codes, q_off, nullptr, nullptr}, T{t_codes, t_off, nullptr, nullptr};
   if ((rc = prepare_set(c, q_codes, q_off, nq, &Q.packed, &Q.bad, &c.small->invalid_q))) return rc;
-  if ((rc = prepare_set(c, t_codes, t_off, nt, &T.packed, &T.bad, &c.small->invalid_t))) return rc;
+  uint32_t *t_packed5 = nullptr;
+  if ((rc = prepare_set(c, t_codes, t_off, nt, &T.packed, &T.bad, &c.small->invalid_t, KnownRange(), &t_packed5)))
+    return rc;
   if (nt >= (1ll << 31) - 64 || nq * nt >= (1ll << 31) - 64) return GA_ERR_ARG;
   uint32_t *keys = c.al.get<uint32_t>((size_t)nt);
   int32_t *sorted = c.al.get<int32_t>((size_t)nt);
@@ -1131,6 +1143,7 @@ int cross_protein_local(Call &c, const uint8_t *q_codes, const int64_t *q_off, i
   kp.q_codes = q_codes;
   kp.q_off = q_off;
   kp.t_codes = t_codes;
+  kp.t_packed5 = t_packed5;
   kp.t_off = t_off;
   kp.t_sorted = sorted;
   kp.ntv = ntv;

@@ -105,6 +105,57 @@ __global__ void flat_pack_kernel(const uint8_t *codes, int64_t start, int64_t to
   flat_pack_body(codes, start, total, A, packed, invalid);
 }
 
+// Flat 5-bit packing of the code buffer for alphabets of up to 32 symbols
+// (protein): residue x of the buffer sits in word x / 6 at bits 5 (x % 6)
+// .. 5 (x % 6) + 4, six residues per word.  One thread per 8 words (48
+// residues: three 16-byte loads when the chunk is aligned and complete, two
+// 16-byte stores); any code >= A raises *invalid as in the 2-bit packing.
+__global__ void flat_pack5_kernel(const uint8_t *codes, int64_t start, int64_t total, int A,
+                                  uint32_t *packed5, int32_t *invalid) {
+  const int64_t nwords = (total + 5) / 6;
+  const int64_t w_first = start / 6 / 8 * 8;  // chunks of 8 words from an 8-word boundary
+  const bool aligned16 = (reinterpret_cast<uintptr_t>(codes) & 15u) == 0;
+  bool bad = false;
+  for (int64_t w0 = w_first + 8 * ((int64_t)blockIdx.x * blockDim.x + threadIdx.x); w0 < nwords;
+       w0 += 8 * (int64_t)gridDim.x * blockDim.x) {
+    const int64_t s0 = w0 * 6;  // 48 residues, s0 a multiple of 48 (16-byte aligned offset)
+    uint8_t r[48];
+    if (aligned16 && s0 + 48 <= total && s0 >= start) {
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const uint4 v = __ldg(reinterpret_cast<const uint4 *>(codes + s0) + k);
+        const uint32_t x[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int i = 0; i < 16; ++i) r[16 * k + i] = (uint8_t)(x[i >> 2] >> (8 * (i & 3)));
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < 48; ++i) r[i] = (s0 + i >= start && s0 + i < total) ? codes[s0 + i] : (uint8_t)0;
+    }
+    uint32_t out[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      uint32_t word = 0;
+#pragma unroll
+      for (int i = 0; i < 6; ++i) {
+        const uint32_t c = r[6 * k + i];
+        bad |= c >= (uint32_t)A;
+        word |= (c & 31u) << (5 * i);
+      }
+      out[k] = word;
+    }
+    if (w0 + 8 <= nwords) {
+      reinterpret_cast<uint4 *>(packed5 + w0)[0] = make_uint4(out[0], out[1], out[2], out[3]);
+      reinterpret_cast<uint4 *>(packed5 + w0)[1] = make_uint4(out[4], out[5], out[6], out[7]);
+    } else {
+#pragma unroll
+      for (int k = 0; k < 8; ++k)
+        if (w0 + k < nwords) packed5[w0 + k] = out[k];
+    }
+  }
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(invalid, 1);
+}
+
 // Batch plans: the residue range [off[0], off[nseq]) of a set is read on
 // the device and clamped to the plan's capacity `cap` (residues at or
 // beyond cap are never read; validation marks their sequences).

@@ -47,6 +47,7 @@ struct KPParams {
   const uint8_t *q_codes;
   const int64_t *q_off;
   const uint8_t *t_codes;
+  const uint32_t *t_packed5;  // the target codes packed 5 bits each (flat_pack5_kernel)
   const int64_t *t_off;
   const int32_t *queries;   // query ids of this launch; entries 2i, 2i+1 form pair i
   int32_t nqb;
@@ -132,6 +133,10 @@ __global__ void __launch_bounds__(32 * kKpWarps, KPMinBlocks<K>::value) kp_kerne
     const int tid = slot < p.ntv ? p.t_sorted[slot] : -1;
     const int64_t tstart = tid >= 0 ? p.t_off[tid] : 0;
     const int len = tid >= 0 ? (int)(p.t_off[tid + 1] - tstart) : 0;
+    // the target's first packed word and its position in it: row r's code is
+    // residue trem + r - 1 of the words from tword on (32-bit arithmetic)
+    const uint32_t *tword = p.t_packed5 + tstart / 6;
+    const int trem = (int)(tstart % 6);
     const int Rw = __reduce_max_sync(0xffffffffu, (unsigned)len);  // rows of this warp
     const int nstage = (::max(m[0], m[1]) + W - 1) / W;            // the same for the whole block
     T best = Cell::splat(0);
@@ -167,7 +172,11 @@ __global__ void __launch_bounds__(32 * kKpWarps, KPMinBlocks<K>::value) kp_kerne
       // ---- row codes, refilled G rows ahead -----------------------------
       auto fill_batch = [&](int b) {
         const int r = b * G + 1 + t;
-        const uint8_t c = r <= len ? p.t_codes[tstart + r - 1] : (uint8_t)A;
+        uint8_t c = (uint8_t)A;
+        if (r <= len) {
+          const unsigned x = (unsigned)(trem + r - 1), wq = x / 6u;
+          c = (uint8_t)((__ldg(tword + wq) >> (5u * (x - 6u * wq))) & 31u);
+        }
         const int sl = r & (kRing - 1);
         ring[sl] = c;
         if (sl < G) ring[sl + kRing] = c;

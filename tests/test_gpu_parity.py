@@ -395,6 +395,30 @@ def test_protein_cross_int16_rerun():
     assert st["pairs_int32_rerun"] >= 1
 
 
+def test_protein_cross_packed5_positions():
+    # the targets reach the kernel packed 5 bits each, six residues per word:
+    # targets of every length 1..41 (and 82 more) start at every position
+    # mod 6, the set
+    # starts 7 residues into its buffer (a chunk of a larger set), and every
+    # code of the 24-symbol alphabet appears; the queries span two tiles
+    rng = np.random.default_rng(29)
+    lens = np.concatenate([np.arange(1, 42), rng.integers(1, 42, size=82)])
+    ts = [rng.integers(0, 24, size=L).astype(np.uint8) for L in lens]
+    tc, to = synth.pack_csr(ts)
+    pre = rng.integers(0, 24, size=7).astype(np.uint8)
+    tc2 = np.concatenate([pre, tc])
+    to2 = to + 7
+    qs = [rng.integers(0, 24, size=L).astype(np.uint8) for L in (90, 150, 300, 700)]
+    qc, qo = synth.pack_csr(qs)
+    mat = synth.blosum62()
+    dev = [torch.from_numpy(a).cuda() for a in (qc, qo, tc2, to2)]
+    got, st = ga.align_cross(*dev, mat, 11, 1, "local", stats=True)
+    assert st["status"] == 0
+    assert sorted({int(o) % 6 for o in to2[:-1]}) == list(range(6))
+    want, _ = oracle.cross(qc, qo, tc, to, mat, 11, 1, "local", nthreads=NTHREADS)
+    assert_same(got.cpu().numpy().ravel(), want.ravel(), "packed5 targets")
+
+
 def test_protein_cross_rerun_list_overflow():
     # more flagged pairs than one rerun list holds (65,536): 260 identical
     # queries against 260 identical targets (sigma = 127 on the diagonal, so
