@@ -62,21 +62,28 @@ extern "C" {
 /* Tiles of the inter-sequence kernels: 16 lanes x K columns per pair,
  * K = 6, 7, ..., 20, 24, 32 for tile index 0..16. */
 #define GA_TILE_COUNT 17
+/* Packed tiles that also exist with another lane-group size of the same
+ * width: tiles 0..6 with 8 lanes x 2K columns, tiles 10, 12, 14, 15, 16
+ * with 32 lanes x K/2 columns. */
+#define GA_TILE_ALT_MASK 0x1d47Fu
 
 /* Launch configuration of a plan.  A set bit k of tiles16 makes tile k a
  * bin of the packed int16x2 kernel: a pair goes to the narrowest active
  * tile at least as wide as its shorter sequence (bin edges = the widths of
  * the active tiles); tiles32 likewise for the int32 kernel.  Pairs wider
- * than every active tile run on the intra-sequence kernel.  concurrent = 1
- * runs the bins as parallel branches (side streams, graph branches), so
- * that one bin's last tasks overlap the next bin's first; 0 runs them one
- * after another on the caller's stream.  Every tuning gives the same
- * (exact) scores; only the time differs. */
+ * than every active tile run on the intra-sequence kernel.  A set bit k of
+ * lanes_alt (only bits of GA_TILE_ALT_MASK) runs packed tile k with its
+ * alternative lane-group size: fewer lanes per pair shorten the wavefront
+ * fill of every pair at the cost of more registers per lane, more lanes do
+ * the opposite.  concurrent = 1 runs the bins as parallel branches (side
+ * streams, graph branches), so that one bin's last tasks overlap the next
+ * bin's first; 0 runs them one after another on the caller's stream.
+ * Every tuning gives the same (exact) scores; only the time differs. */
 typedef struct {
     uint32_t tiles16;
     uint32_t tiles32;
     int32_t concurrent;
-    int32_t reserved;
+    uint32_t lanes_alt;
 } ga_tuning;
 
 typedef struct ga_plan ga_plan;
@@ -118,7 +125,8 @@ int ga_plan_autotune(ga_plan *plan, const uint8_t *q_codes, const int64_t *q_off
                      float *ms_best);
 
 int ga_plan_get_tuning(const ga_plan *plan, ga_tuning *out);
-/* Sets a tuning (drops a captured graph).  GA_ERR_ARG for bits >= GA_TILE_COUNT. */
+/* Sets a tuning (drops a captured graph).  GA_ERR_ARG for bits >= GA_TILE_COUNT
+ * or lanes_alt bits outside GA_TILE_ALT_MASK. */
 int ga_plan_set_tuning(ga_plan *plan, const ga_tuning *tuning);
 
 int ga_plan_destroy(ga_plan *plan);

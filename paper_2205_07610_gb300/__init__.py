@@ -15,7 +15,7 @@ from ._binding import (LOCAL, GLOBAL, SEMIGLOBAL, EXPORTED, GotohError, Scoring,
                        lib_path, load, make_scoring, strerror, version, BAND_NFEAT, MLP_NPARAMS,
                        band_features, band_min_w, band_predict, mlp_forward, mlp_loss_grad,
                        mlp_train, mlp_cast, Server, RESULT_DTYPE, SERVE_MAX_LEN, Plan, Tuning,
-                       TILE_K)
+                       TILE_K, TILE_ALT_MASK)
 from .build import build
 
 __all__ = [
@@ -24,5 +24,5 @@ __all__ = [
     "NOALLOC_MAX_LEN", "probe_bounded_wait", "lib_path", "load",
     "make_scoring", "strerror", "version", "build", "BAND_NFEAT", "MLP_NPARAMS", "band_features",
     "band_min_w", "band_predict", "mlp_forward", "mlp_loss_grad", "mlp_train", "mlp_cast",
-    "Server", "RESULT_DTYPE", "SERVE_MAX_LEN", "Plan", "Tuning", "TILE_K",
+    "Server", "RESULT_DTYPE", "SERVE_MAX_LEN", "Plan", "Tuning", "TILE_K", "TILE_ALT_MASK",
 ]

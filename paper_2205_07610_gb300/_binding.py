@@ -38,6 +38,7 @@ EXPORTED = ("ga_align_batch", "ga_align_batch_modes", "ga_align_batch_host", "ga
             "ga_plan_launch", "ga_plan_stats", "ga_plan_autotune", "ga_plan_get_tuning",
             "ga_plan_set_tuning", "ga_plan_destroy", "ga_probe_bounded_wait")
 TILE_K = (6, 7, 8, 9, 10, 11, 12, 13, 14, 15, 16, 17, 18, 19, 20, 24, 32)  # columns per lane of tile 0..16
+TILE_ALT_MASK = 0x1D47F  # tiles with an alternative lane-group size (8 lanes: 0..6; 32 lanes: 10, 12, 14..16)
 SERVE_MAX_LEN = 65536
 BAND_NFEAT = 32
 MLP_NPARAMS = 6337
@@ -78,13 +79,15 @@ class ServerStats(ctypes.Structure):
 
 
 class Tuning(ctypes.Structure):
-    """ga_tuning: active tiles of the int16x2 / int32 bins and bin concurrency."""
+    """ga_tuning: active tiles of the int16x2 / int32 bins, packed tiles run
+    with their alternative lane-group size, and bin concurrency."""
     _fields_ = [("tiles16", ctypes.c_uint32), ("tiles32", ctypes.c_uint32),
-                ("concurrent", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("concurrent", ctypes.c_int32), ("lanes_alt", ctypes.c_uint32)]
 
     def as_dict(self) -> dict:
         return {"tiles16": [TILE_K[k] for k in range(len(TILE_K)) if self.tiles16 >> k & 1],
                 "tiles32": [TILE_K[k] for k in range(len(TILE_K)) if self.tiles32 >> k & 1],
+                "lanes_alt": [TILE_K[k] for k in range(len(TILE_K)) if self.lanes_alt >> k & 1],
                 "concurrent": int(self.concurrent)}
 
 

@@ -525,6 +525,24 @@ int launch_prepare(Call &c, ChunkPlan &p) {
   return GA_OK;
 }
 
+// Packed tiles that the batch entry points run with their alternative
+// lane-group size (8 lanes x 2K columns for tiles K = 7..11): measured on
+// GB300 on 1M mutated DNA pairs of 100..300 residues in all three modes,
+// each of these tiles is 0.1..0.5 % faster that way, the wide tiles with
+// 32 lanes 1..2.4 % slower.  Plans choose their own (ga_plan_autotune).
+constexpr uint32_t kEagerLanesAlt = 0x3eu;
+static_assert((kEagerLanesAlt & ~kKaAltTiles) == 0, "only tiles with an alternative");
+
+int plan_occupancy_alt(int mode, int bin) {
+  return mode == GA_LOCAL ? blocks_per_sm_ka16alt_local(bin) : mode == GA_GLOBAL ? blocks_per_sm_ka16alt_global(bin)
+                                                                                  : blocks_per_sm_ka16alt_semi(bin);
+}
+
+cudaError_t plan_launch_ka_alt(int mode, int tile, const KAParams &ka, int grid, cudaStream_t s) {
+  return mode == GA_LOCAL ? launch_ka16alt_local(tile, ka, grid, s) : mode == GA_GLOBAL ? launch_ka16alt_global(tile, ka, grid, s)
+                                                                                        : launch_ka16alt_semi(tile, ka, grid, s);
+}
+
 KAParams make_ka(Call &c, const SetView &Q, const SetView &T, const ChunkPlan &p) {
   KAParams ka{};
   ka.packed_q = Q.packed;
@@ -554,10 +572,13 @@ int launch_bin(Call &c, const SetView &Q, const SetView &T, ChunkPlan &p, int cl
   KAParams ka = make_ka(c, Q, T, p);
   ka.range = &p.sm->ranges[2 * (cls * kBins + bin)];
   ka.task_counter = &p.sm->counters[p.counter++];
-  const int ppt = (cls == 0 ? 2 : 1) * (32 / kKaG);
+  const bool alt = cls == 0 && (kEagerLanesAlt >> bin & 1u);
+  const int ppt = (cls == 0 ? 2 : 1) * (32 / (alt ? ka_alt_g(bin) : kKaG));
   const int64_t ntasks = (cnt + ppt - 1) / ppt;
   int occ;
-  if (cls == 0) {
+  if (alt) {
+    occ = plan_occupancy_alt(p.mode, bin);
+  } else if (cls == 0) {
     occ = p.mode == GA_LOCAL ? blocks_per_sm_ka16_local(bin)
         : p.mode == GA_GLOBAL ? blocks_per_sm_ka16_global(bin)
                               : blocks_per_sm_ka16_semi(bin);
@@ -570,7 +591,9 @@ int launch_bin(Call &c, const SetView &Q, const SetView &T, ChunkPlan &p, int cl
   const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)c.nsm * std::max(occ, 1)));
   cudaError_t e;
   const cudaStream_t ls = fk.launch_begin();
-  if (cls == 0) {
+  if (alt) {
+    e = plan_launch_ka_alt(p.mode, bin, ka, grid, ls);
+  } else if (cls == 0) {
     e = p.mode == GA_LOCAL ? launch_ka16_local(bin, ka, grid, ls)
       : p.mode == GA_GLOBAL ? launch_ka16_global(bin, ka, grid, ls)
                             : launch_ka16_semi(bin, ka, grid, ls);
@@ -1239,6 +1262,7 @@ int cross_protein_local(Call &c, const uint8_t *q_codes, const int64_t *q_off, i
 
 constexpr int kPlanSide = 4;  // side streams for concurrent bins
 static_assert(GA_TILE_COUNT == kKaNumBins, "one tuning bit per inter-sequence tile");
+static_assert(GA_TILE_ALT_MASK == kKaAltTiles, "the header lists the tiles with an alternative lane-group size");
 
 struct PlanImpl {
   int dev = 0, nsm = 0, mode = 0;
@@ -1246,7 +1270,7 @@ struct PlanImpl {
   int64_t max_pairs = 0, max_res = 0;
   int32_t max_len = 0;
   ga_tuning tune{};
-  int occ16[kKaNumBins] = {}, occ32[kKaNumBins] = {};
+  int occ16[kKaNumBins] = {}, occ32[kKaNumBins] = {}, occ16alt[kKaNumBins] = {};
   int occ_kb = 0, long_grid = 0;
   bool long_packed = false;
   size_t long_smem = 0;
@@ -1325,6 +1349,7 @@ int plan_create(const ga_scoring *scoring, int32_t mode, int64_t max_pairs, int6
   for (int b = 0; b < kKaNumBins; ++b) {
     P->occ16[b] = std::max(plan_occupancy(0, mode, b), 1);
     P->occ32[b] = std::max(plan_occupancy(1, mode, b), 1);
+    if (kKaAltTiles >> b & 1u) P->occ16alt[b] = std::max(plan_occupancy_alt(mode, b), 1);
   }
   P->long_smem = dna ? 0 : (size_t)kKbWarps * (size_t)(P->sc.A + 1) * (32 * kKbK);
   P->long_packed = long_packed(P->sc, dna);
@@ -1454,11 +1479,14 @@ int plan_enqueue(PlanImpl &P, const uint8_t *q_codes, const int64_t *q_off, cons
         const int tile = cls == 0 ? tile16[i] : tile32[i];
         ka.range = &P.small->ranges[2 * (cls * kBins + i)];
         ka.task_counter = &P.small->counters[counter++];
-        const int occ = cls == 0 ? P.occ16[tile] : P.occ32[tile];
-        const int ppt = (cls == 0 ? 2 : 1) * (32 / kKaG);
+        const bool alt = cls == 0 && (P.tune.lanes_alt >> tile & 1u);
+        const int occ = alt ? P.occ16alt[tile] : cls == 0 ? P.occ16[tile] : P.occ32[tile];
+        const int ppt = (cls == 0 ? 2 : 1) * (32 / (alt ? ka_alt_g(tile) : kKaG));
         const int64_t want = (npairs + ppt * (kKaThreads / 32) - 1) / (ppt * (kKaThreads / 32));
         const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)P.nsm * occ));
-        if (plan_launch_ka(cls, P.mode, tile, ka, grid, stream_for(nlaunch++)) != cudaSuccess) return GA_ERR_CUDA;
+        const cudaError_t e = alt ? plan_launch_ka_alt(P.mode, tile, ka, grid, stream_for(nlaunch++))
+                                  : plan_launch_ka(cls, P.mode, tile, ka, grid, stream_for(nlaunch++));
+        if (e != cudaSuccess) return GA_ERR_CUDA;
       }
     }
   }
@@ -1674,6 +1702,30 @@ int plan_autotune(PlanImpl &P, const uint8_t *qc, const int64_t *qo, const uint8
       } else {
         break;
       }
+    }
+  }
+  // 4. alternative lane-group sizes of the live packed tiles: all narrow
+  //    tiles with 8 lanes, all wide tiles with 32 lanes, then tile by tile
+  //    (one tile alone often moves the whole batch by less than the 1 %
+  //    a change must gain)
+  {
+    uint32_t lm = 0;
+    if ((rc = live_mask(0, &lm))) return rc;
+    const uint32_t alt = lm & kKaAltTiles;
+    uint32_t narrow = 0, wide = 0;
+    for (int b = 0; b < kKaNumBins; ++b)
+      if (alt >> b & 1u) (ka_alt_g(b) == 8 ? narrow : wide) |= 1u << b;
+    for (uint32_t group : {narrow, wide}) {
+      if (!group) continue;
+      ga_tuning cand = best;
+      cand.lanes_alt ^= group;
+      if ((rc = consider(cand))) return rc;
+    }
+    for (int b = 0; b < kKaNumBins; ++b) {
+      if (!(alt >> b & 1u)) continue;
+      ga_tuning cand = best;
+      cand.lanes_alt ^= 1u << b;
+      if ((rc = consider(cand))) return rc;
     }
   }
   P.tune = best;
@@ -2094,7 +2146,8 @@ int ga_plan_get_tuning(const ga_plan *plan, ga_tuning *out) {
 int ga_plan_set_tuning(ga_plan *plan, const ga_tuning *tuning) {
   if (!plan || !tuning) return GA_ERR_ARG;
   const uint32_t all = (1u << GA_TILE_COUNT) - 1;
-  if ((tuning->tiles16 & ~all) || (tuning->tiles32 & ~all) || tuning->concurrent < 0 || tuning->concurrent > 1)
+  if ((tuning->tiles16 & ~all) || (tuning->tiles32 & ~all) || tuning->concurrent < 0 || tuning->concurrent > 1 ||
+      (tuning->lanes_alt & ~kKaAltTiles))
     return GA_ERR_ARG;
   plan->impl->drop_graph();
   plan->impl->tune = *tuning;

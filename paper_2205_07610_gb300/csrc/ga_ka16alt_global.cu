@@ -1,0 +1,6 @@
+// Packed inter-sequence tiles with the alternative lane-group size, global mode.
+#include "ga_launch.h"
+
+namespace ga {
+GA_KA_ALT_DEFINE(ka16alt_global, kModeGlobal)
+}  // namespace ga

@@ -38,6 +38,28 @@ GA_KA_DECLARE(ka32_local)
 GA_KA_DECLARE(ka32_global)
 GA_KA_DECLARE(ka32_semi)
 
+// Alternative lane-group size of the packed int16x2 tiles, same tile width
+// (16 x kKaK[b] columns): tiles 0..6 (K = 6..12) also run with 8 lanes x 2K
+// columns per pair (half the wavefront fill, twice the registers per lane),
+// tiles 10, 12, 14, 15, 16 (K = 16, 18, 20, 24, 32) with 32 lanes x K/2
+// columns (fewer registers, twice the fill).  A plan's tuning picks per tile.
+constexpr int ka_alt_g(int bin) {
+  return bin <= 6 ? 8 : (bin >= 10 && kKaK[bin] % 2 == 0) ? 32 : 0;
+}
+constexpr int ka_alt_k(int bin) {
+  return ka_alt_g(bin) == 8 ? 2 * kKaK[bin] : ka_alt_g(bin) == 32 ? kKaK[bin] / 2 : 0;
+}
+constexpr uint32_t ka_alt_mask() {
+  uint32_t m = 0;
+  for (int b = 0; b < kKaNumBins; ++b)
+    if (ka_alt_g(b)) m |= 1u << b;
+  return m;
+}
+constexpr uint32_t kKaAltTiles = ka_alt_mask();
+GA_KA_DECLARE(ka16alt_local)
+GA_KA_DECLARE(ka16alt_global)
+GA_KA_DECLARE(ka16alt_semi)
+
 #define GA_KB_DECLARE(NAME)                                                                 \
   cudaError_t launch_##NAME(const KBParams &p, int grid, size_t smem, cudaStream_t s);     \
   int blocks_per_sm_##NAME(size_t smem);
@@ -98,6 +120,45 @@ int blocks_per_sm_ka_tile(int bin) {
     return launch_ka_tile<CELL, MODE>(bin, p, grid, s);                                 \
   }                                                                                     \
   int blocks_per_sm_##NAME(int bin) { return blocks_per_sm_ka_tile<CELL, MODE>(bin); }
+
+template <int MODE, int I = 0>
+cudaError_t launch_ka_alt_tile(int bin, const KAParams &p, int grid, cudaStream_t s) {
+  if constexpr (I == kKaNumBins) {
+    return cudaErrorInvalidValue;
+  } else {
+    if (bin == I) {
+      if constexpr (ka_alt_g(I) != 0) {
+        ka_kernel<CellS16x2, MODE, ka_alt_g(I), ka_alt_k(I)><<<grid, kKaThreads, 0, s>>>(p);
+        return cudaGetLastError();
+      } else {
+        return cudaErrorInvalidValue;
+      }
+    }
+    return launch_ka_alt_tile<MODE, I + 1>(bin, p, grid, s);
+  }
+}
+
+template <int MODE, int I = 0>
+int blocks_per_sm_ka_alt_tile(int bin) {
+  if constexpr (I == kKaNumBins) {
+    return 0;
+  } else {
+    if (bin == I) {
+      int n = 0;
+      if constexpr (ka_alt_g(I) != 0)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, ka_kernel<CellS16x2, MODE, ka_alt_g(I), ka_alt_k(I)>,
+                                                      kKaThreads, 0);
+      return n;
+    }
+    return blocks_per_sm_ka_alt_tile<MODE, I + 1>(bin);
+  }
+}
+
+#define GA_KA_ALT_DEFINE(NAME, MODE)                                                    \
+  cudaError_t launch_##NAME(int bin, const KAParams &p, int grid, cudaStream_t s) {     \
+    return launch_ka_alt_tile<MODE>(bin, p, grid, s);                                   \
+  }                                                                                     \
+  int blocks_per_sm_##NAME(int bin) { return blocks_per_sm_ka_alt_tile<MODE>(bin); }
 
 #define GA_KB_DEFINE(NAME, MODE, PROFILE)                                                    \
   cudaError_t launch_##NAME(const KBParams &p, int grid, size_t smem, cudaStream_t s) {     \

@@ -91,6 +91,30 @@ def test_plan_tunings_are_exact(tiles16, tiles32, conc):
             assert plan.stats()["status"] == 0
 
 
+@pytest.mark.parametrize("lanes_alt", [ga.TILE_ALT_MASK, 0x0007F, 0x1D400, 0x00055])
+def test_plan_alternative_lane_groups_are_exact(lanes_alt):
+    # packed tiles with 8 lanes x 2K columns (narrow tiles) or 32 lanes x
+    # K/2 columns (wide tiles) instead of 16 lanes x K: pairs of every width
+    # up to 600 columns, every mode, bins in order and concurrent
+    qc, qo, tc, to = _mixed(103, n=700, lmax=600)
+    mat = synth.dna_matrix(2, -3)
+    d = _dev(qc, qo, tc, to)
+    for mode in MODES:
+        want, _ = _oracle(qc, qo, tc, to, mat, 5, 2, mode)
+        with ga.Plan(mat, 5, 2, mode, 700, max(qo[-1], to[-1]), 700) as plan:
+            for conc in (0, 1):
+                plan.tuning = ga.Tuning((1 << 17) - 1, (1 << 17) - 1, conc, lanes_alt)
+                got = plan.run(*d)
+                assert_same(got.cpu().numpy(), want, f"lanes_alt {lanes_alt:#x} {conc} {mode}")
+                assert plan.stats()["status"] == 0
+
+
+def test_plan_rejects_lane_groups_without_an_alternative():
+    with ga.Plan(synth.dna_matrix(2, -3), 5, 2, "global", 10, 1000, 100) as plan:
+        with pytest.raises(ga.GotohError):
+            plan.tuning = ga.Tuning((1 << 17) - 1, 0, 1, 1 << 8)  # tile 8 (K = 14) has none
+
+
 def test_plan_graph_replay_reads_new_inputs():
     # capture once, then overwrite the captured input buffers with another
     # batch of the same pair count and replay: the replay scores that batch
