@@ -1,10 +1,12 @@
 """GPU parity at the full benchmark sizes, in the launch configuration the
 bench times: the whole workload runs on the GPU in one call (the serving
-stream in one submission).  The 1M-pair batch is compared with the CPU
-oracle pair by pair in full; for the larger workloads a seeded sample of the
-outputs (the longest pairs, targets and requests included) is, with every
-query of the protein search against 4,096 targets.  Properties that hold at
-any size (banded scores equal full-DP scores) are checked on every pair.
+stream in one submission).  Every output is compared with the CPU oracle:
+the 1M-pair batch against the oracle run here; the 20k long pairs (full DP,
+band doubling and the learned band) and the 200k serving requests against
+the oracle's scores stored in tests/golden/ by make_fullsize_goldens.py
+(which calls only oracle/ and synth/; each file carries a digest of the
+generated inputs, checked first).  The protein search, 1e8 pairs, is compared
+on every query against 4,096 sampled targets (the 64 longest included).
 """
 import os
 
@@ -13,6 +15,7 @@ import pytest
 
 import oracle
 import synth
+from tests.golden import make_fullsize_goldens as goldens
 
 pytestmark = pytest.mark.gpu
 
@@ -79,31 +82,42 @@ def test_config3_full_database_sampled():
     np.testing.assert_array_equal(got.cpu().numpy()[:, tsel].astype(np.int64), want)
 
 
-def test_config4_full_dp_and_band_sampled():
-    # 20k long DNA pairs, global: full DP on every pair, band doubling from
-    # the default start; every banded score equals the full-DP score, and a
-    # sample of 150 pairs plus the 4 largest equals the oracle
+def _golden(path, digest):
+    g = np.load(path)
+    assert str(g["digest"]) == digest, f"{os.path.basename(path)}: the generated inputs changed; " \
+        "rerun tests/golden/make_fullsize_goldens.py"
+    return g["scores"].astype(np.int64)
+
+
+def test_config4_full_dp_band_and_learned_band_full():
+    # 20k long DNA pairs, global: full DP, band doubling from the default
+    # start and from the learned start (a predictor trained here on 1,000
+    # other pairs): every score of all three against the oracle
+    from paper_2205_07610_gb300 import band
     b = synth.long_dna_pairs(npairs=20_000)
+    want = _golden(goldens.LONG_PATH, goldens.long_digest(b))
     d = _dev(b.q_codes, b.q_off, b.t_codes, b.t_off)
     full, st = ga.align_batch(*d, b.matrix, b.alpha, b.beta, "global", stats=True)
     assert st["status"] == 0
-    band, w_used = ga.align_banded(*d, b.matrix, b.alpha, b.beta, default_w0=16)
-    assert torch.equal(band, full)
+    np.testing.assert_array_equal(full.cpu().numpy().astype(np.int64), want)
+    banded, w_used = ga.align_banded(*d, b.matrix, b.alpha, b.beta, default_w0=16)
+    np.testing.assert_array_equal(banded.cpu().numpy().astype(np.int64), want)
     assert int(w_used.min()) >= 0
-    m, n = b.lengths()
-    idx = _sample(np.random.default_rng(4), m * n, 150, 4)
-    sub = b.subset(idx)
-    want, errs = oracle.batch(sub.q_codes, sub.q_off, sub.t_codes, sub.t_off, b.matrix, b.alpha, b.beta,
-                              "global", nthreads=NTHREADS)
-    assert not errs.any()
-    np.testing.assert_array_equal(full.cpu().numpy()[idx].astype(np.int64), want)
+    tr = synth.long_dna_pairs(npairs=1000, seed=synth.SEED_BASE + 400)
+    pred, _ = band.train(*_dev(tr.q_codes, tr.q_off, tr.t_codes, tr.t_off), b.matrix, b.alpha, b.beta,
+                         synth.mlp_init(synth.SEED_BASE + 401),
+                         synth.minibatches(tr.npairs, 128, 300, synth.SEED_BASE + 402), lr=2e-3)
+    learned, _, st = pred.align(*d, b.matrix, b.alpha, b.beta, stats=True)
+    assert st["status"] == 0
+    np.testing.assert_array_equal(learned.cpu().numpy().astype(np.int64), want)
 
 
-def test_config5_full_serving_stream_sampled():
+def test_config5_full_serving_stream():
     # the whole 200k-request serving stream submitted to the server at once
-    # (mixed DNA / protein, local / global, lengths up to 50k); a sample of
-    # 2,000 results plus the 3 largest requests equals the oracle
+    # (mixed DNA / protein, local / global, lengths up to 50k): every result
+    # against the oracle
     s = synth.serving_stream()
+    want = _golden(goldens.SERVING_PATH, goldens.serving_digest(s))
     cells = np.diff(s.q_off) * np.diff(s.t_off)
     with ga.Server(arena_bytes=32 << 30, max_inflight=65536, max_tasks=1 << 22) as srv:
         d = srv.add_scoring(*s.dna_scoring)
@@ -117,16 +131,4 @@ def test_config5_full_serving_stream_sampled():
     assert np.array_equal(res["id"], first + np.arange(s.nreq))
     assert np.all(res["status"] == 0)
     assert np.array_equal(res["cells"], cells)
-    idx = _sample(np.random.default_rng(5), cells, 2000, 3)
-    for prot in (False, True):  # the oracle on the sample, by scoring and mode
-        for md in (0, 1):
-            sel = idx[(s.protein[idx] == prot) & (s.mode[idx] == md)]
-            if not len(sel):
-                continue
-            mat, al, be = s.protein_scoring if prot else s.dna_scoring
-            qc, qo = synth.pack_csr([s.q_codes[s.q_off[i]:s.q_off[i + 1]] for i in sel])
-            tc, to = synth.pack_csr([s.t_codes[s.t_off[i]:s.t_off[i + 1]] for i in sel])
-            want, errs = oracle.batch(qc, qo, tc, to, mat, al, be, "global" if md else "local",
-                                      nthreads=NTHREADS)
-            assert not errs.any()
-            np.testing.assert_array_equal(res["score"][sel].astype(np.int64), want)
+    np.testing.assert_array_equal(res["score"].astype(np.int64), want)
