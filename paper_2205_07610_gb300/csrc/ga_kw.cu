@@ -4,19 +4,19 @@
 
 namespace ga {
 
-#define GA_KW_DEFINE(NAME, MODE)                                                      \
+#define GA_KW_DEFINE(NAME, MODE, K)                                                   \
   cudaError_t launch_##NAME(const KBParams &p, int grid, cudaStream_t s) {            \
-    kw_kernel<MODE, kKwK><<<grid, kKbThreads, 0, s>>>(p);                              \
+    kw_kernel<MODE, K><<<grid, kKbThreads, 0, s>>>(p);                                 \
     return cudaGetLastError();                                                         \
   }                                                                                    \
   int blocks_per_sm_##NAME() {                                                         \
     int n = 0;                                                                         \
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kw_kernel<MODE, kKwK>, kKbThreads, 0); \
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kw_kernel<MODE, K>, kKbThreads, 0); \
     return n;                                                                          \
   }
 
-GA_KW_DEFINE(kw_local, kModeLocal)
-GA_KW_DEFINE(kw_global, kModeGlobal)
-GA_KW_DEFINE(kw_semi, kModeSemi)
+GA_KW_DEFINE(kw_local, kModeLocal, kKwKLocal)
+GA_KW_DEFINE(kw_global, kModeGlobal, kKwKGlobal)
+GA_KW_DEFINE(kw_semi, kModeSemi, kKwKSemi)
 
 }  // namespace ga

@@ -71,8 +71,12 @@ GA_KB_DECLARE(kb_global_prof)
 GA_KB_DECLARE(kb_semi_prof)
 
 // Packed long kernel (alphabets of <= 4 symbols, sigma_max + alpha <=
-// kKwMaxStep): 32 lanes x 16 columns per half, two halves per super-stage.
-constexpr int kKwK = 16;
+// kKwMaxStep): 32 lanes x K columns per half, two halves per super-stage.
+// K per mode as measured on GB300 on the 20k long DNA pairs (K = 8, 12, 16,
+// 20, 24): 24 for local and global, 20 for semi-global.
+constexpr int kKwKLocal = 24;
+constexpr int kKwKGlobal = 24;
+constexpr int kKwKSemi = 20;
 cudaError_t launch_kw_local(const KBParams &p, int grid, cudaStream_t s);
 cudaError_t launch_kw_global(const KBParams &p, int grid, cudaStream_t s);
 cudaError_t launch_kw_semi(const KBParams &p, int grid, cudaStream_t s);

@@ -56,8 +56,9 @@
 namespace ga {
 
 constexpr int kKwRenorm = 128;  // iterations between base renormalisations
-// Largest sigma_max + alpha of the packed long kernel: 128 * (128 + 2 * 16 +
-// 8) = 21504 keeps every relative value inside int16 with room for -inf.
+// Largest sigma_max + alpha of the packed long kernel: 128 * (128 + 2K + 8)
+// = 23552 for K <= 24 keeps every relative value inside int16 with room for
+// -inf.
 constexpr int kKwMaxStep = 128;
 
 __device__ __forceinline__ uint32_t pk16(int lo, int hi) {
@@ -90,6 +91,7 @@ __device__ __forceinline__ uint32_t pk_row(uint32_t (&H)[K], uint32_t (&E)[K], u
 
 template <int MODE, int K>
 __global__ void __launch_bounds__(128) kw_kernel(const __grid_constant__ KBParams p) {
+  static_assert(kKwMaxStep * (kKwRenorm + 2 * K + 8) < 32000 - 256, "relative int16 cells of this tile width");
   constexpr int kWarps = 4;
   constexpr int WH = 32 * K;  // columns per half
   constexpr int W2 = 2 * WH;  // columns per super-stage
