@@ -440,15 +440,18 @@ __device__ int sv_strip_pk(const SvParams &p, SvRequest *rq, int slot, const SvV
     const int r = 32 * bb + 1 + t;
     if (r <= R) in_ring[(r - 1) & 63] = __ldcg(edge_in + r);
   };
-  auto fill_rows = [&](int bb) {  // row codes; pad code A past the last row
+  // row codes (pad code A past the last row) of batch bb, rows 32bb+1 ..
+  // 32bb+32: read_rows issues the global load a batch before put_rows
+  // stores it, so the load's latency overlaps a batch of rows
+  auto read_rows = [&](int bb) -> uint32_t {
     const int r = 32 * bb + 1 + t;
-    uint32_t c = (uint32_t)A;
-    if (r <= R) {
-      c = __ldcg(v.rowraw + r - 1);
-      if (c >= (uint32_t)A) {
-        atomicCAS(&rq->status, 0, GA_ERR_RESIDUE);
-        c = 0;
-      }
+    return (r <= R) ? (uint32_t)__ldcg(v.rowraw + r - 1) : (uint32_t)A;
+  };
+  auto put_rows = [&](int bb, uint32_t c) {
+    const int r = 32 * bb + 1 + t;
+    if (c >= (uint32_t)A && r <= R) {
+      atomicCAS(&rq->status, 0, GA_ERR_RESIDUE);
+      c = 0;
     }
     row_ring[r & (kRing - 1)] = c;
   };
@@ -471,8 +474,9 @@ __device__ int sv_strip_pk(const SvParams &p, SvRequest *rq, int slot, const SvV
 
   row_ring[(-t) & (kRing - 1)] = (uint32_t)(A + 1);  // rows 0 .. -31: virtual
   load_batch(0);
-  fill_rows(0);
-  fill_rows(1);
+  put_rows(0, read_rows(0));
+  put_rows(1, read_rows(1));
+  uint32_t next_rows = read_rows(2);  // stored at iteration 0
   __syncwarp();
 
   const int hd0 = h0(col0 + t * K) - b[0], hd1 = h0(col0 + WH + t * K) - b[1];
@@ -490,7 +494,8 @@ __device__ int sv_strip_pk(const SvParams &p, SvRequest *rq, int slot, const SvV
     if ((it & 31) == 0) {
       __syncwarp();
       load_batch(it / 32 + 1);
-      fill_rows(it / 32 + 2);
+      put_rows(it / 32 + 2, next_rows);
+      next_rows = read_rows(it / 32 + 3);
       if (it >= 96 && edge_out) {  // lane 31's high-half rows it-95 .. it-64
         const int r = it - 95 + t;
         edge_out[r] = out_ring[(r - 1) & 63];
@@ -523,6 +528,14 @@ __device__ int sv_strip_pk(const SvParams &p, SvRequest *rq, int slot, const SvV
         D = (t == 0) ? pk16(0, nb0 - b[1]) : pk16(nb0 - b[0], nb1 - b[1]);
       }
       __syncwarp();
+    }
+    // lane 0's next left input (the strip's left edge at row it + 2),
+    // read before the row update so that it is ready when the shuffles are
+    int lx = kNeg16, ly = kNeg16;
+    if (t == 0 && it + 2 <= R) {
+      const int2 lv = left_row(it + 2);
+      lx = lv.x - b[0];
+      ly = lv.y - b[0];
     }
     const int rlo = it - t + 1, rhi = rlo - 32;
     uint32_t Hout, Fout;
@@ -568,12 +581,6 @@ __device__ int sv_strip_pk(const SvParams &p, SvRequest *rq, int slot, const SvV
     uint32_t hs = __shfl_sync(0xffffffffu, Hout, (t + 31) & 31);
     uint32_t fs = __shfl_sync(0xffffffffu, Fout, (t + 31) & 31);
     if (t == 0) {
-      int lx = kNeg16, ly = kNeg16;
-      if (it + 2 <= R) {
-        const int2 lv = left_row(it + 2);
-        lx = lv.x - b[0];
-        ly = lv.y - b[0];
-      }
       hs = prmt((uint32_t)lx, hs, 0x5410u);
       fs = prmt((uint32_t)ly, fs, 0x5410u);
     }
