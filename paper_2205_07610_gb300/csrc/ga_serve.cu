@@ -226,14 +226,86 @@ class ArenaAlloc {
   std::map<int64_t, int64_t> free_;
 };
 
+// Codes of admitted requests are bump-allocated from slabs of the arena, so
+// the codes admitted in one scheduler tick sit back to back in the arena as
+// they do in the pinned staging buffer and reach the device in one copy
+// (a copy per request cost more host time than everything else the
+// admission does).  A slab goes back to the arena when the last request
+// placed in it completes and it is no longer the one being filled; the slab
+// being filled restarts from its beginning once all of its requests are
+// done.  A slab that cannot be had at full size is cut to the request, and
+// an idle slab is given back when a request's edges find no room, so that
+// any request that fits an empty arena is still admitted.
+class CodeSlabs {
+ public:
+  explicit CodeSlabs(int64_t arena_bytes)
+      : slab_(std::min<int64_t>(16ll << 20, std::max<int64_t>(64ll << 10, arena_bytes / 64)) & ~255ll) {}
+  // Arena offset of `bytes` (a multiple of 256) and the slab's id, or -1.
+  int64_t alloc(ArenaAlloc &arena, int64_t bytes, int *id) {
+    if (cur_ >= 0 && slabs_[cur_].refs == 0) slabs_[cur_].used = 0;
+    if (cur_ < 0 || slabs_[cur_].used + bytes > slabs_[cur_].size) {
+      if (cur_ >= 0 && slabs_[cur_].refs == 0) drop(arena, cur_);
+      int64_t size = std::max(slab_, bytes);
+      int64_t off = arena.alloc(size);
+      if (off < 0 && size > bytes) off = arena.alloc(size = bytes);
+      if (off < 0) return -1;
+      cur_ = fresh(off, size);  // a previous slab still in use is dropped by its last release
+    }
+    Slab &sl = slabs_[cur_];
+    const int64_t off = sl.off + sl.used;
+    sl.used += bytes;
+    sl.refs += 1;
+    *id = cur_;
+    return off;
+  }
+  void release(ArenaAlloc &arena, int id) {
+    if (--slabs_[id].refs == 0 && id != cur_) drop(arena, id);
+  }
+  // Returns the slab being filled to the arena if no request uses it (an
+  // idle slab must not split the space a large request needs).
+  bool trim(ArenaAlloc &arena) {
+    if (cur_ < 0 || slabs_[cur_].refs != 0) return false;
+    drop(arena, cur_);
+    return true;
+  }
+
+ private:
+  struct Slab {
+    int64_t off = -1, size = 0, used = 0, refs = 0;
+  };
+  void drop(ArenaAlloc &arena, int id) {
+    arena.release(slabs_[id].off, slabs_[id].size);
+    slabs_[id] = Slab{};
+    free_ids_.push_back(id);
+    if (id == cur_) cur_ = -1;
+  }
+  int fresh(int64_t off, int64_t size) {
+    int id;
+    if (!free_ids_.empty()) {
+      id = free_ids_.back();
+      free_ids_.pop_back();
+    } else {
+      id = (int)slabs_.size();
+      slabs_.emplace_back();
+    }
+    slabs_[id].off = off;
+    slabs_[id].size = size;
+    return id;
+  }
+  int64_t slab_;
+  int cur_ = -1;
+  std::vector<Slab> slabs_;
+  std::vector<int> free_ids_;
+};
+
 // Arena bytes of one admitted request: its codes and its strip edges.
-int64_t seq_bytes_for(int64_t m, int64_t n) { return ((m + 15) & ~15ll) + ((n + 15) & ~15ll); }
+int64_t seq_bytes_for(int64_t m, int64_t n) { return ((((m + 15) & ~15ll) + ((n + 15) & ~15ll)) + 255) & ~255ll; }
 int64_t edge_bytes_for(int64_t m, int64_t n) {
   const int64_t R = m < n ? m : n;
   return (int64_t)sizeof(int2) * (sv_strips_for(m, n) - 1) * (R + 1);
 }
 int64_t request_bytes(int64_t m, int64_t n) {
-  return ((seq_bytes_for(m, n) + 255) & ~255ll) + ((edge_bytes_for(m, n) + 255) & ~255ll);
+  return seq_bytes_for(m, n) + ((edge_bytes_for(m, n) + 255) & ~255ll);
 }
 
 struct SubmitBatch {
@@ -252,7 +324,8 @@ struct Pending {
 struct Inflight {
   bool used = false;
   int64_t id = 0, release_ns = 0, admit_ns = 0, cells = 0;
-  int64_t seq_off = -1, seq_bytes = 0;  // codes (own allocation)
+  int64_t seq_off = -1, seq_bytes = 0;  // codes (in code slab seq_slab)
+  int32_t seq_slab = -1;
   int64_t edge_off = -1, edge_bytes = 0;
   int32_t nstrips = 0;
 };
@@ -299,6 +372,7 @@ struct ga_server {
   std::vector<ga_result> done;
   std::vector<ga::Inflight> slots;
   std::unique_ptr<ga::ArenaAlloc> alloc;
+  std::unique_ptr<ga::CodeSlabs> slabs;
   int64_t next_id = 0;
   int64_t req_seq = 0;        // requests admitted so far (slot = seq % req_cap)
   unsigned long long tail = 0;
@@ -345,15 +419,17 @@ bool sched_tick(ga_server *S) {
       const int64_t seq_bytes = seq_bytes_for(m, n);
       if (stage_bytes + seq_bytes > S->stage_seq_cap) break;
       const int64_t edge_bytes = edge_bytes_for(m, n);
-      const int64_t so = S->alloc->alloc(seq_bytes);
-      if (so < 0) break;
       int64_t eo = -1;
       if (edge_bytes > 0) {
         eo = S->alloc->alloc(edge_bytes);
-        if (eo < 0) {
-          S->alloc->release(so, seq_bytes);
-          break;
-        }
+        if (eo < 0 && S->slabs->trim(*S->alloc)) eo = S->alloc->alloc(edge_bytes);
+        if (eo < 0) break;
+      }
+      int seq_slab = -1;
+      const int64_t so = S->slabs->alloc(*S->alloc, seq_bytes, &seq_slab);
+      if (so < 0) {
+        if (eo >= 0) S->alloc->release(eo, edge_bytes);
+        break;
       }
       Inflight &f = S->slots[slot];
       f.used = true;
@@ -362,6 +438,7 @@ bool sched_tick(ga_server *S) {
       f.cells = m * n;
       f.seq_off = so;
       f.seq_bytes = seq_bytes;
+      f.seq_slab = seq_slab;
       f.edge_off = eo;
       f.edge_bytes = edge_bytes;
       f.nstrips = nstrips;
@@ -513,7 +590,7 @@ bool sched_tick(ga_server *S) {
         res.release_ns = f.release_ns;
         res.admit_ns = f.admit_ns;
         res.cells = f.cells;
-        S->alloc->release(f.seq_off, f.seq_bytes);
+        S->slabs->release(*S->alloc, f.seq_slab);
         if (f.edge_off >= 0) S->alloc->release(f.edge_off, f.edge_bytes);
         S->tasks_inflight -= 1;
         f.used = false;
@@ -636,6 +713,7 @@ int ga_server_create(const ga_server_config *cfg, ga_server **out) {
   }
   S->slots.resize((size_t)S->req_cap);
   S->alloc.reset(new ArenaAlloc(S->arena_bytes));
+  S->slabs.reset(new CodeSlabs(S->arena_bytes));
   S->smem = (size_t)kSvWarps * (size_t)(S->max_A + 2) * kSvW;
   int occ = 0, nsm = 0;
   if (sv_prepare_launch(S->smem, &occ) != cudaSuccess ||
