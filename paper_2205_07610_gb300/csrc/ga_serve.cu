@@ -112,7 +112,7 @@ int sv_align_pair(const uint8_t *q, int64_t m, const uint8_t *t, int64_t n, int 
   unsigned long long *cseq = (unsigned long long *)(base + o_cseq);
   int2 *cont = (int2 *)(base + o_cont);
 
-  const size_t smem = (size_t)kSvWarps * (size_t)(sc.A + 2) * kSvW;
+  const size_t smem = (size_t)kSvWarps * (size_t)(sc.A + 1) * kSvW;
   int occ = 0, dev = 0, nsm = 0;
   if (sv_prepare_launch(smem, &occ) != cudaSuccess || cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
@@ -147,7 +147,7 @@ int sv_align_pair(const uint8_t *q, int64_t m, const uint8_t *t, int64_t n, int 
   p.completed = ht + 4;
   p.idle_ns = 0;
   p.wait_ns = 10ll * 1000 * 1000 * 1000;
-  p.prof_bytes = (sc.A + 2) * kSvW;
+  p.prof_bytes = (sc.A + 1) * kSvW;
   const int grid = std::max(1, std::min((nstrips + kSvWarps - 1) / kSvWarps, nsm * std::max(occ, 1)));
   ks_kernel<<<grid, 32 * kSvWarps, smem, s>>>(p);
   int rc = cudaGetLastError() == cudaSuccess ? GA_OK : GA_ERR_CUDA;
@@ -554,7 +554,7 @@ bool sched_tick(ga_server *S) {
     p.stop = stop_d;
     p.idle_ns = S->idle_ns;
     p.wait_ns = 10ll * 1000 * 1000 * 1000;
-    p.prof_bytes = (S->max_A + 2) * kSvW;
+    p.prof_bytes = (S->max_A + 1) * kSvW;
     p.cont = S->cont;
     p.cont_seq = S->cont_seq;
     p.cont_cap = S->req_cap;
@@ -714,7 +714,7 @@ int ga_server_create(const ga_server_config *cfg, ga_server **out) {
   S->slots.resize((size_t)S->req_cap);
   S->alloc.reset(new ArenaAlloc(S->arena_bytes));
   S->slabs.reset(new CodeSlabs(S->arena_bytes));
-  S->smem = (size_t)kSvWarps * (size_t)(S->max_A + 2) * kSvW;
+  S->smem = (size_t)kSvWarps * (size_t)(S->max_A + 1) * kSvW;
   int occ = 0, nsm = 0;
   if (sv_prepare_launch(S->smem, &occ) != cudaSuccess ||
       cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, S->device) != cudaSuccess) {
@@ -749,7 +749,7 @@ int ga_server_add_scoring(ga_server *S, const ga_scoring *sc, int32_t *scoring_i
   S->sc_host.push_back(h);
   if (h.A > S->max_A) {
     S->max_A = h.A;
-    S->smem = (size_t)kSvWarps * (size_t)(S->max_A + 2) * kSvW;
+    S->smem = (size_t)kSvWarps * (size_t)(S->max_A + 1) * kSvW;
     int occ = 0, nsm = 0;
     if (sv_prepare_launch(S->smem, &occ) != cudaSuccess ||
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, S->device) != cudaSuccess)

@@ -113,7 +113,7 @@ struct SvParams {
   unsigned long long *completed;
   int64_t idle_ns;
   int64_t wait_ns;
-  int32_t prof_bytes;  // per warp: (max A + 2) * kSvW (real residues, pad row, virtual row)
+  int32_t prof_bytes;  // per warp: (max A + 1) * kSvW (real residues, one pad / virtual row)
 };
 
 __device__ __forceinline__ uint64_t sv_now() {
@@ -285,15 +285,17 @@ __device__ int sv_strip(const SvParams &p, SvRequest *rq, int slot, const SvView
   T Fin = (t == 0) ? l1.y : kNeg;
 
   const int nit = R + 31;
+  int flushed = 0;  // edge rows 1..flushed are in global memory
   for (int it = 0; it < nit; ++it) {
     if ((it & 31) == 0) {
       __syncwarp();
       load_batch(it / 32 + 1);
       fill_rows(it / 32 + 2);
-      if (it >= 64 && edge_out) {  // flush lane-31 rows it-63 .. it-32
-        const int r = it - 63 + t;
-        edge_out[r] = out_ring[(r - 1) & 63];
-        publish(it - 32);
+      if (it >= 32 && edge_out) {  // lane 31's rows stored since the last flush: .. it-31
+        const int r = flushed + 1 + t;
+        if (r <= it - 31) edge_out[r] = out_ring[(r - 1) & 31];
+        flushed = it - 31;
+        publish(flushed);
       }
       __syncwarp();
     }
@@ -330,7 +332,7 @@ __device__ int sv_strip(const SvParams &p, SvRequest *rq, int slot, const SvView
       Hout = H[K - 1];
       Fout = kNeg;
     }
-    if (t == 31 && r >= 1 && r <= R) out_ring[(r - 1) & 63] = make_int2(Hout, Fout);
+    if (t == 31 && r >= 1 && r <= R) out_ring[(r - 1) & 31] = make_int2(Hout, Fout);
     Hdiag = Hleft;
     Hleft = __shfl_up_sync(0xffffffffu, Hout, 1);
     Fin = __shfl_up_sync(0xffffffffu, Fout, 1);
@@ -342,8 +344,8 @@ __device__ int sv_strip(const SvParams &p, SvRequest *rq, int slot, const SvView
   }
   __syncwarp();
   if (edge_out) {  // remaining lane-31 rows, then the whole edge is published
-    const int first = (nit >= 64) ? ((nit - 1) / 32) * 32 - 63 + 32 : 1;
-    for (int r = first + t; r <= R; r += 32) edge_out[r] = out_ring[(r - 1) & 63];
+    const int r = flushed + 1 + t;
+    if (r <= R) edge_out[r] = out_ring[(r - 1) & 31];
     publish(R);
   }
   __syncwarp();
@@ -357,10 +359,10 @@ __device__ int sv_strip(const SvParams &p, SvRequest *rq, int slot, const SvView
 template <int MODE>
 __device__ int sv_strip_pk(const SvParams &p, SvRequest *rq, int slot, const SvView &v, int s, int t,
                            uint8_t *prof, uint8_t *colc, int2 *in_ring, int2 *out_ring,
-                           uint32_t *row_ring /* [256] */) {
+                           uint32_t *row_ring /* [128 + 32] */) {
   constexpr int K = kSvKp, WH = 32 * kSvKp, W = kSvW;
   static_assert(2 * WH == W, "a packed strip is two halves of the strip");
-  constexpr int kRing = 256;
+  constexpr int kRing = 128;
   const int R = v.R, C = v.C, A = v.A, alpha = v.alpha, beta = v.beta;
   const int col0 = s * W;
   const int2 *edge_in = (s > 0) ? v.edges + (size_t)(s - 1) * (size_t)(R + 1) : nullptr;
@@ -370,8 +372,10 @@ __device__ int sv_strip_pk(const SvParams &p, SvRequest *rq, int slot, const SvV
   const uint32_t NEGV = pk16(kNeg16, kNeg16);
   auto h0 = [&](int c) -> int { return (MODE == kModeGlobal && c > 0) ? -alpha - beta * (c - 1) : 0; };
 
-  // ---- column codes and the strip's profile: rows 0..A-1, pad row A
-  // (sigma = 0) and virtual row A+1 (leaves row 0 unchanged) --------------
+  // ---- column codes and the strip's profile: rows 0..A-1 and row A, read
+  // by the rows before row 1 and past row R (sigma = -beta in global mode,
+  // which leaves row 0 unchanged, else 0; what the rows past R compute is
+  // never read in global and semi-global mode) ----------------------------
   for (int x = t; x < W; x += 32) {
     const int col = col0 + x;
     int c = A;  // pad
@@ -385,12 +389,12 @@ __device__ int sv_strip_pk(const SvParams &p, SvRequest *rq, int slot, const SvV
     colc[x] = (uint8_t)c;
   }
   __syncwarp();
-  for (int e = t; e < (A + 2) * W; e += 32) {
+  for (int e = t; e < (A + 1) * W; e += 32) {
     const int c = e / W, x = e - c * W;
     const int cc = colc[x];
     int val = 0;
     if (c < A && cc < A) val = v.sw ? v.sigma[cc * A + c] : v.sigma[c * A + cc];
-    else if (c == A + 1 && MODE == kModeGlobal) val = -beta;
+    else if (c == A && MODE == kModeGlobal) val = -beta;
     prof[e] = (uint8_t)(int8_t)val;
   }
 
@@ -447,13 +451,18 @@ __device__ int sv_strip_pk(const SvParams &p, SvRequest *rq, int slot, const SvV
     const int r = 32 * bb + 1 + t;
     return (r <= R) ? (uint32_t)__ldcg(v.rowraw + r - 1) : (uint32_t)A;
   };
+  // The ring holds each row's profile byte offset (code x W); its first 32
+  // entries are mirrored after the last, so that the 32 rows a lane reads in
+  // a batch are contiguous.
   auto put_rows = [&](int bb, uint32_t c) {
     const int r = 32 * bb + 1 + t;
     if (c >= (uint32_t)A && r <= R) {
       atomicCAS(&rq->status, 0, GA_ERR_RESIDUE);
       c = 0;
     }
-    row_ring[r & (kRing - 1)] = c;
+    const int x = r & (kRing - 1);
+    row_ring[x] = c * (uint32_t)W;
+    if (x < 32) row_ring[x + kRing] = c * (uint32_t)W;
   };
   bool queued = false;
   auto publish = [&](int rows) {
@@ -472,11 +481,11 @@ __device__ int sv_strip_pk(const SvParams &p, SvRequest *rq, int slot, const SvV
     queued = queued || rows >= ::min(R, kSvContRows);
   };
 
-  row_ring[(-t) & (kRing - 1)] = (uint32_t)(A + 1);  // rows 0 .. -31: virtual
+  row_ring[(-t) & (kRing - 1)] = (uint32_t)(A * W);  // rows 0 .. -31: virtual
+  if (t == 0) row_ring[kRing] = (uint32_t)(A * W);
   load_batch(0);
   put_rows(0, read_rows(0));
-  put_rows(1, read_rows(1));
-  uint32_t next_rows = read_rows(2);  // stored at iteration 0
+  uint32_t next_rows = read_rows(1);  // stored at iteration 0
   __syncwarp();
 
   const int hd0 = h0(col0 + t * K) - b[0], hd1 = h0(col0 + WH + t * K) - b[1];
@@ -489,60 +498,39 @@ __device__ int sv_strip_pk(const SvParams &p, SvRequest *rq, int slot, const SvV
     Fin = pk16(l1.y - b[0], kNeg16);
   }
 
-  const int nit = R + 63;
-  for (int it = 0; it < nit; ++it) {
-    if ((it & 31) == 0) {
-      __syncwarp();
-      load_batch(it / 32 + 1);
-      put_rows(it / 32 + 2, next_rows);
-      next_rows = read_rows(it / 32 + 3);
-      if (it >= 96 && edge_out) {  // lane 31's high-half rows it-95 .. it-64
-        const int r = it - 95 + t;
-        edge_out[r] = out_ring[(r - 1) & 63];
-        publish(it - 64);
-      }
-      if ((it & (kKwRenorm - 1)) == 0 && it > 0) {
-        const int d0 = lo16(H[0]), d1 = hi16(H[0]);
-        if constexpr (MODE == kModeLocal) {
-          best_abs = ::max(best_abs, ::max(lo16(best) + b[0], hi16(best) + b[1]));
-          best = NEGV;
-        }
-        b[0] += d0;
-        b[1] += d1;
-        const uint32_t dl = pk16(-d0, -d1);
-#pragma unroll
-        for (int j = 0; j < K; ++j) {
-          H[j] = __vadd2(H[j], dl);
-          E[j] = __vadd2(E[j], dl);
-        }
-        Hdiag = __vadd2(Hdiag, dl);
-        Hleft = __vadd2(Hleft, dl);
-        Fin = __vadd2(Fin, dl);
-        if constexpr (MODE == kModeLocal) {
-          Z = pk16(::max(-b[0], kNeg16), ::max(-b[1], kNeg16));
-#pragma unroll
-          for (int j = 0; j < K; ++j) E[j] = __vmaxs2(E[j], Z);
-        }
-        const int nb0 = __shfl_sync(0xffffffffu, b[0], (t + 31) & 31);
-        const int nb1 = __shfl_sync(0xffffffffu, b[1], (t + 31) & 31);
-        D = (t == 0) ? pk16(0, nb0 - b[1]) : pk16(nb0 - b[0], nb1 - b[1]);
-      }
-      __syncwarp();
+  // Lane 31's high-half output rows (H and F of the strip's last column) are
+  // kept as raw packed words and turned into absolute edge values when they
+  // are flushed, with lane 31's high-half base: every batch flushes all rows
+  // stored before it, ahead of any renormalisation.
+  const bool keep_out = (t == 31) && edge_out != nullptr;
+  auto flush_rows = [&](int first, int last_row) {  // at most 32 rows, lane t: row first + t
+    const int b31 = __shfl_sync(0xffffffffu, b[1], 31);
+    const int r = first + t;
+    if (r <= last_row) {
+      const int2 o = out_ring[(r - 1) & 31];
+      edge_out[r] = make_int2(hi16((uint32_t)o.x) + b31, hi16((uint32_t)o.y) + b31);
     }
-    // lane 0's next left input (the strip's left edge at row it + 2),
-    // read before the row update so that it is ready when the shuffles are
+  };
+  const uint8_t *prof_lo = prof + t * K, *prof_hi = prof + WH + t * K;
+
+  // One row step of this lane.  GENERAL: some lane of the warp is before row
+  // 1, past row R or at row R, lane 31's output row or lane 0's next edge
+  // row is outside 1..R; the other batches of 32 steps run without checks.
+  auto step = [&](int it, uint32_t off_lo, uint32_t off_hi, auto general_tag) {
+    constexpr bool GENERAL = decltype(general_tag)::value;
+    // lane 0's next left input (the strip's left edge at row it + 2), read
+    // before the row update so that it is ready when the shuffles are
     int lx = kNeg16, ly = kNeg16;
-    if (t == 0 && it + 2 <= R) {
+    if (t == 0 && (!GENERAL || it + 2 <= R)) {
       const int2 lv = left_row(it + 2);
       lx = lv.x - b[0];
       ly = lv.y - b[0];
     }
     const int rlo = it - t + 1, rhi = rlo - 32;
     uint32_t Hout, Fout;
-    if (rlo >= 1) {
-      const uint32_t cl = row_ring[rlo & (kRing - 1)], ch = row_ring[rhi & (kRing - 1)];
-      const uint2 wl = *reinterpret_cast<const uint2 *>(prof + (size_t)cl * W + t * K);
-      const uint2 wh = *reinterpret_cast<const uint2 *>(prof + (size_t)ch * W + WH + t * K);
+    if (!GENERAL || rlo >= 1) {
+      const uint2 wl = *reinterpret_cast<const uint2 *>(prof_lo + off_lo);
+      const uint2 wh = *reinterpret_cast<const uint2 *>(prof_hi + off_hi);
       Fout = pk_row<MODE, K>(
           H, E, Hdiag, Fin, NB, Z, best,
           [&](int j) -> uint32_t {
@@ -553,7 +541,7 @@ __device__ int sv_strip_pk(const SvParams &p, SvRequest *rq, int slot, const SvV
             else return NAc;
           });
       Hout = H[K - 1];
-      if constexpr (MODE != kModeLocal) {
+      if constexpr (GENERAL && MODE != kModeLocal) {
         if (rlo == R || rhi == R) {
           const int h = (rhi == R) ? 1 : 0;
           if constexpr (MODE == kModeGlobal) {
@@ -576,7 +564,8 @@ __device__ int sv_strip_pk(const SvParams &p, SvRequest *rq, int slot, const SvV
       Hout = H[K - 1];
       Fout = NEGV;
     }
-    if (t == 31 && rhi >= 1 && rhi <= R) out_ring[(rhi - 1) & 63] = make_int2(hi16(Hout) + b[1], hi16(Fout) + b[1]);
+    if (keep_out && (!GENERAL || (rhi >= 1 && rhi <= R)))
+      out_ring[(rhi - 1) & 31] = make_int2((int)Hout, (int)Fout);
     Hdiag = Hleft;
     uint32_t hs = __shfl_sync(0xffffffffu, Hout, (t + 31) & 31);
     uint32_t fs = __shfl_sync(0xffffffffu, Fout, (t + 31) & 31);
@@ -586,12 +575,61 @@ __device__ int sv_strip_pk(const SvParams &p, SvRequest *rq, int slot, const SvV
     }
     Hleft = __vadd2(hs, D);
     Fin = __vadd2(fs, D);
+  };
+
+  const int nit = R + 63;
+  int flushed = 0;  // edge rows 1..flushed are in global memory
+  for (int it0 = 0; it0 < nit; it0 += 32) {
+    __syncwarp();
+    load_batch(it0 / 32 + 1);
+    put_rows(it0 / 32 + 1, next_rows);
+    next_rows = read_rows(it0 / 32 + 2);
+    if (it0 >= 64 && edge_out) {  // lane 31's high-half rows stored since the last flush: .. it0-63
+      flush_rows(flushed + 1, it0 - 63);
+      flushed = it0 - 63;
+      publish(flushed);
+    }
+    if ((it0 & (kKwRenorm - 1)) == 0 && it0 > 0) {
+      const int d0 = lo16(H[0]), d1 = hi16(H[0]);
+      if constexpr (MODE == kModeLocal) {
+        best_abs = ::max(best_abs, ::max(lo16(best) + b[0], hi16(best) + b[1]));
+        best = NEGV;
+      }
+      b[0] += d0;
+      b[1] += d1;
+      const uint32_t dl = pk16(-d0, -d1);
+#pragma unroll
+      for (int j = 0; j < K; ++j) {
+        H[j] = __vadd2(H[j], dl);
+        E[j] = __vadd2(E[j], dl);
+      }
+      Hdiag = __vadd2(Hdiag, dl);
+      Hleft = __vadd2(Hleft, dl);
+      Fin = __vadd2(Fin, dl);
+      if constexpr (MODE == kModeLocal) {
+        Z = pk16(::max(-b[0], kNeg16), ::max(-b[1], kNeg16));
+#pragma unroll
+        for (int j = 0; j < K; ++j) E[j] = __vmaxs2(E[j], Z);
+      }
+      const int nb0 = __shfl_sync(0xffffffffu, b[0], (t + 31) & 31);
+      const int nb1 = __shfl_sync(0xffffffffu, b[1], (t + 31) & 31);
+      D = (t == 0) ? pk16(0, nb0 - b[1]) : pk16(nb0 - b[0], nb1 - b[1]);
+    }
+    __syncwarp();
+    // this lane's ring entries of the batch are contiguous (mirrored ring)
+    const uint32_t *rl = row_ring + ((it0 - t + 1) & (kRing - 1));
+    const uint32_t *rh = row_ring + ((it0 - t - 31) & (kRing - 1));
+    if (it0 >= 64 && it0 + 33 <= R) {
+#pragma unroll 2
+      for (int k = 0; k < 32; ++k) step(it0 + k, rl[k], rh[k], std::false_type{});
+    } else {
+      const int n = ::min(32, nit - it0);
+      for (int k = 0; k < n; ++k) step(it0 + k, rl[k], rh[k], std::true_type{});
+    }
   }
   __syncwarp();
   if (edge_out) {
-    const int last = ((nit - 1) / 32) * 32;
-    const int first = (last >= 96) ? last - 63 : 1;
-    for (int r = first + t; r <= R; r += 32) edge_out[r] = out_ring[(r - 1) & 63];
+    flush_rows(flushed + 1, R);
     publish(R);
   }
   __syncwarp();
@@ -607,12 +645,17 @@ __device__ int sv_strip_pk(const SvParams &p, SvRequest *rq, int slot, const SvV
 
 __global__ void __launch_bounds__(32 * kSvWarps) ks_kernel(const __grid_constant__ SvParams p) {
   extern __shared__ __align__(16) uint8_t sv_smem[];
+  // Static shared memory is kept small so that four blocks fit on an SM
+  // with a 24-symbol profile: a strip's column codes are needed only while
+  // its profile is built, before the left-edge ring is first written, so
+  // the two share their bytes.
   __shared__ int2 in_ring_s[kSvWarps][64];
-  __shared__ int2 out_ring_s[kSvWarps][64];
-  __shared__ uint32_t row_ring_s[kSvWarps][256];
-  __shared__ __align__(16) uint8_t colc_s[kSvWarps][kSvW];
+  __shared__ int2 out_ring_s[kSvWarps][32];
+  __shared__ uint32_t row_ring_s[kSvWarps][128 + 32];
+  static_assert(sizeof(in_ring_s[0]) >= kSvW, "column codes fit in the left-edge ring");
   const int warp = threadIdx.x >> 5, t = threadIdx.x & 31;
   uint8_t *prof = sv_smem + (size_t)warp * (size_t)p.prof_bytes;
+  uint8_t *colc = reinterpret_cast<uint8_t *>(in_ring_s[warp]);
 
   for (;;) {
     // ---- claim the next task (lane 0), bounded idle wait ----------------
@@ -696,22 +739,22 @@ __global__ void __launch_bounds__(32 * kSvWarps) ks_kernel(const __grid_constant
       val = (mode == kModeGlobal && len) ? -(v.alpha + v.beta * (len - 1)) : 0;
     } else if (v.packed) {
       if (mode == kModeLocal)
-        val = sv_strip_pk<kModeLocal>(p, rq, slot, v, strip, t, prof, colc_s[warp], in_ring_s[warp],
+        val = sv_strip_pk<kModeLocal>(p, rq, slot, v, strip, t, prof, colc, in_ring_s[warp],
                                       out_ring_s[warp], row_ring_s[warp]);
       else if (mode == kModeGlobal)
-        val = sv_strip_pk<kModeGlobal>(p, rq, slot, v, strip, t, prof, colc_s[warp], in_ring_s[warp],
+        val = sv_strip_pk<kModeGlobal>(p, rq, slot, v, strip, t, prof, colc, in_ring_s[warp],
                                        out_ring_s[warp], row_ring_s[warp]);
       else
-        val = sv_strip_pk<kModeSemi>(p, rq, slot, v, strip, t, prof, colc_s[warp], in_ring_s[warp],
+        val = sv_strip_pk<kModeSemi>(p, rq, slot, v, strip, t, prof, colc, in_ring_s[warp],
                                      out_ring_s[warp], row_ring_s[warp]);
     } else if (mode == kModeLocal) {
-      val = sv_strip<kModeLocal>(p, rq, slot, v, strip, t, prof, colc_s[warp], in_ring_s[warp],
+      val = sv_strip<kModeLocal>(p, rq, slot, v, strip, t, prof, colc, in_ring_s[warp],
                                  out_ring_s[warp], row_ring_s[warp]);
     } else if (mode == kModeGlobal) {
-      val = sv_strip<kModeGlobal>(p, rq, slot, v, strip, t, prof, colc_s[warp], in_ring_s[warp],
+      val = sv_strip<kModeGlobal>(p, rq, slot, v, strip, t, prof, colc, in_ring_s[warp],
                                   out_ring_s[warp], row_ring_s[warp]);
     } else {
-      val = sv_strip<kModeSemi>(p, rq, slot, v, strip, t, prof, colc_s[warp], in_ring_s[warp],
+      val = sv_strip<kModeSemi>(p, rq, slot, v, strip, t, prof, colc, in_ring_s[warp],
                                 out_ring_s[warp], row_ring_s[warp]);
     }
     if (t == 0) {
