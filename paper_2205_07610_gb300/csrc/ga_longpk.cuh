@@ -95,11 +95,11 @@ __global__ void __launch_bounds__(128) kw_kernel(const __grid_constant__ KBParam
   constexpr int kWarps = 4;
   constexpr int WH = 32 * K;  // columns per half
   constexpr int W2 = 2 * WH;  // columns per super-stage
-  constexpr int kRing = 256;  // row table words, rows r & 255 (rows -63 .. 0 hold the virtual word)
+  constexpr int kRing = 256;  // row table words, rows r & 255 (+ a mirror of the first 32 entries)
 
   __shared__ int2 in_ring_s[kWarps][64];
-  __shared__ int2 out_ring_s[kWarps][64];
-  __shared__ uint32_t row_ring_s[kWarps][kRing];
+  __shared__ int2 out_ring_s[kWarps][32];
+  __shared__ uint32_t row_ring_s[kWarps][kRing + 32];
 
   const int warp = threadIdx.x >> 5, t = threadIdx.x & 31;
   int2 *in_ring = in_ring_s[warp];
@@ -195,17 +195,28 @@ __global__ void __launch_bounds__(128) kw_kernel(const __grid_constant__ KBParam
           in_ring[(r - 1) & 63] = bnd[r];
         }
       };
-      auto fill_rows = [&](int bb) {  // table words of rows 32bb+1 .. 32bb+32
+      // table words of rows 32bb+1 .. 32bb+32 (0 for the pad rows past R):
+      // read_rows loads the packed word a batch before put_rows stores the
+      // table word, so the load's latency overlaps a batch of rows; the
+      // ring's first 32 entries are mirrored after the last, so that the 32
+      // rows a lane reads in a batch are contiguous
+      auto read_rows = [&](int bb) -> uint32_t {
         const int r = 32 * bb + 1 + t;
-        uint32_t v = 0;  // pad rows
-        if (r <= R) v = tab[packed_code(rowbase, rowpos + r - 1)];
-        row_ring[r & (kRing - 1)] = v;
+        return (r <= R) ? __ldg(rowbase + ((rowpos + r - 1) >> 4)) : 0u;
       };
-      row_ring[(-t) & (kRing - 1)] = virt_w;       // rows 0 .. -31
-      row_ring[(-t - 32) & (kRing - 1)] = virt_w;  // rows -32 .. -63
+      auto put_rows = [&](int bb, uint32_t w) {
+        const int r = 32 * bb + 1 + t;
+        const uint32_t v = (r <= R) ? tab[(w >> (2 * (int)((rowpos + r - 1) & 15))) & 3u] : 0u;
+        const int x = r & (kRing - 1);
+        row_ring[x] = v;
+        if (x < 32) row_ring[x + kRing] = v;
+      };
+      row_ring[(-t) & (kRing - 1)] = virt_w;  // rows 0 .. -31
+      if (t == 0) row_ring[kRing] = virt_w;
       load_batch(0);
-      fill_rows(0);
-      fill_rows(1);
+      put_rows(0, read_rows(0));
+      put_rows(1, read_rows(1));
+      uint32_t next_rows = read_rows(2);  // stored at iteration 0
       __syncwarp();
 
       // inputs of each half's first row: diagonal H(0, first - 1); left the
@@ -221,50 +232,36 @@ __global__ void __launch_bounds__(128) kw_kernel(const __grid_constant__ KBParam
         Fin = pk16(l1.y - b[0], kNeg16);
       }
 
-      const int nit = R + 63;
-      for (int it = 0; it < nit; ++it) {
-        if ((it & 31) == 0) {
-          __syncwarp();
-          load_batch(it / 32 + 1);
-          fill_rows(it / 32 + 2);
-          if (it >= 96) {  // lane 31's high-half rows it-95 .. it-64 are complete
-            const int r = it - 95 + t;
-            bnd[r] = out_ring[(r - 1) & 63];
-          }
-          if ((it & (kKwRenorm - 1)) == 0 && it > 0) {
-            // move each half's base to its current H of the first column
-            const int d0 = lo16(H[0]), d1 = hi16(H[0]);
-            if constexpr (MODE == kModeLocal) {
-              best_abs = ::max(best_abs, ::max(lo16(best) + b[0], hi16(best) + b[1]));
-              best = NEGV;
-            }
-            b[0] += d0;
-            b[1] += d1;
-            const uint32_t dl = pk16(-d0, -d1);
-#pragma unroll
-            for (int j = 0; j < K; ++j) {
-              H[j] = __vadd2(H[j], dl);
-              E[j] = __vadd2(E[j], dl);
-            }
-            Hdiag = __vadd2(Hdiag, dl);
-            Hleft = __vadd2(Hleft, dl);
-            Fin = __vadd2(Fin, dl);
-            if constexpr (MODE == kModeLocal) {  // the zero of Eq. H under the new bases
-              Z = pk16(::max(-b[0], kNeg16), ::max(-b[1], kNeg16));
-#pragma unroll
-              for (int j = 0; j < K; ++j) E[j] = __vmaxs2(E[j], Z);
-            }
-            const int nb0 = __shfl_sync(0xffffffffu, b[0], (t + 31) & 31);
-            const int nb1 = __shfl_sync(0xffffffffu, b[1], (t + 31) & 31);
-            D = (t == 0) ? pk16(0, nb0 - b[1]) : pk16(nb0 - b[0], nb1 - b[1]);
-          }
-          __syncwarp();
+      // Lane 31's high-half output rows are kept as raw packed words and
+      // turned into absolute edge values when they are flushed, with lane
+      // 31's high-half base: every batch flushes all rows stored before it,
+      // ahead of any renormalisation.
+      auto flush_rows = [&](int first, int last_row) {  // at most 32 rows, lane t: row first + t
+        const int b31 = __shfl_sync(0xffffffffu, b[1], 31);
+        const int r = first + t;
+        if (r <= last_row) {
+          const int2 o = out_ring[(r - 1) & 31];
+          bnd[r] = make_int2(hi16((uint32_t)o.x) + b31, hi16((uint32_t)o.y) + b31);
+        }
+      };
+
+      // One row step of this lane.  GENERAL: some lane of the warp is before
+      // row 1, past row R or at row R, lane 31's output row or lane 0's next
+      // edge row is outside 1..R; the other batches of 32 steps run without
+      // checks.
+      auto step = [&](int it, uint32_t twl, uint32_t twh, auto general_tag) {
+        constexpr bool GENERAL = decltype(general_tag)::value;
+        // lane 0's next left input (the edge at row it + 2), read before the
+        // row update so that it is ready when the shuffles are
+        int lx = kNeg16, ly = kNeg16;
+        if (t == 0 && (!GENERAL || it + 2 <= R)) {
+          const int2 lv = left_row(it + 2);
+          lx = lv.x - b[0];
+          ly = lv.y - b[0];
         }
         const int rlo = it - t + 1, rhi = rlo - 32;
         uint32_t Hout, Fout;
-        if (rlo >= 1) {
-          const uint32_t twl = row_ring[rlo & (kRing - 1)];
-          const uint32_t twh = row_ring[rhi & (kRing - 1)];
+        if (!GENERAL || rlo >= 1) {
           Fout = pk_row<MODE, K>(
               H, E, Hdiag, Fin, NB, Z, best, [&](int j) -> uint32_t { return prmt(twl, twh, sel[j]); },
               [&](int j) -> uint32_t {
@@ -272,7 +269,7 @@ __global__ void __launch_bounds__(128) kw_kernel(const __grid_constant__ KBParam
                 else return NAc;
               });
           Hout = H[K - 1];
-          if constexpr (MODE != kModeLocal) {
+          if constexpr (GENERAL && MODE != kModeLocal) {
             if (rlo == R || rhi == R) {
               const int h = (rhi == R) ? 1 : 0;
               if constexpr (MODE == kModeGlobal) {
@@ -296,29 +293,71 @@ __global__ void __launch_bounds__(128) kw_kernel(const __grid_constant__ KBParam
           Hout = H[K - 1];
           Fout = NEGV;
         }
-        if (t == 31 && rhi >= 1 && rhi <= R) out_ring[(rhi - 1) & 63] = make_int2(hi16(Hout) + b[1], hi16(Fout) + b[1]);
+        if (t == 31 && (!GENERAL || (rhi >= 1 && rhi <= R)))
+          out_ring[(rhi - 1) & 31] = make_int2((int)Hout, (int)Fout);
         Hdiag = Hleft;
         uint32_t hs = __shfl_sync(0xffffffffu, Hout, (t + 31) & 31);
         uint32_t fs = __shfl_sync(0xffffffffu, Fout, (t + 31) & 31);
         if (t == 0) {  // low half: the edge's next row; high half: lane 31's low half
-          int lx = kNeg16, ly = kNeg16;
-          if (it + 2 <= R) {
-            const int2 lv = left_row(it + 2);
-            lx = lv.x - b[0];
-            ly = lv.y - b[0];
-          }
           hs = prmt((uint32_t)lx, hs, 0x5410u);
           fs = prmt((uint32_t)ly, fs, 0x5410u);
         }
         Hleft = __vadd2(hs, D);
         Fin = __vadd2(fs, D);
+      };
+
+      const int nit = R + 63;
+      int flushed = 0;  // edge rows 1..flushed are in bnd
+      for (int it0 = 0; it0 < nit; it0 += 32) {
+        __syncwarp();
+        load_batch(it0 / 32 + 1);
+        put_rows(it0 / 32 + 2, next_rows);
+        next_rows = read_rows(it0 / 32 + 3);
+        if (it0 >= 64) {  // lane 31's high-half rows stored since the last flush: .. it0-63
+          flush_rows(flushed + 1, it0 - 63);
+          flushed = it0 - 63;
+        }
+        if ((it0 & (kKwRenorm - 1)) == 0 && it0 > 0) {
+          // move each half's base to its current H of the first column
+          const int d0 = lo16(H[0]), d1 = hi16(H[0]);
+          if constexpr (MODE == kModeLocal) {
+            best_abs = ::max(best_abs, ::max(lo16(best) + b[0], hi16(best) + b[1]));
+            best = NEGV;
+          }
+          b[0] += d0;
+          b[1] += d1;
+          const uint32_t dl = pk16(-d0, -d1);
+#pragma unroll
+          for (int j = 0; j < K; ++j) {
+            H[j] = __vadd2(H[j], dl);
+            E[j] = __vadd2(E[j], dl);
+          }
+          Hdiag = __vadd2(Hdiag, dl);
+          Hleft = __vadd2(Hleft, dl);
+          Fin = __vadd2(Fin, dl);
+          if constexpr (MODE == kModeLocal) {  // the zero of Eq. H under the new bases
+            Z = pk16(::max(-b[0], kNeg16), ::max(-b[1], kNeg16));
+#pragma unroll
+            for (int j = 0; j < K; ++j) E[j] = __vmaxs2(E[j], Z);
+          }
+          const int nb0 = __shfl_sync(0xffffffffu, b[0], (t + 31) & 31);
+          const int nb1 = __shfl_sync(0xffffffffu, b[1], (t + 31) & 31);
+          D = (t == 0) ? pk16(0, nb0 - b[1]) : pk16(nb0 - b[0], nb1 - b[1]);
+        }
+        __syncwarp();
+        // this lane's ring entries of the batch are contiguous (mirrored ring)
+        const uint32_t *rl = row_ring + ((it0 - t + 1) & (kRing - 1));
+        const uint32_t *rh = row_ring + ((it0 - t - 31) & (kRing - 1));
+        if (it0 >= 64 && it0 + 33 <= R) {
+#pragma unroll 2
+          for (int k = 0; k < 32; ++k) step(it0 + k, rl[k], rh[k], std::false_type{});
+        } else {
+          const int n = ::min(32, nit - it0);
+          for (int k = 0; k < n; ++k) step(it0 + k, rl[k], rh[k], std::true_type{});
+        }
       }
       __syncwarp();
-      {  // the rest of lane 31's high-half rows
-        const int last = ((nit - 1) / 32) * 32;
-        const int first = (last >= 96) ? last - 63 : 1;
-        for (int r = first + t; r <= R; r += 32) bnd[r] = out_ring[(r - 1) & 63];
-      }
+      flush_rows(flushed + 1, R);  // the rest of lane 31's high-half rows
       if constexpr (MODE == kModeLocal)
         best_abs = ::max(best_abs, ::max(lo16(best) + b[0], hi16(best) + b[1]));
       __syncwarp();
