@@ -37,8 +37,10 @@ constexpr int kKdRenorm = 128;
 // (2 * 512 + 64 + 128 + 2) * 24 = 29,232 < 32,000 - 2 * 24.
 constexpr int kKdMaxStep = 24;
 
+// Three resident blocks per SM: without the bound ptxas takes 255 registers
+// (one block) for the two row-step variants.
 template <int K>
-__global__ void __launch_bounds__(128) kd_kernel(const __grid_constant__ KCParams p) {
+__global__ void __launch_bounds__(128, 3) kd_kernel(const __grid_constant__ KCParams p) {
   constexpr int kWarps = 4;
   constexpr int W = 32 * K;   // columns per half (one kc_kernel stage)
   constexpr int W2 = 2 * W;   // columns per super-stage
@@ -47,7 +49,7 @@ __global__ void __launch_bounds__(128) kd_kernel(const __grid_constant__ KCParam
 
   __shared__ int2 in_ring_s[kWarps][64];
   __shared__ int2 out_ring_s[kWarps][64];
-  __shared__ uint32_t row_ring_s[kWarps][kRing];
+  __shared__ uint32_t row_ring_s[kWarps][kRing + 32];
 
   const int warp = threadIdx.x >> 5, t = threadIdx.x & 31;
   int2 *in_ring = in_ring_s[warp];
@@ -164,7 +166,9 @@ __global__ void __launch_bounds__(128) kd_kernel(const __grid_constant__ KCParam
           const int r = r0 + 32 * bb + t;
           uint32_t v = 0;
           if (r <= m) v = p.tables[packed_code(p.packed_q, qs + r - 1)];
-          row_ring[r & (kRing - 1)] = v;
+          const int x = r & (kRing - 1);
+          row_ring[x] = v;
+          if (x < 32) row_ring[x + kRing] = v;  // mirror: a batch's rows are contiguous
         };
         // lane 0's low-half left input (H(r, col0), F(r, col0 + 1)) relative
         // to base b, -inf outside the left block's window
@@ -188,42 +192,8 @@ __global__ void __launch_bounds__(128) kd_kernel(const __grid_constant__ KCParam
         __syncwarp();
 
         uint32_t Hdiag = NEGV, Hleft = NEGV, Fin = NEGV;
-        for (int it = 0; it < nit; ++it) {
-          if ((it & 31) == 0) {
-            __syncwarp();
-            load_batch(it / 32 + 1);
-            fill_rows(it / 32 + 2);
-            if (it >= 96) {  // lane 31's high-half rows r0 + it - 96 .. r0 + it - 65
-              const int r = r0 + it - 96 + t;
-              bnd[r] = out_ring[(r - r0) & 63];
-            }
-            if ((it & (kKdRenorm - 1)) == 0 && it > 0) {
-              // each half's base moves to the H of its first lane whose state
-              // (the row before its current one) lies inside its window; a
-              // half with no such lane follows the other half
-              const int rl = r0 + it - t - 1, rh = rl - 32;
-              const unsigned in0 = __ballot_sync(0xffffffffu, rl >= wlo[0] && rl <= whi[0]);
-              const unsigned in1 = __ballot_sync(0xffffffffu, rh >= wlo[1] && rh <= whi[1]);
-              const uint32_t h0v = __shfl_sync(0xffffffffu, H[0], in0 ? __ffs(in0) - 1 : 0);
-              const uint32_t h1v = __shfl_sync(0xffffffffu, H[0], in1 ? __ffs(in1) - 1 : 0);
-              int d0 = in0 ? lo16(h0v) : 0;
-              int d1 = in1 ? hi16(h1v) : 0;
-              if (!in0 && in1) d0 = b1 + d1 - b0;
-              if (!in1) d1 = b0 + d0 - b1;
-              b0 += d0;
-              b1 += d1;
-              const uint32_t dl = pk16(d0, d1);
-#pragma unroll
-              for (int j = 0; j < K; ++j) {
-                H[j] = __vmaxs2(__vsubss2(H[j], dl), NEGV);
-                E[j] = __vmaxs2(__vsubss2(E[j], dl), NEGV);
-              }
-              Hdiag = __vmaxs2(__vsubss2(Hdiag, dl), NEGV);
-              Hleft = __vmaxs2(__vsubss2(Hleft, dl), NEGV);
-              Fin = __vmaxs2(__vsubss2(Fin, dl), NEGV);
-            }
-            __syncwarp();
-          }
+        // One row step with the per-row window logic.
+        auto step_general = [&](int it) {
           const int rl = r0 + it - t, rh = rl - 32;
           // a half's window opens: its state becomes the window's row wlo - 1
           if (rl == wlo[0] || rh == wlo[1]) {
@@ -305,6 +275,91 @@ __global__ void __launch_bounds__(128) kd_kernel(const __grid_constant__ KCParam
           Hdiag = Hleft;
           Hleft = (hs & okm) | (NEGV & ~okm);
           Fin = (fs & okm) | (NEGV & ~okm);
+        };
+        // One row step of an iteration in which every lane is strictly inside
+        // both of its windows, every input from its left neighbour lies inside
+        // that neighbour's window and no lane is at row m: the same step
+        // without the window logic.
+        auto step_fast = [&](int it, uint32_t twl, uint32_t twh) {
+          const int rl = r0 + it - t;
+          int hl = kNeg16, fl = kNeg16;
+          if (t == 0) lane0_left(rl + 1, b0, hl, fl);  // read before the row update
+          uint32_t unused_best = 0;
+          const uint32_t Fout = pk_row<kModeGlobal, K>(
+              H, E, Hdiag, Fin, NB, 0u, unused_best, [&](int j) -> uint32_t { return prmt(twl, twh, sel[j]); },
+              [&](int) -> uint32_t { return NAc; });
+          const uint32_t Hout = H[K - 1];
+          if (t == 31) out_ring[(rl - 32 - r0) & 63] = make_int2(hi16(Hout) + b1, hi16(Fout) + b1);
+          uint32_t hs = __shfl_sync(0xffffffffu, Hout, (t + 31) & 31);
+          uint32_t fs = __shfl_sync(0xffffffffu, Fout, (t + 31) & 31);
+          if (t == 0) {
+            const uint32_t dlh = pk16(0, b0 - b1);
+            hs = __vadd2(prmt((uint32_t)hl, hs, 0x5410u), dlh);
+            fs = __vadd2(prmt((uint32_t)fl, fs, 0x5410u), dlh);
+          }
+          Hdiag = Hleft;
+          Hleft = hs;
+          Fin = fs;
+        };
+        // the iterations [fa, fb] where step_fast applies to every lane
+        int fa, fb;
+        {
+          int a = ::max(wlo[0] + 1, wlo[1] + 33) - r0 + t;
+          int z = ::min(::min(whi[0], m - 1), ::min(whi[1], m - 1) + 32) - r0 + t;
+          a = ::max(a, plo[1] + 31 - r0 + t);  // high-half input rows rh + 1
+          z = ::min(z, phi[1] + 31 - r0 + t);
+          if (t > 0) {  // low-half input rows rl + 1 (lane 0 checks its edge itself)
+            a = ::max(a, plo[0] - 1 - r0 + t);
+            z = ::min(z, phi[0] - 1 - r0 + t);
+          }
+          fa = __reduce_max_sync(0xffffffffu, a);
+          fb = __reduce_min_sync(0xffffffffu, z);
+        }
+        for (int it0 = 0; it0 < nit; it0 += 32) {
+          __syncwarp();
+          load_batch(it0 / 32 + 1);
+          fill_rows(it0 / 32 + 2);
+          if (it0 >= 96) {  // lane 31's high-half rows r0 + it0 - 96 .. r0 + it0 - 65
+            const int r = r0 + it0 - 96 + t;
+            bnd[r] = out_ring[(r - r0) & 63];
+          }
+          if ((it0 & (kKdRenorm - 1)) == 0 && it0 > 0) {
+            // each half's base moves to the H of its first lane whose state
+            // (the row before its current one) lies inside its window; a
+            // half with no such lane follows the other half
+            const int rl = r0 + it0 - t - 1, rh = rl - 32;
+            const unsigned in0 = __ballot_sync(0xffffffffu, rl >= wlo[0] && rl <= whi[0]);
+            const unsigned in1 = __ballot_sync(0xffffffffu, rh >= wlo[1] && rh <= whi[1]);
+            const uint32_t h0v = __shfl_sync(0xffffffffu, H[0], in0 ? __ffs(in0) - 1 : 0);
+            const uint32_t h1v = __shfl_sync(0xffffffffu, H[0], in1 ? __ffs(in1) - 1 : 0);
+            int d0 = in0 ? lo16(h0v) : 0;
+            int d1 = in1 ? hi16(h1v) : 0;
+            if (!in0 && in1) d0 = b1 + d1 - b0;
+            if (!in1) d1 = b0 + d0 - b1;
+            b0 += d0;
+            b1 += d1;
+            const uint32_t dl = pk16(d0, d1);
+#pragma unroll
+            for (int j = 0; j < K; ++j) {
+              H[j] = __vmaxs2(__vsubss2(H[j], dl), NEGV);
+              E[j] = __vmaxs2(__vsubss2(E[j], dl), NEGV);
+            }
+            Hdiag = __vmaxs2(__vsubss2(Hdiag, dl), NEGV);
+            Hleft = __vmaxs2(__vsubss2(Hleft, dl), NEGV);
+            Fin = __vmaxs2(__vsubss2(Fin, dl), NEGV);
+          }
+          __syncwarp();
+          if (it0 >= fa && it0 + 31 <= fb) {
+            // this lane's ring entries of the batch are contiguous (mirrored ring)
+            const uint32_t *rpl = row_ring + ((r0 + it0 - t) & (kRing - 1));
+            const uint32_t *rph = row_ring + ((r0 + it0 - t - 32) & (kRing - 1));
+#pragma unroll 2
+            for (int k = 0; k < 32; ++k) step_fast(it0 + k, rpl[k], rph[k]);
+          } else {
+            const int nb = ::min(32, nit - it0);
+#pragma unroll 1
+            for (int k = 0; k < nb; ++k) step_general(it0 + k);
+          }
         }
         __syncwarp();
         if (high_real) {  // the rest of lane 31's high-half rows
