@@ -220,18 +220,18 @@ __global__ void __launch_bounds__(32 * kKpWarps, KPMinBlocks<K>::value) kp_kerne
       if (t == 0) left(1, Hleft, Fin);
       const uint32_t *plane = kp_prof + t * 4;
 
+      // One row step of this lane.  GENERAL: some lane of the group is
+      // outside rows 1..Rw or lane 0's next edge row is past Rw; the other
+      // batches of G steps run without those checks.
       const int nit = Rw + G - 1;
-      for (int it = 0; it < nit; ++it) {
-        if ((it % G) == 0) {
-          __syncwarp();
-          fill_batch(it / G + 2);
-          load_edge(it / G + 1);
-          __syncwarp();
-        }
+      auto step = [&](int it, uint32_t rc, auto general_tag) {
+        constexpr bool GENERAL = decltype(general_tag)::value;
         const int r = it - t + 1;
+        // lane 0's next left input, read before the row update
+        T hl = Cell::splat(0), fl = NAc;
+        if (t == 0 && (!GENERAL || it + 2 <= Rw)) left(it + 2, hl, fl);
         T Hout = H[K - 1], Fout = Cell::splat(CellInfo<Cell>::kNeg);
-        if ((unsigned)(r - 1) < (unsigned)Rw) {
-          const uint32_t rc = ring[r & (kRing - 1)];
+        if (!GENERAL || (unsigned)(r - 1) < (unsigned)Rw) {
           const uint4 *pr = reinterpret_cast<const uint4 *>(plane + (size_t)rc * W);
           uint32_t w[K];
 #pragma unroll
@@ -248,11 +248,23 @@ __global__ void __launch_bounds__(32 * kKpWarps, KPMinBlocks<K>::value) kp_kerne
         Hleft = __shfl_up_sync(0xffffffffu, Hout, 1, G);
         Fin = __shfl_up_sync(0xffffffffu, Fout, 1, G);
         if (t == 0) {
-          if (it + 2 <= Rw) left(it + 2, Hleft, Fin);
-          else {
-            Hleft = Cell::splat(0);
-            Fin = NAc;
-          }
+          Hleft = hl;
+          Fin = fl;
+        }
+      };
+      for (int it0 = 0; it0 < nit; it0 += G) {
+        __syncwarp();
+        fill_batch(it0 / G + 2);
+        load_edge(it0 / G + 1);
+        __syncwarp();
+        // this lane's ring entries of the batch are contiguous (mirrored ring)
+        const uint8_t *rp = ring + ((it0 - t + 1) & (kRing - 1));
+        if (it0 >= G - 1 && it0 + G + 1 <= Rw) {
+#pragma unroll 2
+          for (int k = 0; k < G; ++k) step(it0 + k, rp[k], std::false_type{});
+        } else {
+          const int nb = ::min(G, nit - it0);
+          for (int k = 0; k < nb; ++k) step(it0 + k, rp[k], std::true_type{});
         }
       }
       __syncwarp();  // the edge stores are ordered before the next stage's loads
