@@ -1048,7 +1048,7 @@ int launch_kp(Call &c, KPParams &kp, int64_t max_grid) {
 // several stages pays for its profile rebuilds and stage edges.
 constexpr int kKpTiles = 6;
 constexpr int kKpTileK[kKpTiles] = {8, 16, 20, 24, 28, 32};
-constexpr double kKpRate[kKpTiles] = {0.68, 0.82, 0.97, 1.0, 1.03, 1.01};
+constexpr double kKpRate[kKpTiles] = {0.81, 0.92, 0.96, 1.0, 1.08, 1.02};
 constexpr double kKpStagedRate = 0.97;
 
 // Tile of a query of m columns: the one that minimises the estimated time
