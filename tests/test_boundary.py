@@ -50,9 +50,11 @@ def test_library_loads_without_gpu(libpath):
 
 
 def test_kernels_compiled_for_sm103a_without_spills(libpath):
-    """No kernel spills registers, except the packed global / semi-global
-    inter-sequence kernels, whose occupancy table allows at most 16 bytes of
-    spill stores where that bought a resident block."""
+    """No kernel spills registers, except at most 16 bytes of spill stores in
+    the packed kernels where that was measured faster: the global /
+    semi-global inter-sequence kernels (a resident block bought by the
+    occupancy table), the protein search kernel (its batch loop unrolled by
+    two) and the packed long-pair kernel (semi-global, 20 columns per lane)."""
     logs = glob.glob(os.path.join(ROOT, "paper_2205_07610_gb300", "_build", "*.ptxas.txt"))
     assert logs
     text = "".join(open(f).read() for f in logs)
@@ -60,9 +62,10 @@ def test_kernels_compiled_for_sm103a_without_spills(libpath):
     found = re.findall(r"Compiling entry function '(\S+)'.*?(\d+) bytes spill stores", text, flags=re.S)
     assert found
     for name, spill in found:
-        packed_gs = name.startswith("_ZN2ga9ka_kernelINS_9CellS16x2ELi1") or \
-            name.startswith("_ZN2ga9ka_kernelINS_9CellS16x2ELi2")
-        assert int(spill) <= (16 if packed_gs else 0), (name, spill)
+        allowed = name.startswith("_ZN2ga9ka_kernelINS_9CellS16x2ELi1") or \
+            name.startswith("_ZN2ga9ka_kernelINS_9CellS16x2ELi2") or \
+            name.startswith("_ZN2ga9kp_kernel") or name.startswith("_ZN2ga9kw_kernelILi2E")
+        assert int(spill) <= (16 if allowed else 0), (name, spill)
 
 
 def test_argument_errors_are_synchronous(libpath):
@@ -106,7 +109,9 @@ def test_plan_arguments_rejected_before_any_cuda_call(libpath):
                      ("ga_plan_destroy", (None,))):
         assert getattr(lib, fn)(*args) == 1, fn
     assert ctypes.sizeof(ga.Tuning) == 16
-    assert ga.Tuning((1 << 16) | 0b101, 0, 1, 0).as_dict() == {"tiles16": [6, 8, 32], "tiles32": [], "concurrent": 1}
+    assert ga.Tuning((1 << 16) | 0b101, 0, 1, 0).as_dict() == {"tiles16": [6, 8, 32], "tiles32": [], "concurrent": 1,
+                                                               "lanes_alt": []}
+    assert ga.Tuning(0x1ff, 0, 0, 0b101).as_dict()["lanes_alt"] == [6, 8]
 
 
 def test_multi_mode_arguments_rejected_before_any_cuda_call(libpath):
