@@ -214,3 +214,26 @@ def test_plan_autotune_keeps_scores_exact():
             got = plan.run(*d)
             want, _ = _oracle(b.q_codes, b.q_off, b.t_codes, b.t_off, b.matrix, b.alpha, b.beta, mode)
             assert_same(got.cpu().numpy(), want, f"autotuned {mode}")
+
+
+def test_plan_run_enqueues_without_blocking_the_host():
+    # a run enqueues kernels only: queued behind ~0.1 s of device work on its
+    # stream (a bounded busy-wait of a fixed cycle count), it returns while
+    # that work is still running, and the scores, read after the stream is
+    # synchronised, equal the oracle's
+    b = synth.mutated_dna_pairs(npairs=5000, seed=synth.SEED_BASE + 93)
+    d = _dev(b.q_codes, b.q_off, b.t_codes, b.t_off)
+    want, _ = _oracle(b.q_codes, b.q_off, b.t_codes, b.t_off, b.matrix, b.alpha, b.beta, "global")
+    s = torch.cuda.Stream()
+    with ga.Plan(b.matrix, b.alpha, b.beta, "global", b.npairs, max(b.q_off[-1], b.t_off[-1]), 400) as plan:
+        plan.run(*d, stream=s)  # first run: lazy module loading, workspace touched
+        s.synchronize()
+        scores = torch.empty(b.npairs, dtype=torch.int32, device="cuda")
+        with torch.cuda.stream(s):
+            torch.cuda._sleep(200_000_000)
+        plan.run(*d, scores=scores, stream=s)
+        still_busy = not s.query()
+        s.synchronize()
+        assert still_busy, "plan.run waited for the stream"
+        assert_same(scores.cpu().numpy(), want, "async plan run")
+        assert plan.stats(stream=s)["status"] == 0
