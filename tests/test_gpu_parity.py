@@ -475,3 +475,22 @@ def test_long_entry_point(mode):
         got = ga.align_long(torch.from_numpy(q).cuda(), torch.from_numpy(t).cuda(), mat, al, be,
                             mode).item()
         assert got == oracle.score(q, t, mat, al, be, mode), (m, n, prot, mode)
+
+
+def test_protein_cross_target_rows_around_batch_boundaries():
+    # the protein search runs its rows in batches of 16, the interior ones
+    # without per-row checks once every lane is inside the target's rows and
+    # lane 0's next edge row exists: targets of one length per call, lengths
+    # around those boundaries, queries in one-stage and staged tiles
+    rng = np.random.default_rng(14)
+    bg = np.concatenate([synth.PROTEIN_BACKGROUND, np.zeros(4)])
+    qs = [rng.choice(24, size=n, p=bg).astype(np.uint8) for n in (40, 200, 448, 700)]
+    qc, qo = synth.pack_csr(qs)
+    mat = synth.blosum62()
+    for L in (1, 2, 15, 16, 17, 18, 31, 32, 33, 34, 35, 47, 48, 49, 50, 64, 65):
+        ts = [rng.choice(24, size=L, p=bg).astype(np.uint8) for _ in range(24)]
+        tc, to = synth.pack_csr(ts)
+        dev = [torch.from_numpy(a).cuda() for a in (qc, qo, tc, to)]
+        got = ga.align_cross(*dev, mat, 11, 1, "local")
+        want, _ = oracle.cross(qc, qo, tc, to, mat, 11, 1, "local", nthreads=NTHREADS)
+        assert_same(got.cpu().numpy().ravel(), want.ravel(), f"protein cross, targets of {L}")

@@ -78,3 +78,23 @@ def test_strip_scoring_limit(mode):
     mat = synth.dna_matrix(3, -3)
     for alpha in (125, 126):  # sigma_max + alpha = 128 (packed) and 129 (int32 strips)
         assert _long(q, t, mat, alpha, 1, mode) == oracle.score(q, t, mat, alpha, 1, mode), (alpha, mode)
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_strip_rows_around_batch_boundaries(mode):
+    # the strip loop runs batches of 32 rows, the interior ones without
+    # per-row checks once every lane is past its first rows (iteration 64)
+    # and before row R: row counts around those boundaries, one and several
+    # strips, both orientations
+    rng = np.random.default_rng(64)
+    dna = synth.dna_matrix(2, -3)
+    b62 = synth.blosum62()
+    for R in (1, 2, 31, 32, 33, 63, 64, 65, 95, 96, 97, 98, 127, 128, 129, 130, 160, 161, 191, 192, 193, 225):
+        for C in (R, 300, 1200):
+            q = rng.integers(0, 4, size=R).astype(np.uint8)
+            t = rng.integers(0, 4, size=C).astype(np.uint8)
+            assert _long(q, t, dna, 5, 2, mode) == oracle.score(q, t, dna, 5, 2, mode), (R, C, mode)
+            assert _long(t, q, dna, 5, 2, mode) == oracle.score(t, q, dna, 5, 2, mode), (C, R, mode)
+        pq = rng.integers(0, 20, size=R).astype(np.uint8)
+        pt = rng.integers(0, 20, size=700).astype(np.uint8)
+        assert _long(pq, pt, b62, 11, 1, mode) == oracle.score(pq, pt, b62, 11, 1, mode), (R, "protein", mode)
