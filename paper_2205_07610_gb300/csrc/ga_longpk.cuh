@@ -89,6 +89,41 @@ __device__ __forceinline__ uint32_t pk_row(uint32_t (&H)[K], uint32_t (&E)[K], u
   return F;
 }
 
+// The same row update with a one-op chain across the columns (local and
+// global mode, where every column's gap open alpha >= beta).  With X(j) =
+// max(Hdiag + sigma, E') the H of a column is max(X(j), F(j)), and since
+// F(j) - alpha <= F(j) - beta the gap entering the next column is
+// F(j+1) = max(F(j) - beta, X(j) - alpha): it no longer waits for H(j).
+// One more ALU and one more FMA op per packed column than pk_row, for a
+// dependency chain of one op per column instead of three: faster where a
+// warp's row step is set by its latency (a scheduler with one warp), slower
+// where the issue slots are shared.
+template <int MODE, int K, class SigFn>
+__device__ __forceinline__ uint32_t pk_row_fc(uint32_t (&H)[K], uint32_t (&E)[K], uint32_t Hdiag, uint32_t Fin,
+                                              uint32_t NB, uint32_t NAc, uint32_t Z, uint32_t &best,
+                                              SigFn SIG) {
+  static_assert(MODE != kModeSemi, "semi-global frees the last column's gap open");
+#pragma unroll
+  for (int j = K - 1; j >= 1; --j) H[j] = __vadd2(H[j - 1], SIG(j));
+  H[0] = __vadd2(Hdiag, SIG(0));
+  uint32_t F = Fin;
+#pragma unroll
+  for (int j = 0; j < K; ++j) {
+    const uint32_t X = __vmaxs2(H[j], E[j]);
+    const uint32_t Fj = F;
+    F = __viaddmax_s16x2(F, NB, __vadd2(X, NAc));
+    H[j] = __vmaxs2(X, Fj);
+    const uint32_t A = __vadd2(H[j], NAc);
+    if constexpr (MODE == kModeLocal) E[j] = __vimax3_s16x2(__vadd2(E[j], NB), A, Z);
+    else E[j] = __viaddmax_s16x2(E[j], NB, A);
+    if constexpr (MODE == kModeLocal) {
+      if ((j & 1) == 1) best = __vimax3_s16x2(best, H[j - 1], H[j]);
+      else if (j == K - 1) best = __vmaxs2(best, H[j]);
+    }
+  }
+  return F;
+}
+
 template <int MODE, int K>
 __global__ void __launch_bounds__(128) kw_kernel(const __grid_constant__ KBParams p) {
   static_assert(kKwMaxStep * (kKwRenorm + 2 * K + 8) < 32000 - 256, "relative int16 cells of this tile width");

@@ -148,6 +148,7 @@ int sv_align_pair(const uint8_t *q, int64_t m, const uint8_t *t, int64_t n, int 
   p.idle_ns = 0;
   p.wait_ns = 10ll * 1000 * 1000 * 1000;
   p.prof_bytes = (sc.A + 1) * kSvW;
+  p.short_chain = 1;  // one pair: each strip warp has a scheduler to itself
   const int grid = std::max(1, std::min((nstrips + kSvWarps - 1) / kSvWarps, nsm * std::max(occ, 1)));
   ks_kernel<<<grid, 32 * kSvWarps, smem, s>>>(p);
   int rc = cudaGetLastError() == cudaSuccess ? GA_OK : GA_ERR_CUDA;

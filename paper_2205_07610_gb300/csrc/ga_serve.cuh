@@ -114,6 +114,8 @@ struct SvParams {
   int64_t idle_ns;
   int64_t wait_ns;
   int32_t prof_bytes;  // per warp: (max A + 1) * kSvW (real residues, one pad / virtual row)
+  int32_t short_chain; // packed local / global strips: the one-op column chain (pk_row_fc), for
+                       // launches of one pair, whose strips each have a scheduler to themselves
 };
 
 __device__ __forceinline__ uint64_t sv_now() {
@@ -356,7 +358,7 @@ __device__ int sv_strip(const SvParams &p, SvRequest *rq, int slot, const SvView
 
 // One strip of one request in packed int16x2 cells (see the file comment):
 // returns what sv_strip returns.
-template <int MODE>
+template <int MODE, bool FC>
 __device__ int sv_strip_pk(const SvParams &p, SvRequest *rq, int slot, const SvView &v, int s, int t,
                            uint8_t *prof, uint8_t *colc, int2 *in_ring, int2 *out_ring,
                            uint32_t *row_ring /* [128 + 32] */) {
@@ -531,15 +533,16 @@ __device__ int sv_strip_pk(const SvParams &p, SvRequest *rq, int slot, const SvV
     if (!GENERAL || rlo >= 1) {
       const uint2 wl = *reinterpret_cast<const uint2 *>(prof_lo + off_lo);
       const uint2 wh = *reinterpret_cast<const uint2 *>(prof_hi + off_hi);
-      Fout = pk_row<MODE, K>(
-          H, E, Hdiag, Fin, NB, Z, best,
-          [&](int j) -> uint32_t {
-            return prmt(j < 4 ? wl.x : wl.y, j < 4 ? wh.x : wh.y, sext_sel<CellS16x2>(j & 3));
-          },
-          [&](int j) -> uint32_t {
-            if constexpr (MODE == kModeSemi) return na[j];
-            else return NAc;
-          });
+      auto sig = [&](int j) -> uint32_t {
+        return prmt(j < 4 ? wl.x : wl.y, j < 4 ? wh.x : wh.y, sext_sel<CellS16x2>(j & 3));
+      };
+      if constexpr (FC && MODE != kModeSemi)
+        Fout = pk_row_fc<MODE, K>(H, E, Hdiag, Fin, NB, NAc, Z, best, sig);
+      else
+        Fout = pk_row<MODE, K>(H, E, Hdiag, Fin, NB, Z, best, sig, [&](int j) -> uint32_t {
+          if constexpr (MODE == kModeSemi) return na[j];
+          else return NAc;
+        });
       Hout = H[K - 1];
       if constexpr (GENERAL && MODE != kModeLocal) {
         if (rlo == R || rhi == R) {
@@ -738,15 +741,21 @@ __global__ void __launch_bounds__(32 * kSvWarps) ks_kernel(const __grid_constant
       const int len = v.R + v.C;
       val = (mode == kModeGlobal && len) ? -(v.alpha + v.beta * (len - 1)) : 0;
     } else if (v.packed) {
-      if (mode == kModeLocal)
-        val = sv_strip_pk<kModeLocal>(p, rq, slot, v, strip, t, prof, colc, in_ring_s[warp],
-                                      out_ring_s[warp], row_ring_s[warp]);
+      if (mode == kModeLocal && p.short_chain)
+        val = sv_strip_pk<kModeLocal, true>(p, rq, slot, v, strip, t, prof, colc, in_ring_s[warp],
+                                            out_ring_s[warp], row_ring_s[warp]);
+      else if (mode == kModeLocal)
+        val = sv_strip_pk<kModeLocal, false>(p, rq, slot, v, strip, t, prof, colc, in_ring_s[warp],
+                                             out_ring_s[warp], row_ring_s[warp]);
+      else if (mode == kModeGlobal && p.short_chain)
+        val = sv_strip_pk<kModeGlobal, true>(p, rq, slot, v, strip, t, prof, colc, in_ring_s[warp],
+                                             out_ring_s[warp], row_ring_s[warp]);
       else if (mode == kModeGlobal)
-        val = sv_strip_pk<kModeGlobal>(p, rq, slot, v, strip, t, prof, colc, in_ring_s[warp],
-                                       out_ring_s[warp], row_ring_s[warp]);
+        val = sv_strip_pk<kModeGlobal, false>(p, rq, slot, v, strip, t, prof, colc, in_ring_s[warp],
+                                              out_ring_s[warp], row_ring_s[warp]);
       else
-        val = sv_strip_pk<kModeSemi>(p, rq, slot, v, strip, t, prof, colc, in_ring_s[warp],
-                                     out_ring_s[warp], row_ring_s[warp]);
+        val = sv_strip_pk<kModeSemi, false>(p, rq, slot, v, strip, t, prof, colc, in_ring_s[warp],
+                                            out_ring_s[warp], row_ring_s[warp]);
     } else if (mode == kModeLocal) {
       val = sv_strip<kModeLocal>(p, rq, slot, v, strip, t, prof, colc, in_ring_s[warp],
                                  out_ring_s[warp], row_ring_s[warp]);
