@@ -247,6 +247,7 @@ struct ga_server {
   unsigned long long *stage_tail = nullptr;
   cudaStream_t kstream = nullptr, feed = nullptr;
   bool kernel_running = false;
+  bool prev_tick_busy = false;
   size_t smem = 0;
   int grid = 0;
   int max_A = 4;
@@ -423,7 +424,13 @@ bool sched_tick(ga_server *S) {
     busy = true;
   }
   // ---- keep the persistent kernel running while work is in flight -----
-  if (S->kernel_running && cudaStreamQuery(S->kstream) == cudaSuccess) S->kernel_running = false;
+  // The persistent kernel leaves only after idle_ns without work (or at
+  // stop): asking the driver whether it is still running costs about as much
+  // as admitting a request, so it is asked after an idle tick and every 256
+  // ticks, not in every busy tick.
+  if (S->kernel_running && (!S->prev_tick_busy || (S->st.scheduler_ticks & 255) == 0) &&
+      cudaStreamQuery(S->kstream) == cudaSuccess)
+    S->kernel_running = false;
   if (!S->kernel_running && S->inflight > 0) {
     SvParams p{};
     p.req = S->req;
@@ -501,6 +508,7 @@ bool sched_tick(ga_server *S) {
     S->st.complete_ns += t_d - t_c;
   }
   ++S->st.scheduler_ticks;
+  S->prev_tick_busy = busy;
   return busy;
 }
 
