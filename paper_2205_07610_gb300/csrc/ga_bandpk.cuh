@@ -3,29 +3,36 @@
 // kc_kernel (ga_banded.cuh), with two adjacent stages of the pair in the two
 // int16 halves of every register.
 //
-// Mapping.  A super-stage covers 2 x 32 x K columns: lane t owns block
-// col0 + tK (low halves) and block col0 + 32K + tK (high halves).  The low
+// Mapping.  A pair runs on a group of G lanes (G = 32: a warp; G = 16: two
+// pairs per warp, neighbours in the band order, so alike in super-stages
+// and window length, run in lockstep: the warp's loops run to the larger of
+// the two, and a group past its own rows or pair runs with empty windows).
+// A super-stage covers 2 x G x K columns: lane t of the group owns block
+// col0 + tK (low halves) and block col0 + GK + tK (high halves).  The low
 // half of lane t runs row r0 + it - t, where r0 is the first row of the low
-// stage's region; the high half runs 32 rows behind, so that lane 0's high
-// half receives lane 31's low half one iteration after it produced the row
+// stage's region; the high half runs G rows behind, so that lane 0's high
+// half receives lane G-1's low half one iteration after it produced the row
 // (as in the packed long kernel, ga_longpk.cuh).  Every block runs only the
 // rows of its window of the block-rounded band; a half outside its window
 // computes values that nothing reads: its state is reset to the window's
 // initial values when the window opens, its outputs are replaced by -inf by
 // the receiving lane (the per-half select of kc_kernel), and the right edge
-// (lane 31's high half) is stored only inside the window.
+// (lane G-1's high half) is stored only inside the window.  A band's blocks
+// enter their windows K + 1 iterations apart, so on a narrow band few of a
+// super-stage's 2G blocks are inside at once; two super-stages of G = 16
+// lanes side by side keep more lanes busy than one of 32.
 //
-// Relative int16 values with one base per half for the whole warp.  The
-// cells a half holds inside their windows at one iteration lie within 32
-// rows and 32K columns of each other; adjacent cells differ by at most
-// sigma_max + alpha, so with the bases renormalised every kKdRenorm
-// iterations (to the H of a lane that is inside its window) every value in
-// play stays within (sigma_max + alpha) * (2 * 32K + 64 + kKdRenorm + 2) of
-// its base, inside int16 when sigma_max + alpha <= kKdMaxStep.  -inf is
-// kNeg16; a renormalisation saturates and re-clamps it, so that it stays
-// below every real value.  Lane 0 converts the low half of lane 31 into its
-// high half with the base difference of the two halves, and the stage edges
-// (global memory, batched through shared memory) hold absolute int32 values.
+// Relative int16 values with one base per half for the group.  The cells a
+// half holds inside their windows at one iteration lie within G rows and GK
+// columns of each other; adjacent cells differ by at most sigma_max +
+// alpha, so with the bases renormalised every kKdRenorm iterations (to the H
+// of a lane that is inside its window) every value in play stays within
+// (sigma_max + alpha) * (2 * GK + 2G + kKdRenorm + 2) of its base, inside
+// int16 when sigma_max + alpha <= kKdMaxStep.  -inf is kNeg16; a
+// renormalisation saturates and re-clamps it, so that it stays below every
+// real value.  Lane 0 converts the low half of lane G-1 into its high half
+// with the base difference of the two halves, and the stage edges (global
+// memory, batched through shared memory) hold absolute int32 values.
 #pragma once
 
 #include "ga_banded.cuh"
@@ -34,72 +41,91 @@
 namespace ga {
 
 constexpr int kKdRenorm = 128;
-// (2 * 512 + 64 + 128 + 2) * 24 = 29,232 < 32,000 - 2 * 24.
+// (2 * 32K + 2G + 128 + 2) * 24 = 29,232 < 32,000 - 2 * 24 at K = 16,
+// G = 32 (16,128 at G = 16).
 constexpr int kKdMaxStep = 24;
 
 // Three resident blocks per SM: without the bound ptxas takes 255 registers
 // (one block) for the two row-step variants.
-template <int K>
+template <int K, int G>
 __global__ void __launch_bounds__(128, 3) kd_kernel(const __grid_constant__ KCParams p) {
+  static_assert(G == 16 || G == 32, "lanes per pair");
   constexpr int kWarps = 4;
-  constexpr int W = 32 * K;   // columns per half (one kc_kernel stage)
+  constexpr int kGroups = 32 / G;       // pairs per warp, one per group of G lanes
+  constexpr int kRowsPerLane = 32 / G;  // rows of a 32-row batch per lane
+  constexpr int W = G * K;    // columns per half (one kc_kernel stage when G = 32)
   constexpr int W2 = 2 * W;   // columns per super-stage
   constexpr int kRing = 256;  // row table words by row & 255
   constexpr int kNeg = kNeg32;
 
-  __shared__ int2 in_ring_s[kWarps][64];
-  __shared__ int2 out_ring_s[kWarps][64];
-  __shared__ uint32_t row_ring_s[kWarps][kRing + 32];
+  __shared__ int2 in_ring_s[kWarps * kGroups][64];
+  __shared__ int2 out_ring_s[kWarps * kGroups][64];
+  __shared__ uint32_t row_ring_s[kWarps * kGroups][kRing + 32];
 
-  const int warp = threadIdx.x >> 5, t = threadIdx.x & 31;
-  int2 *in_ring = in_ring_s[warp];
-  int2 *out_ring = out_ring_s[warp];
-  uint32_t *row_ring = row_ring_s[warp];
-  int2 *bnd = p.bnd + (size_t)(blockIdx.x * kWarps + warp) * (size_t)p.bnd_stride;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int g = lane / G, t = lane % G, gl0 = g * G;  // group, lane in the group, its first lane
+  const unsigned glow = (G == 32) ? 0xffffffffu : ((1u << G) - 1u);
+  const int left_lane = gl0 + (t + G - 1) % G;  // the lane of the group's previous block
+  int2 *in_ring = in_ring_s[warp * kGroups + g];
+  int2 *out_ring = out_ring_s[warp * kGroups + g];
+  uint32_t *row_ring = row_ring_s[warp * kGroups + g];
+  int2 *bnd = p.bnd + ((size_t)(blockIdx.x * kWarps + warp) * kGroups + g) * (size_t)p.bnd_stride;
   const int alpha = p.alpha, beta = p.beta;
   const uint32_t NB = pk16(-beta, -beta);
   const uint32_t NAc = pk16(-alpha, -alpha);
   const uint32_t NEGV = pk16(kNeg16, kNeg16);
 
+  const int npairs = p.range[1] - p.range[0];
   for (;;) {
+    // ---- a task: kGroups consecutive pairs of the order, one per group;
+    // the groups run in lockstep (warp-wide loop bounds), a group whose pair
+    // is done (or that has none) runs with empty windows -----------------
     int task = 0;
-    if (t == 0) task = atomicAdd(p.task_counter, 1);
+    if (lane == 0) task = atomicAdd(p.task_counter, 1);
     task = __shfl_sync(0xffffffffu, task, 0);
-    if (task >= p.range[1] - p.range[0]) break;
-    const int pid = p.order[p.range[0] + task];
-    const int64_t qs = p.q_off[pid], ts = p.t_off[pid];
-    const int m = (int)(p.q_off[pid + 1] - qs), n = (int)(p.t_off[pid + 1] - ts);
+    if (task * kGroups >= npairs) break;
+    const int idx = task * kGroups + g;
+    bool done = idx >= npairs;
+    const int pid = done ? 0 : p.order[p.range[0] + idx];
+    const int64_t qs = done ? 0 : p.q_off[pid], ts = done ? 0 : p.t_off[pid];
+    int m = done ? 0 : (int)(p.q_off[pid + 1] - qs), n = done ? 0 : (int)(p.t_off[pid + 1] - ts);
     const bool bisect = p.bis_lo != nullptr;
-    int w;
-    if (bisect) {
-      const int lw = p.bis_lo[pid], hw = p.bis_hi[pid];
-      if (lw >= hw) continue;
-      w = lw + (hw - lw) / 2;
-    } else {
-      w = p.w0 ? p.w0[pid] : p.default_w0;
+    int w = 0;
+    if (!done) {
+      if (bisect) {
+        const int lw = p.bis_lo[pid], hw = p.bis_hi[pid];
+        if (lw >= hw) done = true;
+        w = lw + (hw - lw) / 2;
+      } else {
+        w = p.w0 ? p.w0[pid] : p.default_w0;
+      }
     }
     if (w < 0) w = 0;
-    if (m == 0 || n == 0) {  // closed form, any band
-      if (bisect) {
-        if (t == 0) p.bis_lo[pid] = p.bis_hi[pid] = 0;
-        continue;
-      }
+    if (!done && (m == 0 || n == 0)) {  // closed form, any band
       if (t == 0) {
-        const int len = m + n;
-        p.scores[pid] = len ? -(alpha + beta * (len - 1)) : 0;
-        if (p.w_used) p.w_used[pid] = w;
+        if (bisect) {
+          p.bis_lo[pid] = p.bis_hi[pid] = 0;
+        } else {
+          const int len = m + n;
+          p.scores[pid] = len ? -(alpha + beta * (len - 1)) : 0;
+          if (p.w_used) p.w_used[pid] = w;
+        }
       }
-      continue;
+      done = true;
     }
+    if (done) m = n = 0;
     const int dn = n - m;
-    const int nst2 = (n + W2 - 1) / W2;
     unsigned long long tries = 0, cells = 0;
 
-    for (;;) {
+    for (;;) {  // one attempt of every group's pair per round
+      if (!__any_sync(0xffffffffu, !done)) break;
       const int lo = (dn < 0 ? dn : 0) - w;
       const int hi = (dn > 0 ? dn : 0) + w;
+      const int nst2 = done ? 0 : (n + W2 - 1) / W2;
+      const int nst2w = (int)__reduce_max_sync(0xffffffffu, (unsigned)nst2);
       int S = kNeg;
-      for (int s2 = 0; s2 < nst2; ++s2) {
+      for (int s2 = 0; s2 < nst2w; ++s2) {
+        const bool sact = s2 < nst2;  // this group has a super-stage s2
         const int col0 = s2 * W2;
         // ---- blocks and windows of both halves --------------------------
         int cb[2], wlo[2], whi[2], plo[2], phi[2];
@@ -111,20 +137,28 @@ __global__ void __launch_bounds__(128, 3) kd_kernel(const __grid_constant__ KCPa
           const int pb = cb[h] - K;
           plo[h] = (cb[h] == 0) ? 0 : ::max(1, pb + 1 - hi);
           phi[h] = (cb[h] == 0) ? ::min(m, -lo) : ::min(m, pb + K - lo);
+          if (!sact) {  // no super-stage s2 for this group: empty windows
+            wlo[h] = plo[h] = 1;
+            whi[h] = phi[h] = 0;
+          }
           if (wlo[h] <= whi[h] && cb[h] < n)
             cells += (unsigned long long)(whi[h] - wlo[h] + 1) * (unsigned long long)::min(K, n - cb[h]);
         }
-        const int r0 = ::max(1, col0 + 1 - hi);  // first row of the low stage (lane 0's window)
+        // first row of the low stage (lane 0's window), last row of the last
+        // real block, iterations of this group and of the warp
+        const int r0 = sact ? ::max(1, col0 + 1 - hi) : 1;
         const int cend = ::min(col0 + W2, n);     // real columns of the super-stage
         const int cbl = ((cend - 1) / K) * K;     // last real block
-        const int r_end = ::min(m, cbl + K - lo);
-        const bool high_real = cend > col0 + W;
-        const int nit = (r_end - r0 + 1) + (high_real ? 63 : 31);
+        const int r_end = sact ? ::min(m, cbl + K - lo) : 0;
+        const bool high_real = sact && cend > col0 + W;
+        const int nit_g = sact ? ::max(0, (r_end - r0 + 1) + (high_real ? 2 * G - 1 : G - 1)) : 0;
+        const int nit = (int)__reduce_max_sync(0xffffffffu, (unsigned)nit_g);
+        const bool edge_out = sact && s2 + 1 < nst2;  // the next super-stage reads this one's edge
         // the owner of column n (0-based n-1) and its half
         const int oc = n - 1 - col0;
         const bool own_stage = oc < W2;
         const int oh = oc >= W ? 1 : 0;
-        const bool owner = own_stage && t == (oc - oh * W) / K;
+        const bool owner = sact && own_stage && t == (oc - oh * W) / K;
         const int oj = (oc - oh * W) % K;
 
         uint32_t sel[K], H[K], E[K];
@@ -146,8 +180,8 @@ __global__ void __launch_bounds__(128, 3) kd_kernel(const __grid_constant__ KCPa
         // bases: the low half's from the left edge of its first row, the
         // high half's the same until it has a lane inside its window
         int b0 = 0;  // super-stage 0 starts at row 1 next to H(0, 0) = 0
-        if (s2 > 0 && t == 0) b0 = bnd[::min(r0, phi[0])].x;  // a row of the left edge near row r0
-        b0 = __shfl_sync(0xffffffffu, b0, 0);
+        if (sact && s2 > 0 && t == 0) b0 = bnd[::min(r0, phi[0])].x;  // a row of the left edge near row r0
+        b0 = __shfl_sync(0xffffffffu, b0, gl0);
         int b1 = b0;
 
         auto col0_h = [&](int r) -> int {  // column 0, strict band rule (absolute)
@@ -156,19 +190,28 @@ __global__ void __launch_bounds__(128, 3) kd_kernel(const __grid_constant__ KCPa
         auto row0_h = [&](int c) -> int {  // H(0, c), absolute, for 1-based column c >= 1
           return -alpha - beta * (c - 1);
         };
+        // rows of batch bb: r0 + 32bb .. r0 + 32bb + 31, kRowsPerLane per lane;
+        // the warp may run past this group's rows (another group's longer
+        // stage), so only rows up to m are read
         auto load_batch = [&](int bb) {
           if (s2 > 0) {
-            const int r = r0 + 32 * bb + t;
-            in_ring[(r - r0) & 63] = bnd[r];
+#pragma unroll
+            for (int k = 0; k < kRowsPerLane; ++k) {
+              const int r = r0 + 32 * bb + t + G * k;
+              if (r <= m) in_ring[(r - r0) & 63] = bnd[r];
+            }
           }
         };
         auto fill_rows = [&](int bb) {
-          const int r = r0 + 32 * bb + t;
-          uint32_t v = 0;
-          if (r <= m) v = p.tables[packed_code(p.packed_q, qs + r - 1)];
-          const int x = r & (kRing - 1);
-          row_ring[x] = v;
-          if (x < 32) row_ring[x + kRing] = v;  // mirror: a batch's rows are contiguous
+#pragma unroll
+          for (int k = 0; k < kRowsPerLane; ++k) {
+            const int r = r0 + 32 * bb + t + G * k;
+            uint32_t v = 0;
+            if (r <= m) v = p.tables[packed_code(p.packed_q, qs + r - 1)];
+            const int x = r & (kRing - 1);
+            row_ring[x] = v;
+            if (x < 32) row_ring[x + kRing] = v;  // mirror: a batch's rows are contiguous
+          }
         };
         // lane 0's low-half left input (H(r, col0), F(r, col0 + 1)) relative
         // to base b, -inf outside the left block's window
@@ -194,7 +237,7 @@ __global__ void __launch_bounds__(128, 3) kd_kernel(const __grid_constant__ KCPa
         uint32_t Hdiag = NEGV, Hleft = NEGV, Fin = NEGV;
         // One row step with the per-row window logic.
         auto step_general = [&](int it) {
-          const int rl = r0 + it - t, rh = rl - 32;
+          const int rl = r0 + it - t, rh = rl - G;
           // a half's window opens: its state becomes the window's row wlo - 1
           if (rl == wlo[0] || rh == wlo[1]) {
 #pragma unroll
@@ -256,12 +299,12 @@ __global__ void __launch_bounds__(128, 3) kd_kernel(const __grid_constant__ KCPa
               S = oh ? hi16(v) + b1 : lo16(v) + b0;
             }
           }
-          if (t == 31 && in1) out_ring[(rh - r0) & 63] = make_int2(hi16(Hout) + b1, hi16(Fout) + b1);
+          if (t == G - 1 && in1) out_ring[(rh - r0) & 63] = make_int2(hi16(Hout) + b1, hi16(Fout) + b1);
           // next row's inputs: lane t-1's outputs, -inf outside its window;
           // lane 0: the edge (low half) and lane 31's low half (high half)
           const int rn0 = rl + 1, rn1 = rh + 1;
-          uint32_t hs = __shfl_sync(0xffffffffu, Hout, (t + 31) & 31);
-          uint32_t fs = __shfl_sync(0xffffffffu, Fout, (t + 31) & 31);
+          uint32_t hs = __shfl_sync(0xffffffffu, Hout, left_lane);
+          uint32_t fs = __shfl_sync(0xffffffffu, Fout, left_lane);
           if (t == 0) {
             int hl, fl;
             lane0_left(rn0, b0, hl, fl);
@@ -289,9 +332,9 @@ __global__ void __launch_bounds__(128, 3) kd_kernel(const __grid_constant__ KCPa
               H, E, Hdiag, Fin, NB, 0u, unused_best, [&](int j) -> uint32_t { return prmt(twl, twh, sel[j]); },
               [&](int) -> uint32_t { return NAc; });
           const uint32_t Hout = H[K - 1];
-          if (t == 31) out_ring[(rl - 32 - r0) & 63] = make_int2(hi16(Hout) + b1, hi16(Fout) + b1);
-          uint32_t hs = __shfl_sync(0xffffffffu, Hout, (t + 31) & 31);
-          uint32_t fs = __shfl_sync(0xffffffffu, Fout, (t + 31) & 31);
+          if (t == G - 1) out_ring[(rl - G - r0) & 63] = make_int2(hi16(Hout) + b1, hi16(Fout) + b1);
+          uint32_t hs = __shfl_sync(0xffffffffu, Hout, left_lane);
+          uint32_t fs = __shfl_sync(0xffffffffu, Fout, left_lane);
           if (t == 0) {
             const uint32_t dlh = pk16(0, b0 - b1);
             hs = __vadd2(prmt((uint32_t)hl, hs, 0x5410u), dlh);
@@ -304,34 +347,46 @@ __global__ void __launch_bounds__(128, 3) kd_kernel(const __grid_constant__ KCPa
         // the iterations [fa, fb] where step_fast applies to every lane
         int fa, fb;
         {
-          int a = ::max(wlo[0] + 1, wlo[1] + 33) - r0 + t;
-          int z = ::min(::min(whi[0], m - 1), ::min(whi[1], m - 1) + 32) - r0 + t;
-          a = ::max(a, plo[1] + 31 - r0 + t);  // high-half input rows rh + 1
-          z = ::min(z, phi[1] + 31 - r0 + t);
+          int a = ::max(wlo[0] + 1, wlo[1] + G + 1) - r0 + t;
+          int z = ::min(::min(whi[0], m - 1), ::min(whi[1], m - 1) + G) - r0 + t;
+          a = ::max(a, plo[1] + G - 1 - r0 + t);  // high-half input rows rh + 1
+          z = ::min(z, phi[1] + G - 1 - r0 + t);
           if (t > 0) {  // low-half input rows rl + 1 (lane 0 checks its edge itself)
             a = ::max(a, plo[0] - 1 - r0 + t);
             z = ::min(z, phi[0] - 1 - r0 + t);
           }
+          if (!sact) {  // a group without this super-stage constrains nothing
+            a = -(1 << 29);
+            z = 1 << 29;
+          }
           fa = __reduce_max_sync(0xffffffffu, a);
           fb = __reduce_min_sync(0xffffffffu, z);
         }
+        // lane G-1's high-half edge rows r0 .. flushed are in bnd; a batch
+        // flushes the rows stored since the last one (at most 32)
+        int flushed = r0 - 1;
         for (int it0 = 0; it0 < nit; it0 += 32) {
           __syncwarp();
           load_batch(it0 / 32 + 1);
           fill_rows(it0 / 32 + 2);
-          if (it0 >= 96) {  // lane 31's high-half rows r0 + it0 - 96 .. r0 + it0 - 65
-            const int r = r0 + it0 - 96 + t;
-            bnd[r] = out_ring[(r - r0) & 63];
+          if (edge_out) {  // the last stored row: r0 + it0 - 2G (iteration it0 - 1)
+            const int last = ::min(r0 + it0 - 2 * G, r_end);
+#pragma unroll
+            for (int k = 0; k < kRowsPerLane; ++k) {
+              const int r = flushed + 1 + t + G * k;
+              if (r <= last) bnd[r] = out_ring[(r - r0) & 63];
+            }
+            flushed = ::max(flushed, last);
           }
           if ((it0 & (kKdRenorm - 1)) == 0 && it0 > 0) {
             // each half's base moves to the H of its first lane whose state
             // (the row before its current one) lies inside its window; a
             // half with no such lane follows the other half
-            const int rl = r0 + it0 - t - 1, rh = rl - 32;
-            const unsigned in0 = __ballot_sync(0xffffffffu, rl >= wlo[0] && rl <= whi[0]);
-            const unsigned in1 = __ballot_sync(0xffffffffu, rh >= wlo[1] && rh <= whi[1]);
-            const uint32_t h0v = __shfl_sync(0xffffffffu, H[0], in0 ? __ffs(in0) - 1 : 0);
-            const uint32_t h1v = __shfl_sync(0xffffffffu, H[0], in1 ? __ffs(in1) - 1 : 0);
+            const int rl = r0 + it0 - t - 1, rh = rl - G;
+            const unsigned in0 = (__ballot_sync(0xffffffffu, rl >= wlo[0] && rl <= whi[0]) >> gl0) & glow;
+            const unsigned in1 = (__ballot_sync(0xffffffffu, rh >= wlo[1] && rh <= whi[1]) >> gl0) & glow;
+            const uint32_t h0v = __shfl_sync(0xffffffffu, H[0], gl0 + (in0 ? __ffs(in0) - 1 : 0));
+            const uint32_t h1v = __shfl_sync(0xffffffffu, H[0], gl0 + (in1 ? __ffs(in1) - 1 : 0));
             int d0 = in0 ? lo16(h0v) : 0;
             int d1 = in1 ? hi16(h1v) : 0;
             if (!in0 && in1) d0 = b1 + d1 - b0;
@@ -352,7 +407,7 @@ __global__ void __launch_bounds__(128, 3) kd_kernel(const __grid_constant__ KCPa
           if (it0 >= fa && it0 + 31 <= fb) {
             // this lane's ring entries of the batch are contiguous (mirrored ring)
             const uint32_t *rpl = row_ring + ((r0 + it0 - t) & (kRing - 1));
-            const uint32_t *rph = row_ring + ((r0 + it0 - t - 32) & (kRing - 1));
+            const uint32_t *rph = row_ring + ((r0 + it0 - t - G) & (kRing - 1));
 #pragma unroll 2
             for (int k = 0; k < 32; ++k) step_fast(it0 + k, rpl[k], rph[k]);
           } else {
@@ -362,42 +417,40 @@ __global__ void __launch_bounds__(128, 3) kd_kernel(const __grid_constant__ KCPa
           }
         }
         __syncwarp();
-        if (high_real) {  // the rest of lane 31's high-half rows
-          const int last = ((nit - 1) / 32) * 32;
-          const int first = (last >= 96) ? r0 + last - 64 : r0;
-          for (int r = first + t; r <= r_end; r += 32) bnd[r] = out_ring[(r - r0) & 63];
+        if (edge_out) {  // the rest of lane G-1's high-half rows
+          for (int r = flushed + 1 + t; r <= r_end; r += G) bnd[r] = out_ring[(r - r0) & 63];
         }
         __syncwarp();
       }
-      // certificate (as kc_kernel)
-      S = __reduce_max_sync(0xffffffffu, S);
-      const bool covers = (lo <= -m) && (hi >= n);
-      int64_t ub = INT64_MIN;
-      if (lo - 1 >= -m) ub = ::max(ub, band_ub(m, n, p.sigma_max_pos, alpha, beta, lo - 1));
-      if (hi + 1 <= n) ub = ::max(ub, band_ub(m, n, p.sigma_max_pos, alpha, beta, hi + 1));
-      if (bisect) {
-        if (t == 0) {
-          if (covers || (int64_t)S >= ub) p.bis_hi[pid] = w;
-          else p.bis_lo[pid] = w + 1;
+      // certificate (as kc_kernel), per group
+      S = group_max<G>(S);
+      if (!done) {
+        const bool covers = (lo <= -m) && (hi >= n);
+        int64_t ub = INT64_MIN;
+        if (lo - 1 >= -m) ub = ::max(ub, band_ub(m, n, p.sigma_max_pos, alpha, beta, lo - 1));
+        if (hi + 1 <= n) ub = ::max(ub, band_ub(m, n, p.sigma_max_pos, alpha, beta, hi + 1));
+        if (bisect) {
+          if (t == 0) {
+            if (covers || (int64_t)S >= ub) p.bis_hi[pid] = w;
+            else p.bis_lo[pid] = w + 1;
+          }
+          done = true;
+        } else if (covers || (int64_t)S >= ub) {
+          if (t == 0) {
+            p.scores[pid] = S;
+            if (p.w_used) p.w_used[pid] = w;
+          }
+          done = true;
+        } else {
+          w = (w == 0) ? 1 : 2 * w;
+          ++tries;
         }
-        break;
       }
-      if (covers || (int64_t)S >= ub) {
-        if (t == 0) {
-          p.scores[pid] = S;
-          if (p.w_used) p.w_used[pid] = w;
-        }
-        break;
-      }
-      w = (w == 0) ? 1 : 2 * w;
-      ++tries;
     }
 #pragma unroll
     for (int o = 16; o >= 1; o >>= 1) cells += __shfl_xor_sync(0xffffffffu, cells, o);
-    if (t == 0) {
-      if (tries) atomicAdd(p.retries, tries);
-      atomicAdd(p.cells, cells);
-    }
+    if (t == 0 && tries) atomicAdd(p.retries, tries);
+    if (lane == 0) atomicAdd(p.cells, cells);
   }
 }
 

@@ -16,14 +16,16 @@ int blocks_per_sm_kc() {
   return n;
 }
 
-cudaError_t launch_kd(const KCParams &p, int grid, cudaStream_t s) {
-  kd_kernel<kKcK><<<grid, kKcThreads, 0, s>>>(p);
+cudaError_t launch_kd(const KCParams &p, int grid, cudaStream_t s, bool narrow) {
+  if (narrow) kd_kernel<kKcK, kKdGNarrow><<<grid, kKcThreads, 0, s>>>(p);
+  else kd_kernel<kKcK, kKdGWide><<<grid, kKcThreads, 0, s>>>(p);
   return cudaGetLastError();
 }
 
-int blocks_per_sm_kd() {
+int blocks_per_sm_kd(bool narrow) {
   int n = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kd_kernel<kKcK>, kKcThreads, 0);
+  if (narrow) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kd_kernel<kKcK, kKdGNarrow>, kKcThreads, 0);
+  else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kd_kernel<kKcK, kKdGWide>, kKcThreads, 0);
   return n;
 }
 

@@ -23,6 +23,20 @@ constexpr int kKbK = 16;
 constexpr int kKcK = 16;
 constexpr int kKcThreads = 128;
 constexpr int kKcWarps = kKcThreads / 32;
+// Lanes per pair of the packed band kernel.  A band's blocks enter their
+// windows one after another, 17 iterations apart, so on a narrow band a
+// super-stage of 64 blocks on one warp leaves most lanes outside their
+// windows; with 16 lanes per pair a warp runs two pairs (neighbours in the
+// band order, alike in super-stages and window length) in lockstep, two
+// super-stages of 32 blocks side by side.  Measured on GB300 (20k long DNA
+// pairs), 16 lanes are faster only for band doubling from a small constant
+// start (w0 = 16: 689 -> 586 ms); from the learned or the best constant
+// start (wider bands, and a pair whose partner needs another attempt idles
+// meanwhile) 32 lanes are (168 vs 189 ms, 278 vs 296 ms).
+constexpr int kKdGNarrow = 16;
+constexpr int kKdGWide = 32;
+constexpr int kKdNarrowMaxW0 = 64;  // constant starts up to this run 16 lanes per pair
+constexpr int kKdStageCols = 2 * kKdGNarrow * kKcK;  // the band order's super-stage unit
 constexpr int kKbThreads = 128;
 constexpr int kKbWarps = kKbThreads / 32;
 
@@ -88,8 +102,8 @@ struct KCParams;
 cudaError_t launch_kc(const KCParams &p, int grid, cudaStream_t s);
 int blocks_per_sm_kc();
 // Packed banded kernel (sigma_max + alpha <= kKdMaxStep, ga_bandpk.cuh).
-cudaError_t launch_kd(const KCParams &p, int grid, cudaStream_t s);
-int blocks_per_sm_kd();
+cudaError_t launch_kd(const KCParams &p, int grid, cudaStream_t s, bool narrow);
+int blocks_per_sm_kd(bool narrow);
 
 // Launch / occupancy of tile `bin` (compile-time recursion over the tiles).
 template <class CELL, int MODE, int I = 0>

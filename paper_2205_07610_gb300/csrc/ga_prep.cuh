@@ -301,6 +301,7 @@ struct BandPlanParams {
   int32_t *status;
   unsigned long long *cells;
   int32_t *max_rows;
+  int32_t stage_cols;  // columns of a super-stage of the packed band kernel
 };
 
 __global__ void band_plan_kernel(BandPlanParams p) {
@@ -326,12 +327,17 @@ __global__ void band_plan_kernel(BandPlanParams p) {
     } else {
       my_cells = (unsigned long long)(m * n);
       atomicMax(p.max_rows, (int)m);
+      // Neighbours in the order share a warp of the packed band kernel and
+      // run in lockstep, so the key groups pairs of the same shape: super-
+      // stages of stage_cols columns (exact up to 31), then the length of a
+      // block's row window, 2w + |n - m| + 16 (four buckets per octave);
+      // largest first.
       const int64_t d = n - m;
-      const unsigned long long est =
-          (unsigned long long)m * (unsigned long long)((d < 0 ? -d : d) + 2 * (int64_t)w + 1);
-      const int lg = 63 - __clzll((long long)est);
-      const int bucket = lg >= 5 ? lg * 32 + (int)((est >> (lg - 5)) & 31u) : (int)est;
-      key = (uint32_t)(kRBuckets - 1 - ::min(bucket, kRBuckets - 1));
+      const int64_t nst = (n + p.stage_cols - 1) / p.stage_cols;
+      const int64_t L = (d < 0 ? -d : d) + 2 * (int64_t)w + 16;
+      const int lg = 63 - __clzll((long long)L);
+      const int lb = ::min(63, lg * 4 + (int)((L >> (lg - 2)) & 3));
+      key = (uint32_t)(kRBuckets - 1 - (int)((nst < 31 ? nst : 31) * 64 + lb));
     }
     p.keys[i] = key;
   }
