@@ -868,8 +868,7 @@ struct BandRun {
   uint32_t *keys = nullptr;
   int32_t *sorted = nullptr;
   int max_rows = 0, grid = 0, launches = 0;
-  bool packed = false;  // packed int16x2 kernel (sigma_max + alpha <= kKdMaxStep)
-  bool narrow = false;  // packed kernel with 16 lanes per pair (small constant start)
+  bool packed = false;  // packed int16x2 kernel (sigma_max + alpha <= kKzMaxStep)
   int64_t stride = 0;
   int2 *bnd = nullptr;
   BandRun(Call &cc, const uint8_t *qc, const int64_t *qo, const uint8_t *tc, const int64_t *to, int64_t np)
@@ -903,7 +902,7 @@ struct BandRun {
     bp.status = &c.small->status;
     bp.cells = &c.small->cells;
     bp.max_rows = &c.small->max_rows;
-    bp.stage_cols = kKdStageCols;
+    bp.stage_cols = kBandStageCols;
     const unsigned nb = (unsigned)((npairs + 255) / 256);
     band_plan_kernel<<<nb, 256, 0, c.s>>>(bp);
     hist_kernel<<<nb, 256, 0, c.s>>>(keys, npairs, c.hist);
@@ -919,14 +918,15 @@ struct BandRun {
       return GA_ERR_CUDA;
     max_rows = h[0];
     if (max_rows > 0) {
-      packed = std::max(c.sc.smax, 0) + c.sc.alpha <= kKdMaxStep;
-      narrow = packed && w0 == nullptr && default_w0 <= kKdNarrowMaxW0;
-      const int occ = std::max(packed ? blocks_per_sm_kd(narrow) : blocks_per_sm_kc(), 1);
-      const int per_warp = narrow ? 32 / kKdGNarrow : 1;  // edge buffers: one per pair in flight
-      const int64_t want = (npairs + kKcWarps * per_warp - 1) / (kKcWarps * per_warp);
+      packed = std::max(c.sc.smax, 0) + c.sc.alpha <= kKzMaxStep;
+      const int occ = std::max(packed ? blocks_per_sm_kz() : blocks_per_sm_kc(), 1);
+      const int64_t want = (npairs + kKcWarps - 1) / kKcWarps;
       grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)c.nsm * occ));
       stride = (int64_t)max_rows + 128;
-      bnd = c.al.get<int2>((size_t)grid * kKcWarps * per_warp * (size_t)stride);
+      // edge buffers, one per warp: int2 per row (kc_kernel), KZEdge (16
+      // bytes) per row (kz_kernel)
+      const size_t rows = (size_t)grid * kKcWarps * (size_t)stride;
+      bnd = packed ? reinterpret_cast<int2 *>(c.al.get<int4>(rows)) : c.al.get<int2>(rows);
       if (c.al.failed) return GA_ERR_OOM;
     }
     return GA_OK;
@@ -962,7 +962,7 @@ struct BandRun {
     kc.bis_lo = bis_lo;
     kc.bis_hi = bis_hi;
     c.dp_begin();
-    const cudaError_t e = packed ? launch_kd(kc, grid, c.s, narrow) : launch_kc(kc, grid, c.s);
+    const cudaError_t e = packed ? launch_kz(kc, grid, c.s) : launch_kc(kc, grid, c.s);
     c.dp_end();
     return e == cudaSuccess ? GA_OK : GA_ERR_CUDA;
   }

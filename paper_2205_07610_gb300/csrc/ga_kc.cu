@@ -1,5 +1,5 @@
 // Banded (band-doubling) kernel instantiations: int32 and packed int16x2.
-#include "ga_bandpk.cuh"
+#include "ga_bandcz.cuh"
 #include "ga_banded.cuh"
 #include "ga_launch.h"
 
@@ -16,16 +16,14 @@ int blocks_per_sm_kc() {
   return n;
 }
 
-cudaError_t launch_kd(const KCParams &p, int grid, cudaStream_t s, bool narrow) {
-  if (narrow) kd_kernel<kKcK, kKdGNarrow><<<grid, kKcThreads, 0, s>>>(p);
-  else kd_kernel<kKcK, kKdGWide><<<grid, kKcThreads, 0, s>>>(p);
+cudaError_t launch_kz(const KCParams &p, int grid, cudaStream_t s) {
+  kz_kernel<kKcK><<<grid, kKcThreads, 0, s>>>(p);
   return cudaGetLastError();
 }
 
-int blocks_per_sm_kd(bool narrow) {
+int blocks_per_sm_kz() {
   int n = 0;
-  if (narrow) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kd_kernel<kKcK, kKdGNarrow>, kKcThreads, 0);
-  else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kd_kernel<kKcK, kKdGWide>, kKcThreads, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kz_kernel<kKcK>, kKcThreads, 0);
   return n;
 }
 

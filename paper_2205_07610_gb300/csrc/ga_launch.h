@@ -8,7 +8,7 @@
 #include "ga_inter.cuh"
 #include "ga_long.cuh"
 #include "ga_longpk.cuh"
-#include "ga_bandpk.cuh"
+#include "ga_bandcz.cuh"
 
 namespace ga {
 
@@ -23,20 +23,9 @@ constexpr int kKbK = 16;
 constexpr int kKcK = 16;
 constexpr int kKcThreads = 128;
 constexpr int kKcWarps = kKcThreads / 32;
-// Lanes per pair of the packed band kernel.  A band's blocks enter their
-// windows one after another, 17 iterations apart, so on a narrow band a
-// super-stage of 64 blocks on one warp leaves most lanes outside their
-// windows; with 16 lanes per pair a warp runs two pairs (neighbours in the
-// band order, alike in super-stages and window length) in lockstep, two
-// super-stages of 32 blocks side by side.  Measured on GB300 (20k long DNA
-// pairs), 16 lanes are faster only for band doubling from a small constant
-// start (w0 = 16: 689 -> 586 ms); from the learned or the best constant
-// start (wider bands, and a pair whose partner needs another attempt idles
-// meanwhile) 32 lanes are (168 vs 189 ms, 278 vs 296 ms).
-constexpr int kKdGNarrow = 16;
-constexpr int kKdGWide = 32;
-constexpr int kKdNarrowMaxW0 = 64;  // constant starts up to this run 16 lanes per pair
-constexpr int kKdStageCols = 2 * kKdGNarrow * kKcK;  // the band order's super-stage unit
+// Columns of a super-stage of the packed band kernel (64 blocks of kKcK
+// columns): the unit of the band order's work key.
+constexpr int kBandStageCols = 64 * kKcK;
 constexpr int kKbThreads = 128;
 constexpr int kKbWarps = kKbThreads / 32;
 
@@ -101,9 +90,10 @@ int blocks_per_sm_kw_semi();
 struct KCParams;
 cudaError_t launch_kc(const KCParams &p, int grid, cudaStream_t s);
 int blocks_per_sm_kc();
-// Packed banded kernel (sigma_max + alpha <= kKdMaxStep, ga_bandpk.cuh).
-cudaError_t launch_kd(const KCParams &p, int grid, cudaStream_t s, bool narrow);
-int blocks_per_sm_kd(bool narrow);
+// Packed banded kernel (sigma_max + alpha <= kKzMaxStep, ga_bandcz.cuh);
+// its edge buffer holds one KZEdge (16 bytes) per row and warp.
+cudaError_t launch_kz(const KCParams &p, int grid, cudaStream_t s);
+int blocks_per_sm_kz();
 
 // Launch / occupancy of tile `bin` (compile-time recursion over the tiles).
 template <class CELL, int MODE, int I = 0>

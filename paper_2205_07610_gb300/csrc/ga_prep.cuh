@@ -327,11 +327,11 @@ __global__ void band_plan_kernel(BandPlanParams p) {
     } else {
       my_cells = (unsigned long long)(m * n);
       atomicMax(p.max_rows, (int)m);
-      // Neighbours in the order share a warp of the packed band kernel and
-      // run in lockstep, so the key groups pairs of the same shape: super-
-      // stages of stage_cols columns (exact up to 31), then the length of a
-      // block's row window, 2w + |n - m| + 16 (four buckets per octave);
-      // largest first.
+      // The band kernels take pairs from a queue in this order, so the key
+      // puts the most work first (the last pairs to start are the short
+      // ones): super-stages of stage_cols columns (exact up to 31), then the
+      // length of a block's row window, 2w + |n - m| + 16 (four buckets per
+      // octave).
       const int64_t d = n - m;
       const int64_t nst = (n + p.stage_cols - 1) / p.stage_cols;
       const int64_t L = (d < 0 ? -d : d) + 2 * (int64_t)w + 16;
