@@ -126,3 +126,34 @@ def test_banded_single_diagonal_and_super_stage_edges():
     b = synth.Batch(qc, qo, tc, to, synth.dna_matrix(2, -3), 5, 2, "diag")
     st = _check(b, np.zeros(b.npairs, dtype=np.int64))
     assert st["band_retries"] > 0
+
+
+def test_banded_schedule_spacing_boundaries():
+    # The packed band kernel starts super-stage s (64 blocks of 16 columns)
+    # D * s iterations after super-stage 0, D = max(128, min(m, B - 1008) + 1)
+    # for a window of B = 2w + |n - m| + 16 rows: shapes at the 128 floor
+    # and just above it, D clipped by a short query, a query much longer
+    # than its target, and widths around multiples of 1,024 columns; each as
+    # a related pair (a mutated copy) and an unrelated one.
+    rng = np.random.default_rng(17)
+    shapes = [(1500, 1500, 559), (1500, 1500, 560), (1500, 1500, 561), (3000, 3300, 400),
+              (300, 4000, 0), (130, 5000, 0), (100, 5000, 0), (5000, 100, 0),
+              (2047, 2047, 16), (2048, 2048, 16), (2049, 2049, 16), (4097, 4097, 100)]
+    qs, ts, w0s = [], [], []
+    for m, n, w in shapes:
+        q = rng.integers(0, 4, size=m).astype(np.uint8)
+        t = q.copy()
+        if n <= m:
+            t = t[:n]
+        else:
+            t = np.concatenate([t, rng.integers(0, 4, size=n - m).astype(np.uint8)])
+        sub = rng.random(n) < 0.05
+        t[sub] = (t[sub] + rng.integers(1, 4, size=int(sub.sum()))) % 4
+        qs += [q, q]
+        ts += [t, rng.integers(0, 4, size=n).astype(np.uint8)]
+        w0s += [w, w]
+    qc, qo = synth.pack_csr(qs)
+    tc, to = synth.pack_csr(ts)
+    b = synth.Batch(qc, qo, tc, to, synth.dna_matrix(2, -3), 5, 2, "spacing")
+    st = _check(b, np.asarray(w0s, dtype=np.int64))
+    assert st["band_retries"] > 0
