@@ -75,15 +75,15 @@ __global__ void __launch_bounds__(128, 3) kz_kernel(const __grid_constant__ KCPa
   constexpr int kRing = 256; // row table words per super-stage slot
   constexpr int kFifo = 128; // edge FIFO slots (iterations)
 
-  __shared__ uint32_t row_s[kWarps][3][kRing];
+  __shared__ uint32_t row_s[kWarps][3][kRing + 32];  // + a copy of slots 0..31
   __shared__ uint4 selb_s[kWarps][3][W2 / 16];  // one selector byte per column
   __shared__ int2 fabs_s[kWarps][kFifo];        // absolute edge values by iteration
-  __shared__ uint32_t frel_s[kWarps][kFifo];    // the same relative to lane 0's base
+  __shared__ uint32_t frel_s[kWarps][kFifo + 32];  // the same relative to lane 0's base, + a copy of slots 0..31
   __shared__ int2 blk_s[kWarps][2][32];         // per lane-half: first column, first window row
 
   const int warp = threadIdx.x >> 5, t = threadIdx.x & 31;
   const int left_lane = (t + 31) & 31, right_lane = (t + 1) & 31;
-  uint32_t(*rowr)[kRing] = row_s[warp];
+  uint32_t(*rowr)[kRing + 32] = row_s[warp];
   uint4(*selb)[W2 / 16] = selb_s[warp];
   int2 *fabs = fabs_s[warp];
   uint32_t *frel = frel_s[warp];
@@ -212,7 +212,9 @@ __global__ void __launch_bounds__(128, 3) kz_kernel(const __grid_constant__ KCPa
         const int r = X + t - Ts(s);
         uint32_t v = 0u;
         if (r >= 1 && r <= m) v = p.tables[packed_code(p.packed_q, qs + r - 1)];
-        rowr[s % 3][r & (kRing - 1)] = v;
+        const int x = r & (kRing - 1);
+        rowr[s % 3][x] = v;
+        if (x < 32) rowr[s % 3][x + kRing] = v;  // a segment reads up to 32 slots on
       };
       auto fill_rows_for = [&](int X) {
         while (sf < nst && X > Ts(sf) + rhi(sf)) ++sf;
@@ -222,6 +224,10 @@ __global__ void __launch_bounds__(128, 3) kz_kernel(const __grid_constant__ KCPa
         const int hv = (v.x <= kKzNegAbs) ? kNeg16 : ::min(::max(v.x - b, kNeg16), 32767);
         const int fv = (v.y <= kKzNegAbs) ? kNeg16 : ::min(::max(v.y - b, kNeg16), 32767);
         return pk16(hv, fv);
+      };
+      auto put_frel = [&](int x, uint32_t v) {
+        frel[x] = v;
+        if (x < 32) frel[x + kFifo] = v;  // a segment reads up to 32 slots on
       };
       // the left input of lane-half 0 at iterations Y .. Y + 31: the previous
       // super-stage's right edge (or column 0), -inf outside the left
@@ -250,7 +256,7 @@ __global__ void __launch_bounds__(128, 3) kz_kernel(const __grid_constant__ KCPa
         }
         fabs[itf & (kFifo - 1)] = v;
         const int b0l = __shfl_sync(FULL, base[0], 0);
-        frel[itf & (kFifo - 1)] = rel_pack(v, b0l);
+        put_frel(itf & (kFifo - 1), rel_pack(v, b0l));
       };
       // lane-half h waits for its window of super-stage s
       auto enter = [&](int h, int s) {
@@ -349,7 +355,7 @@ __global__ void __launch_bounds__(128, 3) kz_kernel(const __grid_constant__ KCPa
             Fin = __vmaxs2(__vsubss2(Fin, dh), NEGV);
             // FIFO entries of this batch, relative to lane 0's new base
             const int b0l = __shfl_sync(FULL, base[0], 0);
-            frel[(it + t) & (kFifo - 1)] = rel_pack(fabs[(it + t) & (kFifo - 1)], b0l);
+            put_frel((it + t) & (kFifo - 1), rel_pack(fabs[(it + t) & (kFifo - 1)], b0l));
             recompute_dr();
           }
           fill_rows_for(it + 64);
@@ -424,10 +430,10 @@ __global__ void __launch_bounds__(128, 3) kz_kernel(const __grid_constant__ KCPa
             const int b0l = __shfl_sync(FULL, base[0], 0);
             const int s0 = __shfl_sync(FULL, o0 ? 1 : 0, 0);
             if (s0) {
-              frel[t] = rel_pack(fabs[t], b0l);
-              frel[t + 32] = rel_pack(fabs[t + 32], b0l);
-              frel[t + 64] = rel_pack(fabs[t + 64], b0l);
-              frel[t + 96] = rel_pack(fabs[t + 96], b0l);
+              put_frel(t, rel_pack(fabs[t], b0l));
+              put_frel(t + 32, rel_pack(fabs[t + 32], b0l));
+              put_frel(t + 64, rel_pack(fabs[t + 64], b0l));
+              put_frel(t + 96, rel_pack(fabs[t + 96], b0l));
             }
           }
           recompute_dr();
@@ -440,12 +446,17 @@ __global__ void __launch_bounds__(128, 3) kz_kernel(const __grid_constant__ KCPa
         const int seg_end = ::max(::min(::min(ne, (it & ~31) + 32), nit), it + 1);
         const uint32_t actm = (act[0] ? 0x0000ffffu : 0u) | (act[1] ? 0xffff0000u : 0u);
         const bool edge_on = (t == 31) && act[1];
-        const uint32_t *rp0 = rowr[sh[0] % 3];
-        const uint32_t *rp1 = rowr[sh[1] % 3];
+        // a segment stays inside one batch of 32 iterations, so its ring and
+        // FIFO entries are contiguous (the rings end in a copy of their
+        // first 32 slots)
         const int ro0 = -t - Ts(sh[0]), ro1 = -t - 32 - Ts(sh[1]), b1 = base[1];
-        for (; it < seg_end; ++it) {
-          const uint32_t twl = rp0[(it + ro0) & (kRing - 1)];
-          const uint32_t twh = rp1[(it + ro1) & (kRing - 1)];
+        const uint32_t *q0 = rowr[sh[0] % 3] + ((it + ro0) & (kRing - 1));
+        const uint32_t *q1 = rowr[sh[1] % 3] + ((it + ro1) & (kRing - 1));
+        const uint32_t *fq = frel + ((it + 1) & (kFifo - 1));
+        KZEdge *bp = bnd + (edge_on ? it + ro1 : 0);
+        for (; it < seg_end; ++it, ++q0, ++q1, ++fq, ++bp) {
+          const uint32_t twl = *q0;
+          const uint32_t twh = *q1;
           uint32_t unused_best = 0u;
           const uint32_t Fout = pk_row<kModeGlobal, K>(
               H, E, Hdiag, Fin, NB, 0u, unused_best, [&](int j) -> uint32_t { return prmt(twl, twh, sel[j]); },
@@ -457,14 +468,14 @@ __global__ void __launch_bounds__(128, 3) kz_kernel(const __grid_constant__ KCPa
             e.f = Fout;
             e.base = b1;
             e.pad = 0;
-            bnd[it + ro1] = e;
+            *bp = e;
           }
           const uint32_t hsnd = (__vadd2(Hout, dr) & actm) | (NEGV & ~actm);
           const uint32_t fsnd = (__vadd2(Fout, dr) & actm) | (NEGV & ~actm);
           uint32_t hs = __shfl_sync(FULL, hsnd, left_lane);
           uint32_t fs = __shfl_sync(FULL, fsnd, left_lane);
           if (t == 0) {
-            const uint32_t wv = frel[(it + 1) & (kFifo - 1)];
+            const uint32_t wv = *fq;
             hs = prmt(wv, hs, 0x5410u);
             fs = prmt(wv, fs, 0x5432u);
           }
