@@ -188,6 +188,7 @@ struct Small {
   int32_t invalid_q, invalid_t;
   unsigned long long band_retries, band_cells;
   int32_t max_rows;
+  int32_t max_band_span;  // max over band pairs of max(m + 1, 128) x super-stages + m, saturated
 };
 
 struct Readback {
@@ -902,6 +903,7 @@ struct BandRun {
     bp.status = &c.small->status;
     bp.cells = &c.small->cells;
     bp.max_rows = &c.small->max_rows;
+    bp.max_span = &c.small->max_band_span;
     bp.stage_cols = kBandStageCols;
     const unsigned nb = (unsigned)((npairs + 255) / 256);
     band_plan_kernel<<<nb, 256, 0, c.s>>>(bp);
@@ -913,12 +915,15 @@ struct BandRun {
     c.launches += 5;
     if (cudaGetLastError() != cudaSuccess) return GA_ERR_CUDA;
     int32_t *h = (int32_t *)pinned_scratch();
-    if (cudaMemcpyAsync(h, &c.small->max_rows, sizeof(int32_t), cudaMemcpyDeviceToHost, c.s) != cudaSuccess ||
+    if (cudaMemcpyAsync(h, &c.small->max_rows, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, c.s) != cudaSuccess ||
         cudaStreamSynchronize(c.s) != cudaSuccess)
       return GA_ERR_CUDA;
     max_rows = h[0];
     if (max_rows > 0) {
-      packed = std::max(c.sc.smax, 0) + c.sc.alpha <= kKzMaxStep;
+      // the packed kernel numbers its iterations in int32: a pair runs at
+      // most max(m + 1, 128) x super-stages + m + 64 of them; calls with
+      // larger pairs take the int32 kernel, which runs one stage at a time
+      packed = std::max(c.sc.smax, 0) + c.sc.alpha <= kKzMaxStep && h[1] < kKzMaxSpan;
       const int occ = std::max(packed ? blocks_per_sm_kz() : blocks_per_sm_kc(), 1);
       const int64_t want = (npairs + kKcWarps - 1) / kKcWarps;
       grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)c.nsm * occ));

@@ -58,6 +58,9 @@ constexpr int kKzMaxStep = 24;
 constexpr int kKzRenorm = 128;          // iterations between base moves
 constexpr int kKzNegAbs = -(1 << 29);   // absolute -inf in the edge FIFO
 constexpr int kKzNever = 1 << 30;       // event iteration of a block that does not exist
+// Largest max(m + 1, 128) x super-stages + m of a pair: its iterations
+// number less than that plus 64, so they stay below kKzNever.
+constexpr int kKzMaxSpan = (1 << 30) - 4096;
 
 // One row of a super-stage's right edge as lane 31 produced it: its raw
 // packed H and F words (the high halves are the edge) and its high half's
@@ -80,6 +83,7 @@ __global__ void __launch_bounds__(128, 3) kz_kernel(const __grid_constant__ KCPa
   __shared__ int2 fabs_s[kWarps][kFifo];        // absolute edge values by iteration
   __shared__ uint32_t frel_s[kWarps][kFifo + 32];  // the same relative to lane 0's base, + a copy of slots 0..31
   __shared__ int2 blk_s[kWarps][2][32];         // per lane-half: first column, first window row
+  __shared__ unsigned long long cells_s[kWarps][32];  // region cells entered, per lane
 
   const int warp = threadIdx.x >> 5, t = threadIdx.x & 31;
   const int left_lane = (t + 31) & 31, right_lane = (t + 1) & 31;
@@ -130,7 +134,9 @@ __global__ void __launch_bounds__(128, 3) kz_kernel(const __grid_constant__ KCPa
     const int dn = n - m;
     const int nb = (n + K - 1) / K;      // blocks
     const int nst = (n + W2 - 1) / W2;   // super-stages
-    unsigned tries = 0, cells = 0;  // per lane: at most m x 16 x super-stages per attempt
+    unsigned tries = 0;
+    unsigned long long *cells = &cells_s[warp][t];
+    *cells = 0ull;
 
     for (;;) {  // one attempt at band width w
       const int lo = (dn < 0 ? dn : 0) - w;
@@ -268,7 +274,7 @@ __global__ void __launch_bounds__(128, 3) kz_kernel(const __grid_constant__ KCPa
           A[h] = Ts(s) + wlo + l;
           Z[h] = Ts(s) + whi + l;
           *(h ? blk1 : blk0) = make_int2(cb, wlo);
-          cells += (unsigned)(whi - wlo + 1) * (unsigned)::min(K, n - cb);
+          *cells += (unsigned long long)(whi - wlo + 1) * (unsigned long long)::min(K, n - cb);
           uint4 v = selb[s % 3][32 * h + t];
           if (h) {
             v.x += 0x44444444u;
@@ -522,7 +528,7 @@ __global__ void __launch_bounds__(128, 3) kz_kernel(const __grid_constant__ KCPa
       ++tries;
       __syncwarp();
     }
-    unsigned long long c64 = cells;
+    unsigned long long c64 = *cells;
 #pragma unroll
     for (int o = 16; o >= 1; o >>= 1) c64 += __shfl_xor_sync(FULL, c64, o);
     if (t == 0 && tries) atomicAdd(p.retries, (unsigned long long)tries);

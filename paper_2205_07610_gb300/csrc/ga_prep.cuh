@@ -301,6 +301,7 @@ struct BandPlanParams {
   int32_t *status;
   unsigned long long *cells;
   int32_t *max_rows;
+  int32_t *max_span;   // max of max(m + 1, 128) x super-stages + m, saturated
   int32_t stage_cols;  // columns of a super-stage of the packed band kernel
 };
 
@@ -327,6 +328,12 @@ __global__ void band_plan_kernel(BandPlanParams p) {
     } else {
       my_cells = (unsigned long long)(m * n);
       atomicMax(p.max_rows, (int)m);
+      {
+        // bound on the packed band kernel's iteration numbers: its super-
+        // stages are at most max(m + 1, 128) iterations apart
+        const int64_t span = (m + 1 > 128 ? m + 1 : 128) * ((n + p.stage_cols - 1) / p.stage_cols) + m;
+        atomicMax(p.max_span, (int)(span < INT32_MAX ? span : INT32_MAX));
+      }
       // The band kernels take pairs from a queue in this order, so the key
       // puts the most work first (the last pairs to start are the short
       // ones): super-stages of stage_cols columns (exact up to 31), then the
