@@ -601,9 +601,15 @@ def compact_band(v):
         return None
     runs = v["runs"]
     best = next(k for k in runs if k.startswith("best_constant"))
-    return r4({"full_dp_ms": v["full_dp_ms"], "learned_ms": runs["learned"]["ms"],
+    lr = runs["learned"]
+    return r4({"full_dp_ms": v["full_dp_ms"], "learned_ms": lr["ms"],
                "best_const_ms": runs[best]["ms"], "w0_16_ms": runs["default_w0_16"]["ms"],
-               "speedup": v["full_dp_ms"] / runs["learned"]["ms"],
+               "speedup": v["full_dp_ms"] / lr["ms"],
+               # cells of the block-rounded bands the learned run evaluated, per
+               # second (full DP: every m x n cell; the two rates compare the
+               # kernels' speed per evaluated cell)
+               "learned_region_gcups": lr["banded_cells"] / (lr["ms"] / 1e3) / 1e9 if lr["ms"] else None,
+               "full_dp_gcups": v.get("full_dp_gcups"),
                "exact": all(r["exact"] for r in runs.values())})
 
 
